@@ -1,0 +1,355 @@
+"""Throughput of the online stage (instantiate + H^2 matvec) on the GB300.
+
+Workload (the FP32 GPU configuration of the parametric H^2 matrix): n = 65536
+points uniform in [0,1]^3 (seed 1002), Matern nu = 3/2 with l in [0.05, 0.5],
+Chebyshev degree 20 in l, p_s = 8, uniform tree of depth 3 (mean leaf 128),
+eta = sqrt(3), TT tolerance 1e-5, far-field rank cap 64, 16 right-hand sides
+~N(0, 1) (seed 2002), one theta per step drawn from U(B_theta) (seed 3002).
+
+A step is one ph_instantiate(theta) + one ph_matvec(X) through the C ABI.
+Metric: (theta * RHS)/s = steps * m / time, summed over ranks (each rank owns
+its own replica and its own thetas: theta-sharded, no collective on the data
+path).  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2511_03109_gb300 import inputs  # noqa: E402
+
+WL = inputs.LARGE_3D_MATERN_H2
+METRIC = "online instantiate+H-MVM (theta*RHS)/s and % HBM roofline at rel.err vs FP64 oracle"
+UNIT = "(theta*RHS)/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+ORACLE_SAMPLE_LEAVES = 1
+
+
+def workload_config():
+    return {
+        "workload": WL.name, "n": WL.n, "d": WL.d, "kernel": WL.kernel,
+        "theta_box": [WL.theta_lo[0], WL.theta_hi[0]], "degree": WL.degree[0], "p_s": WL.p_s,
+        "l_max": WL.l_max, "eta": WL.eta, "tol": WL.tol, "rank_cap": WL.rank_cap,
+        "format": WL.fmt, "m": WL.m, "thetas": "one per step, U(B_theta), seed %d" % WL.theta_seed,
+        "l2": "no flush: the near-field cores streamed every step (> 4 GB) exceed the 129 MB L2",
+        "parallelism": "theta-sharded replicas, one process per GPU",
+    }
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# --------------------------------------------------------------------- oracle (CPU) baseline
+def oracle_sample(P, X, theta, n_leaves=ORACLE_SAMPLE_LEAVES, seed=7):
+    """Oracle online stage on a bounded sample: the rows of n_leaves target leaves.
+
+    Offline work for the sample (its near blocks and the far blocks of its ancestors) is done
+    first with a spawn-started process pool and is not timed; the timed part is the oracle's
+    instantiate + matvec for the sample rows.  Returns (seconds, rows, Y_rows, cores).
+    """
+    import multiprocessing as mp
+
+    from oracle import pmatrix
+
+    M = pmatrix.ParametricMatrix(P, WL.kernel, WL.theta_lo, WL.theta_hi, WL.degree, WL.p_s,
+                                 WL.l_max, WL.eta, WL.tol, rank_cap=WL.rank_cap, fmt=WL.fmt)
+    rng = np.random.default_rng(seed)
+    pick = sorted(rng.choice(len(M.leaves), size=n_leaves, replace=False))
+    targets = [M.leaves[i] for i in pick]
+    workers = max(1, (os.cpu_count() or 2))
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers) as pool:
+        M.offline(targets, pool=pool)
+    t0 = time.perf_counter()
+    inst = M.instantiate(theta, targets)
+    Y = M.matvec(inst, X, targets)
+    dt = time.perf_counter() - t0
+    rows = np.sort(np.concatenate([c.idx for c in targets]))
+    return dt, rows, Y[rows], os.cpu_count() or 1, len(M.leaves)
+
+
+# ------------------------------------------------------------------------ clock sampling
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# -------------------------------------------------------------------------------- our arm
+def run_gpu(args, rank, world, local_rank):
+    import torch
+
+    from paper_2511_03109_gb300 import ph
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    P = WL.points()
+    Xh = WL.rhs()
+    m, n = WL.m, WL.n
+    opts = ph.make_opts(WL.d, WL.theta_lo, WL.theta_hi, WL.degree, WL.p_s, WL.l_max, WL.eta, WL.tol,
+                        rank_cap=WL.rank_cap, fmt=WL.fmt, prec=WL.precision, device=local_rank)
+    A = ph.ParametricMatrix(P, WL.kernel, opts)
+    info = A.info()
+    total_steps = args.warmup + args.steps
+    thetas_all = inputs.uniform_thetas(WL.theta_lo, WL.theta_hi, max(30, world * total_steps), WL.theta_seed)
+    thetas = thetas_all[rank::world][:total_steps]
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    X = torch.tensor(Xh.T, dtype=torch.float32, device=dev).contiguous()  # column-major n x m
+    Y = torch.empty((m, n), dtype=torch.float32, device=dev)
+
+    def step(th):
+        A.instantiate(th, sp)
+        A.matvec_ptr(X.data_ptr(), n, m, Y.data_ptr(), n, sp)
+
+    for k in range(args.warmup):
+        step(thetas[k])
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    A.profile(True)
+    A.profile_read()  # reset counters
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for k in range(args.steps):
+        step(thetas[args.warmup + k])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    clocks = sampler.stop()
+    prof = A.profile_read()
+    A.profile(False)
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # end to end through the host entry point: pinned host X in, Y out every step
+    Xp = torch.tensor(Xh.T, dtype=torch.float32).contiguous().pin_memory()
+    Yp = torch.empty((m, n), dtype=torch.float32).pin_memory()
+
+    def step_host(th):
+        A.instantiate(th, sp)
+        A.matvec_host_ptr(Xp.data_ptr(), n, m, Yp.data_ptr(), n, sp)
+
+    for k in range(min(args.warmup, 3)):
+        step_host(thetas[k])
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        step_host(thetas[args.warmup + k])
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    if rank != 0:
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        A.close()
+        return
+
+    value = world * args.steps * m / (ms / 1e3)
+    peaks, peak_kind = load_peaks()
+    # dominant kernel by device time
+    kinds = {k: v for k, v in prof.items() if v[1] > 0}
+    dom = max(kinds, key=lambda k: kinds[k][0])
+    dom_ms, dom_launches = kinds[dom]
+    avg_ms = dom_ms / dom_launches
+    sc = 4
+    if dom == "near":
+        alg = info["near_bytes"] + 2.0 * n * m * sc + info["near_rank_sum"] * sc
+        roof = {"bound": "hbm", "achieved": alg / (avg_ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "per_launch_bytes": alg}
+    else:
+        # FP32 SIMT flops of the far path: the coupling chain and sweeps
+        fl = (info["flops_per_rhs"] - 2.0 * info["near_entries"]) * m
+        alu_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) / 1e6
+        roof = {"bound": "alu", "achieved": fl / (avg_ms / 1e3) / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
+                "per_launch_flops": fl}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["kernel"] = dom + "_kernel"
+    roof["peak_source"] = peak_kind
+    roof["traffic"] = None
+    gpu_launches = int(sum(v[1] for v in prof.values()))
+    # whole-step bytes over the step time, for context
+    step_bytes = info["alg_bytes_per_call"] + 2.0 * n * m * sc
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(), "roofline": roof,
+        "step_hbm_fraction": step_bytes / (ms / args.steps / 1e3) / 1e9 / peaks["hbm_gbs"],
+        "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kinds.items()},
+        "gpu_launches": gpu_launches, "clocks": clocks,
+        "e2e": {"value": world * args.steps * m / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": n * m * sc + 8 * WL.d, "d2h_bytes_per_step": n * m * sc},
+        "offline_seconds": info["offline_seconds"],
+        "structure": {k: info[k] for k in ("n_near", "n_far", "n_far_keys", "near_entries", "near_rank_max",
+                                           "far_rank_max", "far_rank_mean", "near_bytes", "far_bytes")},
+    }
+    if not args.no_cpu_baseline:
+        th0 = thetas[args.warmup]
+        A.instantiate(th0, sp)
+        A.matvec_ptr(X.data_ptr(), n, m, Y.data_ptr(), n, sp)
+        torch.cuda.synchronize()
+        Ygpu = Y.double().cpu().numpy().T
+        dt, rows, Yo, cores, nleaves = oracle_sample(P, Xh, th0)
+        frac = len(rows) / n
+        out["cpu_baseline"] = {"value": m / (dt / frac), "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": f"rows of {ORACLE_SAMPLE_LEAVES} of {nleaves} target leaves "
+                                         f"({len(rows)} rows, 16 RHS, one theta); time scaled by n / rows"}
+        err = np.linalg.norm(Ygpu[rows] - Yo, axis=0) / np.linalg.norm(Yo, axis=0)
+        out["rel_err_vs_oracle"] = float(err.max())
+        from oracle import kernels
+        exact = kernels.dense_apply(WL.kernel, P, th0, Xh, rows=rows)
+        out["rel_err_vs_exact"] = float((np.linalg.norm(Ygpu[rows] - exact, axis=0)
+                                         / np.linalg.norm(exact, axis=0)).max())
+    print(json.dumps(out), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    A.close()
+
+
+# -------------------------------------------------------------------- reference (oracle) arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    P = WL.points()
+    Xh = WL.rhs()
+    m, n = WL.m, WL.n
+    thetas = inputs.uniform_thetas(WL.theta_lo, WL.theta_hi, max(30, args.warmup + args.steps), WL.theta_seed)
+    import multiprocessing as mp
+
+    from oracle import pmatrix
+
+    M = pmatrix.ParametricMatrix(P, WL.kernel, WL.theta_lo, WL.theta_hi, WL.degree, WL.p_s, WL.l_max,
+                                 WL.eta, WL.tol, rank_cap=WL.rank_cap, fmt=WL.fmt)
+    rng = np.random.default_rng(7)
+    targets = [M.leaves[i] for i in sorted(rng.choice(len(M.leaves), size=ORACLE_SAMPLE_LEAVES, replace=False))]
+    with mp.get_context("spawn").Pool(max(1, os.cpu_count() or 2)) as pool:
+        M.offline(targets, pool=pool)
+    rows = np.concatenate([c.idx for c in targets])
+    frac = len(rows) / n
+
+    def step(th):
+        M.matvec(M.instantiate(th, targets), Xh, targets)
+
+    for k in range(args.warmup):
+        step(thetas[k])
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        step(thetas[args.warmup + k])
+    dt = (time.perf_counter() - t0) / frac
+    value = args.steps * m / dt
+    cores = os.cpu_count() or 1
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": workload_config(),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"rows of {ORACLE_SAMPLE_LEAVES} of {len(M.leaves)} target leaves per step "
+                                      f"({len(rows)} rows, 16 RHS); time scaled by n / rows"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gpu(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,187 @@
+/*
+ * libph -- online stage of parametric H- and H^2-matrices on one GB300 (sm_103a).
+ *
+ * Method: Khan, Chen, Rao, Saibaba, "Parametric Hierarchical Matrix
+ * Approximations to Kernel Matrices".  The problem statement (§1): for points
+ * X = (x_i) in a box B of R^d and a parametric kernel kappa(x, y; theta) with
+ * theta in a box B_theta of R^{d_theta}, approximate K(X, X; theta) once
+ * (offline) so that for any theta the hierarchical matrix K_hat(theta) can be
+ * instantiated without new kernel evaluations and applied to vectors (online).
+ *
+ * Conventions shared by every call:
+ *   - Every call returns a ph_status; no C++ exception crosses this boundary.
+ *     On failure, ph_last_error(handle) (or ph_last_error(NULL) when no handle
+ *     exists) returns a one-line description.
+ *   - Device pointers are plain CUDA global-memory addresses on the handle's
+ *     device; host pointers are ordinary process memory.
+ *   - Matrices are column-major: element (i, j) of an n x m matrix with
+ *     leading dimension ld is at [i + j * ld], ld >= n.
+ *   - Streams are passed as `void*` holding a cudaStream_t (NULL = default
+ *     stream).  ph_instantiate and ph_matvec are stream-ordered and
+ *     asynchronous; one handle must not be used on two streams at once.
+ *   - The scalar type of X and Y is double for PH_FP64 handles and float for
+ *     PH_FP32 handles.
+ */
+#ifndef PH_H
+#define PH_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ph_handle ph_handle;
+
+typedef enum {
+    PH_OK = 0,
+    PH_ERR_INVALID_ARG = 1,       /* bad pointer, size, option or point outside the root box */
+    PH_ERR_THETA_OUT_OF_BOX = 2,  /* theta outside B_theta: the interpolant is defined on B_theta only */
+    PH_ERR_NOT_INSTANTIATED = 3,  /* ph_matvec before any successful ph_instantiate */
+    PH_ERR_OOM = 4,               /* host or device allocation failed */
+    PH_ERR_CUDA = 5,              /* a CUDA, cuBLAS or cuSOLVER call failed (no device, launch error ...) */
+    PH_ERR_NONFINITE = 6,         /* non-finite theta, or non-finite X when check_finite is set */
+    PH_ERR_TIMEOUT = 7,           /* a bounded device-side wait ran out */
+    PH_ERR_IO = 8,                /* ph_save / ph_load file error or bad file */
+    PH_ERR_UNSUPPORTED = 9        /* option combination not implemented */
+} ph_status;
+
+/* Kernel functions kappa(x, y; theta), r = |x - y|_2.  The first three are the
+ * workloads' kernels; SE, E and MQ are the paper's (§6 kernel table);
+ * POLY / POLYXY are exact-interpolation test kernels. */
+typedef enum {
+    PH_KERNEL_GAUSS = 0,        /* exp(-r^2 / (2 l^2)),                     theta = (l)        */
+    PH_KERNEL_MATERN32 = 1,     /* (1 + sqrt(3) r/l) exp(-sqrt(3) r/l),     theta = (l)        */
+    PH_KERNEL_MATERN52 = 2,     /* (1 + sqrt(5) r/l + 5 r^2/(3 l^2)) exp(-sqrt(5) r/l)          */
+    PH_KERNEL_ANISO_GAUSS = 3,  /* exp(-sum_k (x_k - y_k)^2 / (2 l_k^2)),   theta = (l_1..l_d) */
+    PH_KERNEL_SE = 4,           /* exp(-(r/l)^2)                                                */
+    PH_KERNEL_EXPONENTIAL = 5,  /* exp(-r/l)                                                    */
+    PH_KERNEL_MULTIQUADRIC = 6, /* (1 + (r/l)^2)^(1/2)                                          */
+    PH_KERNEL_POLY = 7,         /* 1 + theta r^2 + theta^2 r^4                                  */
+    PH_KERNEL_POLYXY = 8        /* (1 + x.y)^2 (1 + theta); not translation-invariant           */
+} ph_kernel;
+
+typedef enum { PH_FMT_H2 = 0, PH_FMT_H = 1 } ph_format;       /* Definitions of §4.1 */
+typedef enum { PH_FP64 = 0, PH_FP32 = 1 } ph_precision;       /* stored cores and online arithmetic */
+
+/* Options of the offline stage (Algs. "Offline Stage: Parametric H-matrix" and
+ * "... H^2-matrix", §4.4).  Fixed-size arrays keep the struct plain. */
+typedef struct {
+    int d;                 /* spatial dimension, 1..3 */
+    int dtheta;            /* parameter dimension, 1..3 */
+    double theta_lo[3];    /* parameter box B_theta = prod [theta_lo_i, theta_hi_i] */
+    double theta_hi[3];
+    int degree[3];         /* Chebyshev degree in theta_i; p_theta_i = degree_i + 1 nodes (§2.2) */
+    int p_s;               /* spatial Chebyshev nodes per dimension (§2.2), 1..16 */
+    int l_max;             /* depth of the uniform 2^d-ary cluster tree (§3.2), 0..10 */
+    double eta;            /* admissibility parameter (§3.4) */
+    double tol;            /* TT-SVD tolerance eps for the far field */
+    double near_tol;       /* TT-SVD tolerance for the near field; < 0 means tol */
+    int rank_cap;          /* cap on every far-field TT rank; 0 = no cap */
+    ph_format fmt;
+    ph_precision prec;
+    int dedup;             /* 1: compress one far tensor per (level, offset) class (§5.2);
+                              forced off for kernels that are not translation-invariant */
+    int check_finite;      /* 1: ph_matvec checks X for non-finite entries (synchronises) */
+    int device;            /* CUDA device ordinal */
+} ph_build_opts;
+
+/* Sizes and counts of a built handle; all byte counts are of stored data. */
+typedef struct {
+    long n;                  /* points */
+    int d, dtheta, p_s, p_theta[3];
+    int prec, fmt;
+    int n_nodes, n_leaves, tree_depth;
+    long n_near, n_far, n_far_keys;   /* near blocks, far blocks, compressed far tensors */
+    long near_entries;       /* sum over near blocks of n_s * n_t */
+    long near_rank_sum;      /* sum over near blocks of r_{b,1} */
+    int near_rank_max, far_rank_max;
+    double far_rank_mean;    /* mean over far blocks of max(r_{b,d}, r_{b,d+dtheta}) (paper's "Rank", §6) */
+    long near_bytes;         /* stored near-field cores G_{b,1} (the online stream) */
+    long near_theta_bytes;   /* stored near-field theta cores */
+    long far_bytes;          /* far-field cores (all keys), plus S_b / T_b for the H format */
+    long basis_bytes;        /* leaf factor matrices U_{s,k} and transfer factors */
+    double alg_bytes_per_call;   /* bytes one ph_instantiate + ph_matvec with m = 1 must move
+                                    (excluding X / Y); add 2 * n * m * scalar for X and Y */
+    double flops_per_rhs;    /* online flops per right-hand side (instantiate excluded) */
+    double offline_seconds;  /* wall time of ph_offline_build */
+} ph_info;
+
+/* Build the parametric matrix (offline stage).
+ *   points : host, n x d, row-major doubles (point i at points[i*d .. i*d+d-1]),
+ *            read only during the call; every point must lie in [0,1]^d (§6).
+ *   out    : receives a new handle owning all host and device data.
+ * The tree is the uniform tree of §3.2 (depth l_max), the block tree that of
+ * §3.4; near blocks are compressed by TT-SVD of A_b (§4.3), far blocks by
+ * TT-SVD of M_b (§4.2, App. A.4).  Runs on the GPU (FP64). */
+ph_status ph_offline_build(const double* points, long n, ph_kernel kernel,
+                           const ph_build_opts* opts, ph_handle** out);
+
+/* Online stage (Alg. "Online Stage", §4.4): evaluate the parametric vectors
+ * v_i(theta_i) (App. A.4) in FP64, the near-field weights prod_i G_{b,i+1} x_2 v_i
+ * (§4.3) and the far-field core matrices H_b(theta) (Alg. PTTK online, App. A.4).
+ *   theta : host, d_theta doubles; must lie in B_theta.
+ * Stream-ordered; theta is copied before the call returns. */
+ph_status ph_instantiate(ph_handle* h, const double* theta, void* stream);
+
+/* Y = K_hat(theta) X for the last instantiated theta (§4.5: the H-matrix MVM with
+ * S_b H_b T_b^T far blocks, or Alg. "Modified H^2-Matrix MVM").
+ *   X : device, n x m column-major, leading dimension ldx >= n, original point order.
+ *   Y : device, n x m column-major, leading dimension ldy >= n; overwritten.
+ *   m : number of right-hand sides, 1..1024.
+ * X and Y must not overlap.  Stream-ordered and asynchronous. */
+ph_status ph_matvec(ph_handle* h, const void* X, long ldx, int m, void* Y, long ldy,
+                    void* stream);
+
+/* ph_matvec on HOST buffers: copies X to the device, applies K_hat(theta),
+ * copies Y back and synchronises the stream before returning.  X and Y are
+ * host pointers with the same layout as in ph_matvec (pinned memory makes the
+ * copies asynchronous DMA). */
+ph_status ph_matvec_host(ph_handle* h, const void* X, long ldx, int m, void* Y, long ldy,
+                         void* stream);
+
+/* Fill *info with sizes and counts of a built handle. */
+ph_status ph_get_info(const ph_handle* h, ph_info* info);
+
+/* Serialise a handle (tree, block lists, all stored cores) to a file / rebuild a
+ * handle from such a file on the device recorded in it (or opts-less default 0). */
+ph_status ph_save(const ph_handle* h, const char* path);
+ph_status ph_load(const char* path, int device, ph_handle** out);
+
+/* Release every host and device resource of the handle; NULL is ignored. */
+void ph_destroy(ph_handle* h);
+
+/* Description of the last error on this handle (or of the last failed call
+ * without a handle when h is NULL).  Never NULL; valid until the next call. */
+const char* ph_last_error(const ph_handle* h);
+
+/* Host-only planning (no GPU needed): builds the cluster tree (§3.2) and the
+ * block cluster tree (§3.4) for the given points and reports their sizes.
+ *   counts : host array of 8 longs receiving
+ *            {nodes, leaves, near blocks, far blocks, far keys (dedup classes),
+ *             sum of near n_s*n_t, max near blocks per leaf, depth}
+ *   perm   : host array of n ints or NULL; receives, for each position of the
+ *            cluster order, the original point index. */
+ph_status ph_plan(const double* points, long n, int d, int l_max, double eta,
+                  long* counts, int* perm);
+
+/* Per-kernel device time, measured with CUDA events recorded on the stream each
+ * kernel is launched on (for roofline reports).  While enabled, every launch of
+ * the library is bracketed by an event pair; ph_profile_read synchronises the
+ * handle's streams and returns, for each of the PH_PROF_KINDS kernel kinds in
+ * the order
+ *   0 instantiate, 1 gather, 2 near, 3 upsweep_leaf, 4 transfer_up,
+ *   5 coupling, 6 transfer_down, 7 far_h, 8 combine,
+ * the summed milliseconds and the number of launches since the last read (or
+ * since enabling), then starts a new count.  ms and launches are host arrays of
+ * PH_PROF_KINDS elements. */
+#define PH_PROF_KINDS 9
+ph_status ph_profile_enable(ph_handle* h, int enable);
+ph_status ph_profile_read(ph_handle* h, double* ms, long* launches);
+
+/* Library version string. */
+const char* ph_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PH_H */

@@ -1,0 +1,508 @@
+// The C ABI of libph (include/ph.h): argument checks, error capture, device
+// views, workspace, save / load.  No computation of the method happens here.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <exception>
+#include <fstream>
+#include <new>
+#include <stdexcept>
+#include <string>
+
+#include "common.cuh"
+#include "handle.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+ph_status fail(ph_handle* h, ph_status s, const std::string& msg) {
+    g_last_error = msg;
+    if (h) h->last_error = msg;
+    return s;
+}
+
+template <typename F>
+ph_status guarded(ph_handle* h, F&& f) {
+    try {
+        return f();
+    } catch (const ph::Error& e) {
+        return fail(h, e.status, e.what());
+    } catch (const std::bad_alloc&) {
+        return fail(h, PH_ERR_OOM, "host allocation failed");
+    } catch (const std::invalid_argument& e) {
+        return fail(h, PH_ERR_INVALID_ARG, e.what());
+    } catch (const std::exception& e) {
+        return fail(h, PH_ERR_CUDA, e.what());
+    }
+}
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+}  // namespace
+
+namespace ph {
+
+void dev_free(ph_handle* h, void* p) {
+    if (!p) return;
+    for (auto it = h->buffers.begin(); it != h->buffers.end(); ++it)
+        if (it->ptr == p) {
+            cudaFree(p);
+            h->buffers.erase(it);
+            return;
+        }
+}
+
+template <typename T>
+static void fill_view(ph_handle* h, DevView<T>& v, const std::vector<long>& io, const std::vector<long>& lo) {
+    const Plan& plan = h->plan;
+    const int* I = h->d_int;
+    const long long* L = h->d_ll;
+    v = DevView<T>{};
+    v.n = (int)plan.n;
+    v.d = plan.d;
+    v.p_s = h->opts.p_s;
+    v.PD = h->PD;
+    v.n_leaves = (int)plan.leaves.size();
+    v.n_nodes = (int)plan.nodes.size();
+    v.perm = I + io[0];
+    v.node_begin = I + io[1];
+    v.node_end = I + io[2];
+    v.node_halves = I + io[3];
+    v.node_children = I + io[4];
+    v.node_child_off = I + io[5];
+    v.leaf_node = I + io[6];
+    v.node_leaf = I + io[7];
+    v.node_level = I + io[8];
+    v.near_by_leaf = I + io[9];
+    v.nb_t = I + io[10];
+    v.nb_rank = I + io[11];
+    v.nb_woff = I + io[12];
+    v.key_ranks = I + io[13];
+    v.fb_t = I + io[14];
+    v.fb_key = I + io[15];
+    v.far_targets = I + io[16];
+    v.far_by_target = I + io[17];
+    v.level_slot = I + io[18];
+    v.nb_off = L + lo[0];
+    v.nb_toff = L + lo[1];
+    v.key_off = L + lo[2];
+    v.key_hoff = L + lo[3];
+    v.fb_soff = L + lo[4];
+    v.fb_toff = L + lo[5];
+    v.dtheta = h->opts.dtheta;
+    for (int k = 0; k < 3; ++k) v.p_theta[k] = (k < h->opts.dtheta) ? h->opts.degree[k] + 1 : 1;
+    v.theta_nodes = h->d_dbl;
+    v.theta_bw = h->d_dbl + kMaxDim * kMaxPTheta;
+    v.v64 = h->d_v64;
+    v.n_near = (int)plan.near_s.size();
+    v.near_cores = (const T*)h->d_near;
+    v.near_theta = h->d_near_theta;
+    v.w = (T*)h->d_w;
+    v.n_keys = (int)plan.key_rep.size();
+    v.Delta = h->Delta;
+    v.far_cores = (const T*)h->d_far;
+    v.far_theta = h->d_far_theta;
+    v.H = (T*)h->d_H;
+    v.n_far = (int)plan.far_s.size();
+    v.n_far_targets = (int)plan.far_targets.size();
+    v.st = (const T*)h->d_st;
+    v.n_far_levels = h->n_far_levels;
+    v.U = (const T*)h->d_U;
+    v.E = (const T*)h->d_E;
+    v.mcap = h->mcap;
+    v.Xc = (T*)h->d_Xc;
+    v.Ynear = (T*)h->d_Ynear;
+    v.yfar = (T*)h->d_yfar;
+    v.xhat = (T*)h->d_xhat;
+    v.yhat = (T*)h->d_yhat;
+    v.flags = h->d_flags;
+}
+
+// Packs the plan's index arrays into two device allocations and fills the views.
+void refresh_views(ph_handle* h) {
+    const Plan& plan = h->plan;
+    std::vector<int> ints;
+    std::vector<long> io;
+    auto put = [&](const std::vector<int>& a) {
+        io.push_back((long)ints.size());
+        ints.insert(ints.end(), a.begin(), a.end());
+        ints.push_back(0);  // keep every segment non-empty
+    };
+    const int nn = (int)plan.nodes.size();
+    std::vector<int> nb(nn), ne(nn), nh(nn), ch, choff(nn + 1, 0), nl(nn), lev(nn);
+    for (int i = 0; i < nn; ++i) {
+        nb[i] = plan.nodes[i].begin;
+        ne[i] = plan.nodes[i].end;
+        nh[i] = plan.nodes[i].halves;
+        nl[i] = plan.nodes[i].leaf;
+        lev[i] = plan.nodes[i].level;
+        for (int c : plan.nodes[i].children) ch.push_back(c);
+        choff[i + 1] = (int)ch.size();
+    }
+    // levels that own far targets get a slot in y_far (H format)
+    h->level_slot.assign(plan.depth + 1, -1);
+    h->n_far_levels = 0;
+    h->min_far_level = plan.depth;
+    for (int s : plan.far_targets) {
+        int l = plan.nodes[s].level;
+        h->min_far_level = std::min(h->min_far_level, l);
+        if (h->level_slot[l] < 0) h->level_slot[l] = 1;
+    }
+    for (int l = 0; l <= plan.depth; ++l)
+        if (h->level_slot[l] > 0) h->level_slot[l] = h->n_far_levels++;
+    // inner nodes per level, for the sweeps
+    h->level_nodes.assign(plan.depth + 1, {});
+    for (int i = 0; i < nn; ++i)
+        if (!plan.nodes[i].children.empty()) h->level_nodes[plan.nodes[i].level].push_back(i);
+    std::vector<int> lvl_flat;
+    h->level_nodes_off.assign(plan.depth + 2, 0);
+    for (int l = 0; l <= plan.depth; ++l) {
+        lvl_flat.insert(lvl_flat.end(), h->level_nodes[l].begin(), h->level_nodes[l].end());
+        h->level_nodes_off[l + 1] = (int)lvl_flat.size();
+    }
+    std::vector<int> fbt = plan.far_by_target;
+    if (fbt.empty()) fbt.push_back(0);
+    put(plan.perm);                 // 0
+    put(nb);                        // 1
+    put(ne);                        // 2
+    put(nh);                        // 3
+    put(ch);                        // 4
+    put(choff);                     // 5
+    put(plan.leaves);               // 6
+    put(nl);                        // 7
+    put(lev);                       // 8
+    put(plan.near_by_leaf);         // 9
+    put(plan.near_t);               // 10
+    put(h->nb_rank);                // 11
+    put(h->nb_woff);                // 12
+    put(h->key_ranks);              // 13
+    put(plan.far_t);                // 14
+    put(plan.far_key);              // 15
+    put(plan.far_targets);          // 16
+    put(fbt);                       // 17
+    put(h->level_slot);             // 18
+    put(lvl_flat);                  // 19
+    std::vector<long long> lls;
+    std::vector<long> lo;
+    auto putl = [&](const std::vector<long long>& a) {
+        lo.push_back((long)lls.size());
+        lls.insert(lls.end(), a.begin(), a.end());
+        lls.push_back(0);
+    };
+    putl(h->nb_off);
+    putl(h->nb_toff);
+    putl(h->key_off);
+    putl(h->key_hoff);
+    putl(h->fb_soff);
+    putl(h->fb_toff);
+    dev_free(h, h->d_int);
+    dev_free(h, h->d_ll);
+    dev_free(h, h->d_dbl);
+    h->d_int = (int*)dev_alloc(h, ints.size() * sizeof(int));
+    PH_CUDA(cudaMemcpy(h->d_int, ints.data(), ints.size() * sizeof(int), cudaMemcpyHostToDevice));
+    h->d_ll = (long long*)dev_alloc(h, lls.size() * sizeof(long long));
+    PH_CUDA(cudaMemcpy(h->d_ll, lls.data(), lls.size() * sizeof(long long), cudaMemcpyHostToDevice));
+    std::vector<double> dbl(h->theta_nodes);
+    dbl.insert(dbl.end(), h->theta_bw.begin(), h->theta_bw.end());
+    h->d_dbl = (double*)dev_alloc(h, dbl.size() * sizeof(double));
+    PH_CUDA(cudaMemcpy(h->d_dbl, dbl.data(), dbl.size() * sizeof(double), cudaMemcpyHostToDevice));
+    if (!h->d_v64) h->d_v64 = (double*)dev_alloc(h, kMaxDim * kMaxPTheta * sizeof(double));
+    if (!h->d_flags) h->d_flags = (int*)dev_alloc(h, 4 * sizeof(int));
+    h->d_level_nodes = h->d_int + io[19];
+    fill_view<float>(h, h->vf, io, lo);
+    fill_view<double>(h, h->vd, io, lo);
+    h->view_io = io;
+    h->view_lo = lo;
+}
+
+// Sizes the per-call workspace for m right-hand sides (padded to the chunk width).
+void ensure_workspace(ph_handle* h, int m) {
+    const int mc = (m <= 1) ? 1 : (m <= 2) ? 2 : (m <= 4) ? 4 : (m <= 8) ? 8 : 16;
+    const int S = (int)ceil_div(m, mc) * mc;
+    if (S <= h->mcap) return;
+    const Plan& plan = h->plan;
+    const size_t sc = h->scalar;
+    for (void* p : {h->d_Xc, h->d_Ynear, h->d_yfar, h->d_xhat, h->d_yhat}) dev_free(h, p);
+    h->d_Xc = dev_alloc(h, (size_t)plan.n * S * sc);
+    h->d_Ynear = dev_alloc(h, (size_t)plan.n * S * sc);
+    h->d_yfar = nullptr;
+    h->d_xhat = h->d_yhat = nullptr;
+    if (h->opts.fmt == PH_FMT_H && h->n_far_levels > 0)
+        h->d_yfar = dev_alloc(h, (size_t)h->n_far_levels * plan.n * S * sc);
+    if (h->opts.fmt == PH_FMT_H2 && !plan.far_targets.empty()) {
+        h->d_xhat = dev_alloc(h, (size_t)plan.nodes.size() * h->PD * S * sc);
+        h->d_yhat = dev_alloc(h, (size_t)plan.nodes.size() * h->PD * S * sc);
+    }
+    h->mcap = S;
+    fill_view<float>(h, h->vf, h->view_io, h->view_lo);
+    fill_view<double>(h, h->vd, h->view_io, h->view_lo);
+}
+
+}  // namespace ph
+
+extern "C" {
+
+const char* ph_version(void) { return "libph 0.1 (sm_103a)"; }
+
+const char* ph_last_error(const ph_handle* h) {
+    if (h) return h->last_error.c_str();
+    return g_last_error.c_str();
+}
+
+ph_status ph_plan(const double* points, long n, int d, int l_max, double eta, long* counts, int* perm) {
+    return guarded(nullptr, [&]() -> ph_status {
+        if (!points || !counts || n < 1 || d < 1 || d > 3 || l_max < 0 || l_max > 10 || !(eta > 0))
+            return fail(nullptr, PH_ERR_INVALID_ARG, "ph_plan: invalid argument");
+        ph::Plan plan;
+        ph::build_plan(points, n, d, l_max, eta, true, plan);
+        long sum_near = 0;
+        for (size_t b = 0; b < plan.near_s.size(); ++b)
+            sum_near += (long)plan.nodes[plan.near_s[b]].size() * plan.nodes[plan.near_t[b]].size();
+        int maxper = 0;
+        for (size_t l = 0; l + 1 < plan.near_by_leaf.size(); ++l)
+            maxper = std::max(maxper, plan.near_by_leaf[l + 1] - plan.near_by_leaf[l]);
+        counts[0] = (long)plan.nodes.size();
+        counts[1] = (long)plan.leaves.size();
+        counts[2] = (long)plan.near_s.size();
+        counts[3] = (long)plan.far_s.size();
+        counts[4] = (long)plan.key_rep.size();
+        counts[5] = sum_near;
+        counts[6] = maxper;
+        counts[7] = plan.depth;
+        if (perm)
+            for (long i = 0; i < n; ++i) perm[i] = plan.perm[i];
+        return PH_OK;
+    });
+}
+
+ph_status ph_offline_build(const double* points, long n, ph_kernel kernel, const ph_build_opts* o,
+                           ph_handle** out) {
+    if (!out) return fail(nullptr, PH_ERR_INVALID_ARG, "ph_offline_build: out is NULL");
+    *out = nullptr;
+    if (!points || !o || n < 1) return fail(nullptr, PH_ERR_INVALID_ARG, "ph_offline_build: invalid argument");
+    if (o->d < 1 || o->d > 3 || o->dtheta < 1 || o->dtheta > 3 || o->p_s < 1 || o->p_s > ph::kMaxPs ||
+        o->l_max < 0 || o->l_max > 10 || !(o->eta > 0) || !(o->tol >= 0) || o->rank_cap < 0 ||
+        (o->fmt != PH_FMT_H && o->fmt != PH_FMT_H2) || (o->prec != PH_FP32 && o->prec != PH_FP64) ||
+        (int)kernel < 0 || (int)kernel > PH_KERNEL_POLYXY)
+        return fail(nullptr, PH_ERR_INVALID_ARG, "ph_offline_build: option out of range");
+    if (kernel == PH_KERNEL_ANISO_GAUSS && o->dtheta != o->d)
+        return fail(nullptr, PH_ERR_INVALID_ARG, "anisotropic Gaussian needs d_theta = d");
+    for (int k = 0; k < o->dtheta; ++k)
+        if (!(o->theta_lo[k] < o->theta_hi[k]) || o->degree[k] < 0 || o->degree[k] + 1 > ph::kMaxPTheta)
+            return fail(nullptr, PH_ERR_INVALID_ARG, "ph_offline_build: bad parameter box or degree");
+    ph_handle* h = nullptr;
+    try {
+        h = new ph_handle();
+    } catch (...) {
+        return fail(nullptr, PH_ERR_OOM, "host allocation failed");
+    }
+    h->kernel = kernel;
+    h->opts = *o;
+    h->device = o->device;
+    ph_status st = guarded(h, [&]() -> ph_status {
+        int ndev = 0;
+        if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= o->device || o->device < 0) {
+            cudaGetLastError();
+            throw ph::Error(PH_ERR_CUDA, "no CUDA device " + std::to_string(o->device));
+        }
+        ph::offline_build(h, points, n);
+        ph::refresh_views(h);
+        PH_CUDA(cudaDeviceSynchronize());
+        return PH_OK;
+    });
+    if (st != PH_OK) {
+        g_last_error = h->last_error;
+        ph::free_device(h);
+        delete h;
+        return st;
+    }
+    *out = h;
+    return PH_OK;
+}
+
+ph_status ph_instantiate(ph_handle* h, const double* theta, void* stream) {
+    if (!h) return fail(nullptr, PH_ERR_INVALID_ARG, "ph_instantiate: NULL handle");
+    if (!theta) return fail(h, PH_ERR_INVALID_ARG, "ph_instantiate: NULL theta");
+    for (int k = 0; k < h->opts.dtheta; ++k) {
+        if (!std::isfinite(theta[k])) return fail(h, PH_ERR_NONFINITE, "theta is not finite");
+        if (theta[k] < h->opts.theta_lo[k] || theta[k] > h->opts.theta_hi[k])
+            return fail(h, PH_ERR_THETA_OUT_OF_BOX, "theta outside the parameter box");
+    }
+    return guarded(h, [&]() -> ph_status {
+        PH_CUDA(cudaSetDevice(h->device));
+        ph::online_instantiate(h, theta, as_stream(stream));
+        h->instantiated = true;
+        return PH_OK;
+    });
+}
+
+static ph_status check_mv(ph_handle* h, const void* X, long ldx, int m, void* Y, long ldy) {
+    if (!h) return fail(nullptr, PH_ERR_INVALID_ARG, "ph_matvec: NULL handle");
+    if (!X || !Y || m < 1 || m > 1024 || ldx < h->plan.n || ldy < h->plan.n)
+        return fail(h, PH_ERR_INVALID_ARG, "ph_matvec: invalid argument");
+    if (!h->instantiated) return fail(h, PH_ERR_NOT_INSTANTIATED, "ph_matvec before ph_instantiate");
+    return PH_OK;
+}
+
+ph_status ph_matvec(ph_handle* h, const void* X, long ldx, int m, void* Y, long ldy, void* stream) {
+    ph_status s = check_mv(h, X, ldx, m, Y, ldy);
+    if (s != PH_OK) return s;
+    return guarded(h, [&]() -> ph_status {
+        PH_CUDA(cudaSetDevice(h->device));
+        return ph::online_matvec(h, X, ldx, m, Y, ldy, as_stream(stream));
+    });
+}
+
+ph_status ph_matvec_host(ph_handle* h, const void* X, long ldx, int m, void* Y, long ldy, void* stream) {
+    ph_status s = check_mv(h, X, ldx, m, Y, ldy);
+    if (s != PH_OK) return s;
+    return guarded(h, [&]() -> ph_status {
+        PH_CUDA(cudaSetDevice(h->device));
+        cudaStream_t st = as_stream(stream);
+        const size_t sc = h->scalar, n = (size_t)h->plan.n;
+        const size_t need = n * m * sc;
+        if (h->host_stage_x.bytes < need) {
+            ph::dev_free(h, h->host_stage_x.ptr);
+            ph::dev_free(h, h->host_stage_y.ptr);
+            h->host_stage_x = {ph::dev_alloc(h, need), need};
+            h->host_stage_y = {ph::dev_alloc(h, need), need};
+        }
+        PH_CUDA(cudaMemcpy2DAsync(h->host_stage_x.ptr, n * sc, X, (size_t)ldx * sc, n * sc, m,
+                                  cudaMemcpyHostToDevice, st));
+        ph::online_matvec(h, h->host_stage_x.ptr, (long)n, m, h->host_stage_y.ptr, (long)n, st);
+        PH_CUDA(cudaMemcpy2DAsync(Y, (size_t)ldy * sc, h->host_stage_y.ptr, n * sc, n * sc, m,
+                                  cudaMemcpyDeviceToHost, st));
+        PH_CUDA(cudaStreamSynchronize(st));
+        return PH_OK;
+    });
+}
+
+ph_status ph_get_info(const ph_handle* h, ph_info* info) {
+    if (!h || !info) return fail(nullptr, PH_ERR_INVALID_ARG, "ph_get_info: NULL argument");
+    const ph::Plan& plan = h->plan;
+    ph_info r{};
+    r.n = plan.n;
+    r.d = plan.d;
+    r.dtheta = h->opts.dtheta;
+    r.p_s = h->opts.p_s;
+    for (int k = 0; k < 3; ++k) r.p_theta[k] = (k < h->opts.dtheta) ? h->opts.degree[k] + 1 : 0;
+    r.prec = h->opts.prec;
+    r.fmt = h->opts.fmt;
+    r.n_nodes = (int)plan.nodes.size();
+    r.n_leaves = (int)plan.leaves.size();
+    r.tree_depth = plan.depth;
+    r.n_near = (long)plan.near_s.size();
+    r.n_far = (long)plan.far_s.size();
+    r.n_far_keys = (long)plan.key_rep.size();
+    const int D = h->Delta, d = plan.d;
+    for (size_t b = 0; b < plan.near_s.size(); ++b) {
+        r.near_entries += (long)plan.nodes[plan.near_s[b]].size() * plan.nodes[plan.near_t[b]].size();
+        r.near_rank_sum += h->nb_rank[b];
+        r.near_rank_max = std::max(r.near_rank_max, h->nb_rank[b]);
+    }
+    double rank_sum = 0;
+    for (size_t k = 0; k < plan.key_rep.size(); ++k)
+        for (int i = 0; i <= D; ++i) r.far_rank_max = std::max(r.far_rank_max, h->key_ranks[k * (D + 1) + i]);
+    for (size_t b = 0; b < plan.far_s.size(); ++b) {
+        const int* rk = &h->key_ranks[(size_t)plan.far_key[b] * (D + 1)];
+        rank_sum += std::max(rk[d], rk[d + h->opts.dtheta]);
+    }
+    r.far_rank_mean = plan.far_s.empty() ? 0.0 : rank_sum / plan.far_s.size();
+    const size_t sc = h->scalar;
+    r.near_bytes = (long)(h->near_elems * sc);
+    r.near_theta_bytes = (long)(h->near_theta_elems * 8);
+    r.far_bytes = (long)(h->far_elems * sc + h->far_theta_elems * 8 + h->st_elems * sc);
+    r.basis_bytes = (long)((size_t)plan.n * d * h->opts.p_s * sc + 2 * h->opts.p_s * h->opts.p_s * sc);
+    // one call moves every stored core the online stage reads once, plus H_k and w_b written and read
+    double alg = (double)r.near_bytes + r.near_theta_bytes + (double)h->far_theta_elems * 8 +
+                 2.0 * (double)(h->H_elems + h->w_elems) * sc;
+    if (h->opts.fmt == PH_FMT_H2 && !plan.far_s.empty())
+        alg += (double)h->far_elems * sc + (double)r.basis_bytes;
+    if (h->opts.fmt == PH_FMT_H) alg += (double)h->st_elems * sc;
+    r.alg_bytes_per_call = alg;
+    // flops per right-hand side
+    double fl = 2.0 * (double)r.near_entries;  // D_b x
+    for (size_t b = 0; b < plan.near_s.size(); ++b)
+        fl += 2.0 * h->nb_rank[b] * (double)plan.nodes[plan.near_s[b]].size() * plan.nodes[plan.near_t[b]].size() /
+              16.0;  // forming d_ij, shared by 16 right-hand sides in a chunk
+    const int p = h->opts.p_s, PD = h->PD;
+    for (size_t b = 0; b < plan.far_s.size(); ++b) {
+        const int* rk = &h->key_ranks[(size_t)plan.far_key[b] * (D + 1)];
+        if (h->opts.fmt == PH_FMT_H) {
+            fl += 2.0 * (plan.nodes[plan.far_s[b]].size() * (double)rk[d] +
+                         plan.nodes[plan.far_t[b]].size() * (double)rk[d + 1] + (double)rk[d] * rk[d + 1]);
+        } else {
+            double a = PD / p, chain = 0;
+            for (int i = 0; i < d; ++i) {  // right cores
+                int core = D - 1 - i;
+                chain += 2.0 * a * rk[core] * p * rk[core + 1];
+                a /= p;
+            }
+            chain += 2.0 * rk[d] * rk[d + 1];
+            double bsz = 1;
+            for (int i = 0; i < d; ++i) {  // left cores
+                int core = d - 1 - i;
+                chain += 2.0 * rk[core] * p * rk[core + 1] * bsz;
+                bsz *= p;
+            }
+            fl += chain;
+        }
+    }
+    if (h->opts.fmt == PH_FMT_H2 && !plan.far_s.empty()) {
+        fl += 2.0 * 2.0 * (double)plan.n * PD;                                           // leaf up / down
+        fl += 2.0 * 2.0 * (double)plan.nodes.size() * d * (double)PD * p;                  // transfers
+    }
+    r.flops_per_rhs = fl;
+    r.offline_seconds = h->offline_seconds;
+    *info = r;
+    return PH_OK;
+}
+
+ph_status ph_profile_enable(ph_handle* h, int enable) {
+    if (!h) return fail(nullptr, PH_ERR_INVALID_ARG, "ph_profile_enable: NULL handle");
+    h->prof = enable != 0;
+    return PH_OK;
+}
+
+ph_status ph_profile_read(ph_handle* h, double* ms, long* launches) {
+    if (!h || !ms || !launches) return fail(h, PH_ERR_INVALID_ARG, "ph_profile_read: NULL argument");
+    return guarded(h, [&]() -> ph_status {
+        PH_CUDA(cudaSetDevice(h->device));
+        for (int k = 0; k < PH_PROF_KINDS; ++k) {
+            ms[k] = 0.0;
+            launches[k] = 0;
+        }
+        for (auto& r : h->prof_recs) {
+            PH_CUDA(cudaEventSynchronize(r.b));
+            float t = 0.f;
+            PH_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+            if (r.kind >= 0 && r.kind < PH_PROF_KINDS) {
+                ms[r.kind] += t;
+                launches[r.kind] += 1;
+            }
+            h->prof_pool.push_back(r.a);
+            h->prof_pool.push_back(r.b);
+        }
+        h->prof_recs.clear();
+        return PH_OK;
+    });
+}
+
+void ph_destroy(ph_handle* h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    for (auto& r : h->prof_recs) {
+        h->prof_pool.push_back(r.a);
+        h->prof_pool.push_back(r.b);
+    }
+    for (cudaEvent_t e : h->prof_pool) cudaEventDestroy(e);
+    ph::free_device(h);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,172 @@
+// The handle behind the opaque ph_handle pointer, and the device views the
+// online kernels receive.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "ph_internal.h"
+
+// Device pointers of the online stage for compute type T (float or double).
+// Passed by value to kernels.
+template <typename T>
+struct DevView {
+    // geometry / tree
+    int n, d, p_s, PD;          // PD = p_s^d
+    int n_leaves, n_nodes;
+    const int* perm;            // cluster position -> original index
+    const int* node_begin;      // per node
+    const int* node_end;
+    const int* node_halves;
+    const int* node_children;   // CSR over nodes
+    const int* node_child_off;
+    const int* leaf_node;       // leaf -> node id
+    const int* node_leaf;       // node -> leaf index or -1
+    // theta
+    int dtheta;
+    int p_theta[3];
+    const double* theta_nodes;  // dtheta x 32
+    const double* theta_bw;     // barycentric weights, dtheta x 32
+    double* v64;                // instantiated parametric vectors, dtheta x 32
+    // near field
+    int n_near;
+    const int* near_by_leaf;    // CSR over leaves
+    const int* nb_t;            // source node of each near block
+    const int* nb_rank;
+    const long long* nb_off;    // element offset of G_{b,1} (r slabs of n_s x n_t) in near_cores
+    const long long* nb_toff;   // offset of the theta cores in near_theta (FP64)
+    const int* nb_woff;         // offset of w_b in w
+    const T* near_cores;
+    const double* near_theta;
+    T* w;                       // instantiated near weights
+    // far field
+    int n_keys, Delta;
+    const int* key_ranks;       // (Delta + 1) per key
+    const long long* key_off;   // Delta per key: element offset of each core (spatial cores in far_cores,
+                                // theta cores in far_theta)
+    const long long* key_hoff;  // offset of H_k in H
+    const T* far_cores;
+    const double* far_theta;
+    T* H;
+    int n_far;
+    const int* fb_t;            // source node per far block
+    const int* fb_key;
+    int n_far_targets;
+    const int* far_targets;     // target node ids
+    const int* far_by_target;   // CSR over far_targets
+    // H format
+    const long long* fb_soff;   // S_b offset in st
+    const long long* fb_toff;   // T_b offset in st
+    const T* st;
+    const int* node_level;
+    int n_far_levels;
+    const int* level_slot;      // level -> slot in yfar, -1 if no far targets on that level
+    // bases
+    const T* U;                 // n x d x p_s (cluster order)
+    const T* E;                 // 2 x p_s x p_s: E_lo then E_hi, [j * p_s + i] = ell_i^{parent}(eta_j^{child})
+    // workspace
+    int mcap;
+    T* Xc;                      // n x mcap, cluster order, row-major
+    T* Ynear;                   // n x mcap
+    T* yfar;                    // n_far_levels x n x mcap (H format)
+    T* xhat;                    // n_nodes x PD x mcap
+    T* yhat;
+    int* flags;                 // [0]: non-finite input count
+};
+
+struct DeviceBuffer {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+struct ph_handle {
+    // configuration
+    ph_kernel kernel = PH_KERNEL_GAUSS;
+    ph_build_opts opts{};
+    int device = 0;
+    int PD = 0, Delta = 0, p_theta_total = 1;
+    size_t scalar = 8;  // sizeof compute type
+    ph::Plan plan;
+    double offline_seconds = 0;
+    std::string last_error;
+    // host copies of everything stored (for ph_save and ph_get_info)
+    std::vector<int> nb_rank;
+    std::vector<long long> nb_off, nb_toff;
+    std::vector<int> nb_woff;
+    std::vector<int> key_ranks;
+    std::vector<long long> key_off, key_hoff;
+    std::vector<long long> fb_soff, fb_toff;
+    long long near_elems = 0, near_theta_elems = 0, far_elems = 0, far_theta_elems = 0, H_elems = 0,
+              st_elems = 0, w_elems = 0;
+    std::vector<double> theta_nodes, theta_bw;  // dtheta x 32
+    std::vector<double> E64;                    // 2 x p_s x p_s
+    // device data
+    std::vector<DeviceBuffer> buffers;          // every device allocation, freed in ph_destroy
+    void* d_near = nullptr;
+    double* d_near_theta = nullptr;
+    void* d_far = nullptr;
+    double* d_far_theta = nullptr;
+    void* d_st = nullptr;
+    void* d_U = nullptr;
+    void* d_E = nullptr;
+    void* d_w = nullptr;
+    void* d_H = nullptr;
+    double* d_v64 = nullptr;
+    int* d_flags = nullptr;
+    int* d_int = nullptr;                       // packed integer index arrays
+    long long* d_ll = nullptr;                  // packed 64-bit offset arrays
+    double* d_dbl = nullptr;                    // theta nodes / weights
+    // workspace, sized for mcap right-hand sides
+    int mcap = 0;
+    void* d_Xc = nullptr;
+    void* d_Ynear = nullptr;
+    void* d_yfar = nullptr;
+    void* d_xhat = nullptr;
+    void* d_yhat = nullptr;
+    DeviceBuffer ws;
+    DeviceBuffer host_stage_x, host_stage_y;    // device staging for ph_matvec_host
+    int n_far_levels = 0;
+    std::vector<int> level_slot;
+    std::vector<std::vector<int>> level_nodes;  // nodes per level (for the sweeps)
+    int* d_level_nodes = nullptr;
+    std::vector<int> level_nodes_off;
+    int min_far_level = 0;
+    // streams
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    bool instantiated = false;
+    // per-kernel timing (ph_profile_enable / ph_profile_read)
+    bool prof = false;
+    std::vector<cudaEvent_t> prof_pool;
+    struct ProfRec { int kind; cudaEvent_t a, b; };
+    std::vector<ProfRec> prof_recs;
+    // index views (into d_int / d_ll)
+    std::vector<long> view_io, view_lo;
+    DevView<float> vf{};
+    DevView<double> vd{};
+};
+
+namespace ph {
+// offline.cu
+ph_status offline_build(ph_handle* h, const double* points, long n);
+// online.cu
+ph_status online_instantiate(ph_handle* h, const double* theta, cudaStream_t stream);
+ph_status online_matvec(ph_handle* h, const void* X, long ldx, int m, void* Y, long ldy,
+                        cudaStream_t stream);
+void ensure_workspace(ph_handle* h, int m);
+void refresh_views(ph_handle* h);
+void free_device(ph_handle* h);
+void* dev_alloc(ph_handle* h, size_t bytes);  // throws ph::Error(PH_ERR_OOM) on failure
+void dev_free(ph_handle* h, void* p);
+// Event pair around one launch when profiling is on (no-op otherwise).
+struct ProfScope {
+    ph_handle* h;
+    int kind;
+    cudaStream_t s;
+    cudaEvent_t b = nullptr;
+    ProfScope(ph_handle* h_, int kind_, cudaStream_t s_);
+    ~ProfScope();
+};
+}  // namespace ph

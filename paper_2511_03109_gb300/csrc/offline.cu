@@ -1,0 +1,737 @@
+// Offline stage of the parametric H / H^2 matrix (Algs. "Offline Stage: Parametric
+// H-matrix" and "... H^2-matrix", §4.4), in FP64 on the GPU.
+//
+//  * near field (§4.3): A_b[(i,j), k] = kappa(x_{s,i}, x_{t,j}; eta_k) is never stored.
+//    One kernel reduces A_b to its triangular factor R_b by Householder QR over
+//    row chunks generated on the fly (R <- qr([R; A_chunk])), cuSOLVER's batched
+//    Jacobi SVD gives R_b = U S V^T for all blocks at once, and a second kernel
+//    re-evaluates A_b and writes G_{b,1} = A_b V_r (r slabs of n_s x n_t, i
+//    fastest) with G_{b,2} = V_r^T: the truncated SVD of TT-SVD's single cut for
+//    d_theta = 1, in the gauge U_r S_r / V_r^T.
+//  * far field (§4.2, App. A.4): M_b on the Chebyshev grids, compressed by
+//    TT-SVD (Oseledets 2011, Alg. 1); each cut is a QR of the tall side of the
+//    unfolding (cuSOLVER geqrf) followed by an SVD of its square factor
+//    (cuSOLVER gesvd), so singular values carry absolute error eps ||A|| and the
+//    truncation matches a dense SVD; one tensor per translation class
+//    (level, offset) when the kernel is translation-invariant (§5.2).
+//  * H format: S_b = U_s L_b and T_b = U_t R_b by the recurrences of Phase 3 of
+//    the PTTK offline algorithm (App. A.4), on the host in FP64.
+//  * H^2 format: leaf factor matrices U_{s,k} (§3.3) and the two transfer
+//    factors of a midpoint split (§3.6.1).
+#include <cublas_v2.h>
+#include <cusolverDn.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "handle.h"
+
+namespace ph {
+
+namespace {
+
+#define PH_BLAS(call)                                                                         \
+    do {                                                                                      \
+        cublasStatus_t st_ = (call);                                                          \
+        if (st_ != CUBLAS_STATUS_SUCCESS)                                                     \
+            throw Error(PH_ERR_CUDA, std::string("cuBLAS: ") + #call + " status " +          \
+                                         std::to_string((int)st_));                           \
+    } while (0)
+#define PH_SOLVER(call)                                                                       \
+    do {                                                                                      \
+        cusolverStatus_t st_ = (call);                                                        \
+        if (st_ != CUSOLVER_STATUS_SUCCESS)                                                   \
+            throw Error(PH_ERR_CUDA, std::string("cuSOLVER: ") + #call + " status " +        \
+                                         std::to_string((int)st_));                           \
+    } while (0)
+
+constexpr double kTieRel = 1e-9;
+
+// kappa(x, y; theta) in FP64 for the kernels of include/ph.h.
+__device__ __forceinline__ double kappa64(int kernel, const double* x, const double* y,
+                                          const double* th, int d) {
+    double r2 = 0.0;
+    for (int k = 0; k < d; ++k) {
+        double df = x[k] - y[k];
+        r2 += df * df;
+    }
+    const double l = th[0];
+    switch (kernel) {
+        case PH_KERNEL_GAUSS: return exp(-r2 / (2.0 * l * l));
+        case PH_KERNEL_MATERN32: {
+            double s = sqrt(3.0) * sqrt(r2) / l;
+            return (1.0 + s) * exp(-s);
+        }
+        case PH_KERNEL_MATERN52: {
+            double s = sqrt(5.0) * sqrt(r2) / l;
+            return (1.0 + s + s * s / 3.0) * exp(-s);
+        }
+        case PH_KERNEL_ANISO_GAUSS: {
+            double q = 0.0;
+            for (int k = 0; k < d; ++k) {
+                double df = x[k] - y[k];
+                q += df * df / (2.0 * th[k] * th[k]);
+            }
+            return exp(-q);
+        }
+        case PH_KERNEL_SE: return exp(-r2 / (l * l));
+        case PH_KERNEL_EXPONENTIAL: return exp(-sqrt(r2) / l);
+        case PH_KERNEL_MULTIQUADRIC: return sqrt(1.0 + r2 / (l * l));
+        case PH_KERNEL_POLY: return 1.0 + l * r2 + l * l * r2 * r2;
+        case PH_KERNEL_POLYXY: {
+            double dot = 0.0;
+            for (int k = 0; k < d; ++k) dot += x[k] * y[k];
+            return (1.0 + dot) * (1.0 + dot) * (1.0 + l);
+        }
+    }
+    return 0.0;
+}
+
+struct NearBuild {
+    int kernel, d, P, dt;
+    const double* pts;       // cluster order, n x d
+    const int* s_begin;      // per near block
+    const int* s_n;
+    const int* t_begin;
+    const int* t_n;
+    const double* grid;      // P x dt theta grid points (k fastest over dimension 1)
+};
+
+constexpr int kChunk = 256;
+
+// Fills A[row][k] for rows q0 .. q0 + kChunk - 1 of block b into shared memory.
+__device__ void eval_near_chunk(const NearBuild& a, int b, long long q0, long long nq, double* A) {
+    const int ns = a.s_n[b];
+    const int sb = a.s_begin[b], tb = a.t_begin[b];
+    for (int row = threadIdx.x; row < kChunk; row += blockDim.x) {
+        long long q = q0 + row;
+        if (q < nq) {
+            int i = (int)(q % ns), j = (int)(q / ns);  // (i, j) little-endian, i fastest (§4.3)
+            double x[kMaxDim], y[kMaxDim];
+            for (int k = 0; k < a.d; ++k) {
+                x[k] = a.pts[(long long)(sb + i) * a.d + k];
+                y[k] = a.pts[(long long)(tb + j) * a.d + k];
+            }
+            for (int k = 0; k < a.P; ++k) A[row * a.P + k] = kappa64(a.kernel, x, y, a.grid + k * a.dt, a.d);
+        } else {
+            for (int k = 0; k < a.P; ++k) A[row * a.P + k] = 0.0;
+        }
+    }
+}
+
+// Triangular factor R_b (P x P, column-major, upper) of every near block A_b, one CTA per block:
+// the rows of A_b are generated in chunks and folded in by Householder QR of the stacked
+// matrix [R; A_chunk] (LAPACK dlarfg convention).  Only R is kept: the right singular
+// vectors and singular values of A_b are those of R_b.
+__global__ void near_tsqr_kernel(NearBuild a, double* Rout) {
+    extern __shared__ double sm[];
+    const int P = a.P, LD = P + kChunk;
+    double* W = sm;                 // LD x P, column-major: rows 0..P-1 hold R, rows P.. the chunk
+    double* A = sm + (size_t)LD * P; // kChunk x P row-major scratch for the evaluation
+    const int b = blockIdx.x;
+    const long long nq = (long long)a.s_n[b] * a.t_n[b];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nwarps = blockDim.x / 32;
+    for (int e = threadIdx.x; e < P * P; e += blockDim.x) W[(e % P) + LD * (e / P)] = 0.0;
+    for (long long q0 = 0; q0 < nq; q0 += kChunk) {
+        __syncthreads();
+        eval_near_chunk(a, b, q0, nq, A);
+        __syncthreads();
+        for (int e = threadIdx.x; e < kChunk * P; e += blockDim.x) {
+            const int row = e / P, k = e % P;
+            W[P + row + LD * k] = A[e];
+        }
+        __syncthreads();
+        for (int k = 0; k < P; ++k) {
+            // every warp recomputes the reflector of column k (column k is read-only in this step)
+            double x2 = 0.0;
+            for (int row = lane; row < kChunk; row += 32) {
+                double x = W[P + row + LD * k];
+                x2 += x * x;
+            }
+            for (int o = 16; o > 0; o >>= 1) x2 += __shfl_xor_sync(0xffffffffu, x2, o);
+            const double alpha = W[k + LD * k];
+            if (x2 > 0.0) {
+                const double beta = -copysign(sqrt(alpha * alpha + x2), alpha);
+                const double tau = (beta - alpha) / beta;
+                const double scale = 1.0 / (alpha - beta);
+                for (int j = k + 1 + warp; j < P; j += nwarps) {
+                    double w = 0.0;
+                    for (int row = lane; row < kChunk; row += 32) w += W[P + row + LD * k] * scale * W[P + row + LD * j];
+                    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+                    w += W[k + LD * j];
+                    const double tw = tau * w;
+                    for (int row = lane; row < kChunk; row += 32)
+                        W[P + row + LD * j] -= tw * W[P + row + LD * k] * scale;
+                    if (lane == 0) W[k + LD * j] -= tw;
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) W[k + LD * k] = beta;
+            }
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
+        const int r = e % P, c = e / P;
+        Rout[(long long)b * P * P + e] = (r <= c) ? W[r + LD * c] : 0.0;
+    }
+}
+
+// G_{b,1} = A_b V_r written as r slabs of n_s x n_t (i fastest) in compute type T.
+template <typename T>
+__global__ void near_project_kernel(NearBuild a, const double* vecs, const int* rank,
+                                    const long long* off, T* out) {
+    extern __shared__ double sA[];
+    double* sV = sA + kChunk * a.P;  // P x r_b, column-major
+    const int b = blockIdx.x;
+    const int r = rank[b];
+    const long long nq = (long long)a.s_n[b] * a.t_n[b];
+    const double* V = vecs + (long long)b * a.P * a.P;  // first r columns: largest singular values
+    for (int e = threadIdx.x; e < a.P * r; e += blockDim.x) sV[e] = V[e];
+    T* G = out + off[b];
+    for (long long q0 = 0; q0 < nq; q0 += kChunk) {
+        __syncthreads();
+        eval_near_chunk(a, b, q0, nq, sA);
+        __syncthreads();
+        for (int e = threadIdx.x; e < kChunk * r; e += blockDim.x) {
+            int row = e % kChunk, c = e / kChunk;
+            long long q = q0 + row;
+            if (q < nq) {
+                double s = 0.0;
+                for (int k = 0; k < a.P; ++k) s += sA[row * a.P + k] * sV[c * a.P + k];
+                G[(long long)c * nq + q] = (T)s;
+            }
+        }
+    }
+}
+
+// M_b on the Chebyshev grids, modes (i_1..i_d, k_1..k_dt, j_1..j_d), little-endian (App. A.4).
+__global__ void far_tensor_kernel(int kernel, int d, int dt, int ps, const int* pt, long long PD,
+                                  long long PT, const double* sx, const double* tx,
+                                  const double* tn, double* M) {
+    const long long total = PD * PT * PD;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        long long i = idx % PD, rest = idx / PD;
+        long long kk = rest % PT, j = rest / PT;
+        double x[kMaxDim], y[kMaxDim], th[kMaxDim];
+        for (int q = 0; q < d; ++q) {
+            x[q] = sx[q * ps + (int)(i % ps)];
+            y[q] = tx[q * ps + (int)(j % ps)];
+            i /= ps;
+            j /= ps;
+        }
+        for (int q = 0; q < dt; ++q) {
+            th[q] = tn[q * kMaxPTheta + (int)(kk % pt[q])];
+            kk /= pt[q];
+        }
+        M[idx] = kappa64(kernel, x, y, th, d);
+    }
+}
+
+// Rank kept at a TT-SVD cut from the singular values s[0] >= s[1] >= ... >= s[n-1]:
+// the smallest r >= 1 whose discarded tail sum_{i>r} s_i^2 <= delta2, then the cap,
+// then numerically tied singular values (s_r - s_{r+1} <= 1e-9 s_1) are kept together.
+int choose_rank_sv(const double* s, int n, double delta2, int cap) {
+    std::vector<double> tail(n + 1, 0.0);
+    for (int i = n - 1; i >= 0; --i) tail[i] = tail[i + 1] + s[i] * s[i];
+    int lim = (cap > 0) ? std::min(n, cap) : n;
+    int r = n;
+    for (int k = 1; k <= n; ++k)
+        if (tail[k] <= delta2) {
+            r = k;
+            break;
+        }
+    r = std::max(1, std::min(r, lim));
+    if (n > 0 && s[0] > 0)
+        while (r < lim && s[r - 1] - s[r] <= kTieRel * s[0]) ++r;
+    return r;
+}
+
+// Copies the upper triangle of the first n rows of T (ld m) into R (n x n), zeros below.
+__global__ void copy_upper_kernel(const double* T, long long m, int n, double* R) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) {
+        const int r = e % n, c = e / n;
+        R[e] = (r <= c) ? T[r + m * c] : 0.0;
+    }
+}
+
+// TT-SVD on the device.  Each cut factors the tall side of the unfolding by Householder QR
+// and takes the SVD of the square factor, so the singular values and the kept subspace have
+// the accuracy of a dense SVD (absolute error ~ eps ||A||).
+struct TTEngine {
+    cublasHandle_t blas = nullptr;
+    cusolverDnHandle_t solver = nullptr;
+    double *C = nullptr, *Cn = nullptr, *T = nullptr, *tau = nullptr, *R = nullptr, *VT = nullptr, *V = nullptr, *Uw = nullptr,
+           *S = nullptr, *work = nullptr, *rwork = nullptr;
+    int* info = nullptr;
+    size_t capT = 0, capN = 0, capWork = 0;
+    ph_handle* h = nullptr;
+
+    void reserve(size_t total, size_t maxn) {
+        if (total > capT) {
+            C = (double*)dev_alloc(h, total * sizeof(double));
+            Cn = (double*)dev_alloc(h, total * sizeof(double));
+            T = (double*)dev_alloc(h, total * sizeof(double));
+            capT = total;
+        }
+        if (maxn > capN) {
+            R = (double*)dev_alloc(h, maxn * maxn * sizeof(double));
+            VT = (double*)dev_alloc(h, maxn * maxn * sizeof(double));
+            V = (double*)dev_alloc(h, maxn * maxn * sizeof(double));
+            Uw = (double*)dev_alloc(h, maxn * maxn * sizeof(double));
+            S = (double*)dev_alloc(h, maxn * sizeof(double));
+            tau = (double*)dev_alloc(h, maxn * sizeof(double));
+            rwork = (double*)dev_alloc(h, maxn * sizeof(double));
+            capN = maxn;
+        }
+        if (!info) info = (int*)dev_alloc(h, sizeof(int));
+    }
+
+    void need_work(int lwork) {
+        if ((size_t)lwork > capWork) {
+            work = (double*)dev_alloc(h, (size_t)lwork * sizeof(double));
+            capWork = lwork;
+        }
+    }
+
+    void check_info(const char* what) {
+        int hinfo = 0;
+        PH_CUDA(cudaMemcpy(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost));
+        if (hinfo != 0) throw Error(PH_ERR_CUDA, std::string(what) + " failed, info = " + std::to_string(hinfo));
+    }
+
+    // T (m x n, m >= n, destroyed) = Q R;  R = U_R S V_R^T.  Leaves V_R (n x n) in V and returns S.
+    void qr_svd(long long m, int n, std::vector<double>& s) {
+        int lwork = 0;
+        PH_SOLVER(cusolverDnDgeqrf_bufferSize(solver, (int)m, n, T, (int)m, &lwork));
+        need_work(lwork);
+        PH_SOLVER(cusolverDnDgeqrf(solver, (int)m, n, T, (int)m, tau, work, lwork, info));
+        check_info("geqrf");
+        copy_upper_kernel<<<(n * n + 255) / 256, 256>>>(T, m, n, R);
+        PH_LAUNCH("copy_upper_kernel");
+        PH_SOLVER(cusolverDnDgesvd_bufferSize(solver, n, n, &lwork));
+        need_work(lwork);
+        PH_SOLVER(cusolverDnDgesvd(solver, 'N', 'A', n, n, R, n, S, Uw, n, VT, n, work, lwork, rwork, info));
+        check_info("gesvd");
+        const double one = 1.0, zero = 0.0;
+        PH_BLAS(cublasDgeam(blas, CUBLAS_OP_T, CUBLAS_OP_N, n, n, &one, VT, n, &zero, V, n, V, n));
+        s.resize(n);
+        PH_CUDA(cudaMemcpy(s.data(), S, n * sizeof(double), cudaMemcpyDeviceToHost));
+    }
+
+    // TT-SVD of the tensor already in C (Fortran order, dims).  Returns host cores
+    // (core k is r_k x dims[k] x r_{k+1}, Fortran) and the ranks r_0..r_q.
+    void run(const std::vector<int>& dims, double eps, int cap, std::vector<std::vector<double>>& cores,
+             std::vector<int>& ranks) {
+        const int q = (int)dims.size();
+        long long size = 1;
+        for (int v : dims) size *= v;
+        double nrm = 0.0;
+        PH_BLAS(cublasDnrm2(blas, (int)size, C, 1, &nrm));
+        const double delta2 = eps * eps * nrm * nrm / std::max(1, q - 1);
+        cores.assign(q, {});
+        ranks.assign(q + 1, 1);
+        int rp = 1;
+        std::vector<double> s;
+        const double one = 1.0, zero = 0.0;
+        for (int k = 0; k < q - 1; ++k) {
+            const long long rows = (long long)rp * dims[k];
+            const long long cols = size / rows;
+            int r;
+            if (rows <= cols) {
+                // C^T = Q R, so C = R^T Q^T and the left singular vectors of C are V_R
+                PH_BLAS(cublasDgeam(blas, CUBLAS_OP_T, CUBLAS_OP_N, (int)cols, (int)rows, &one, C, (int)rows, &zero,
+                                    T, (int)cols, T, (int)cols));
+                qr_svd(cols, (int)rows, s);
+                r = choose_rank_sv(s.data(), (int)rows, delta2, cap);
+                cores[k].resize(rows * r);
+                PH_CUDA(cudaMemcpy(cores[k].data(), V, rows * r * sizeof(double), cudaMemcpyDeviceToHost));
+                PH_BLAS(cublasDgemm(blas, CUBLAS_OP_T, CUBLAS_OP_N, r, (int)cols, (int)rows, &one, V, (int)rows, C,
+                                    (int)rows, &zero, Cn, r));
+            } else {
+                // C = Q R = (Q U_R) S V_R^T: core = C V_r S_r^{-1}, remainder S_r V_r^T
+                PH_CUDA(cudaMemcpy(T, C, size * sizeof(double), cudaMemcpyDeviceToDevice));
+                qr_svd(rows, (int)cols, s);
+                r = choose_rank_sv(s.data(), (int)cols, delta2, cap);
+                PH_BLAS(cublasDgemm(blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)rows, r, (int)cols, &one, C, (int)rows, V,
+                                    (int)cols, &zero, T, (int)rows));
+                std::vector<double> Vh(cols * r);
+                PH_CUDA(cudaMemcpy(Vh.data(), V, cols * r * sizeof(double), cudaMemcpyDeviceToHost));
+                cores[k].resize(rows * r);
+                PH_CUDA(cudaMemcpy(cores[k].data(), T, rows * r * sizeof(double), cudaMemcpyDeviceToHost));
+                std::vector<double> next(r * cols);
+                for (int c = 0; c < r; ++c) {
+                    const double inv = s[c] > 0 ? 1.0 / s[c] : 0.0;
+                    for (long long row = 0; row < rows; ++row) cores[k][c * rows + row] *= inv;
+                    for (long long col = 0; col < cols; ++col) next[c + r * col] = s[c] * Vh[c * cols + col];
+                }
+                PH_CUDA(cudaMemcpy(Cn, next.data(), next.size() * sizeof(double), cudaMemcpyHostToDevice));
+            }
+            std::swap(C, Cn);
+            size = (long long)r * cols;
+            rp = r;
+            ranks[k + 1] = r;
+        }
+        cores[q - 1].resize(size);
+        PH_CUDA(cudaMemcpy(cores[q - 1].data(), C, size * sizeof(double), cudaMemcpyDeviceToHost));
+    }
+};
+
+template <typename T>
+T* upload_as(ph_handle* h, const std::vector<double>& v) {
+    std::vector<T> tmp(v.begin(), v.end());
+    T* p = (T*)dev_alloc(h, std::max<size_t>(1, tmp.size()) * sizeof(T));
+    if (!tmp.empty()) PH_CUDA(cudaMemcpy(p, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return p;
+}
+
+template <typename V>
+V* upload_vec(ph_handle* h, const std::vector<V>& v) {
+    V* p = (V*)dev_alloc(h, std::max<size_t>(1, v.size()) * sizeof(V));
+    if (!v.empty()) PH_CUDA(cudaMemcpy(p, v.data(), v.size() * sizeof(V), cudaMemcpyHostToDevice));
+    return p;
+}
+
+}  // namespace
+
+void* dev_alloc(ph_handle* h, size_t bytes) {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(bytes, 16));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Error(PH_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " +
+                                    cudaGetErrorString(e));
+    }
+    h->buffers.push_back({p, bytes});
+    return p;
+}
+
+void free_device(ph_handle* h) {
+    for (auto& b : h->buffers)
+        if (b.ptr) cudaFree(b.ptr);
+    h->buffers.clear();
+    if (h->side) cudaStreamDestroy(h->side);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    h->side = nullptr;
+    h->ev_fork = h->ev_join = nullptr;
+}
+
+ph_status offline_build(ph_handle* h, const double* points, long n) {
+    auto t0 = std::chrono::steady_clock::now();
+    const ph_build_opts& o = h->opts;
+    const int d = o.d, dt = o.dtheta, ps = o.p_s;
+    Plan& plan = h->plan;
+    const bool dedup = o.dedup && kernel_translation_invariant(h->kernel);
+    build_plan(points, n, d, o.l_max, o.eta, dedup, plan);
+
+    PH_CUDA(cudaSetDevice(h->device));
+    PH_CUDA(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+    PH_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    PH_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+
+    h->scalar = (o.prec == PH_FP32) ? 4 : 8;
+    h->PD = 1;
+    for (int k = 0; k < d; ++k) h->PD *= ps;
+    h->Delta = 2 * d + dt;
+    int pt[kMaxDim] = {1, 1, 1};
+    h->p_theta_total = 1;
+    for (int k = 0; k < dt; ++k) {
+        pt[k] = o.degree[k] + 1;
+        h->p_theta_total *= pt[k];
+    }
+    if (dt != 1) throw Error(PH_ERR_UNSUPPORTED, "near-field compression implemented for d_theta = 1");
+    const int P = h->p_theta_total;
+    if (P > kMaxPTheta) throw Error(PH_ERR_UNSUPPORTED, "p_theta must be at most 32");
+    if (ps < 1 || ps > kMaxPs) throw Error(PH_ERR_INVALID_ARG, "p_s must be 1..16");
+
+    // theta nodes and barycentric weights (dtheta x 32)
+    h->theta_nodes.assign(kMaxDim * kMaxPTheta, 0.0);
+    h->theta_bw.assign(kMaxDim * kMaxPTheta, 0.0);
+    for (int k = 0; k < dt; ++k) {
+        cheb_nodes(o.theta_lo[k], o.theta_hi[k], pt[k], &h->theta_nodes[k * kMaxPTheta]);
+        bary_weights(&h->theta_nodes[k * kMaxPTheta], pt[k], &h->theta_bw[k * kMaxPTheta]);
+    }
+    std::vector<double> grid(P * dt);  // theta grid points, k_1 fastest
+    for (int idx = 0; idx < P; ++idx) {
+        int rest = idx;
+        for (int k = 0; k < dt; ++k) {
+            grid[idx * dt + k] = h->theta_nodes[k * kMaxPTheta + rest % pt[k]];
+            rest /= pt[k];
+        }
+    }
+
+    // points in cluster order
+    std::vector<double> pts(n * d);
+    for (long i = 0; i < n; ++i)
+        for (int k = 0; k < d; ++k) pts[i * d + k] = points[(long)plan.perm[i] * d + k];
+    double* d_pts = upload_vec(h, pts);
+    double* d_grid = upload_vec(h, grid);
+
+    // ------------------------------------------------------------------ near field
+    const int nn = (int)plan.near_s.size();
+    std::vector<int> sb(nn), sn(nn), tb(nn), tn(nn);
+    for (int b = 0; b < nn; ++b) {
+        const Node& s = plan.nodes[plan.near_s[b]];
+        const Node& t = plan.nodes[plan.near_t[b]];
+        sb[b] = s.begin; sn[b] = s.size(); tb[b] = t.begin; tn[b] = t.size();
+    }
+    NearBuild nbld{(int)h->kernel, d, P, dt, d_pts, upload_vec(h, sb), upload_vec(h, sn), upload_vec(h, tb),
+                   upload_vec(h, tn), d_grid};
+    h->nb_rank.assign(nn, 0);
+    h->nb_off.assign(nn, 0);
+    h->nb_toff.assign(nn, 0);
+    h->nb_woff.assign(nn + 1, 0);
+    std::vector<double> near_theta;
+    if (nn > 0) {
+        double* d_R = (double*)dev_alloc(h, (size_t)nn * P * P * sizeof(double));
+        double* d_S = (double*)dev_alloc(h, (size_t)nn * P * sizeof(double));
+        double* d_U = (double*)dev_alloc(h, (size_t)nn * P * P * sizeof(double));
+        double* d_V = (double*)dev_alloc(h, (size_t)nn * P * P * sizeof(double));
+        size_t smem = ((size_t)(P + kChunk) * P + (size_t)kChunk * P) * sizeof(double);
+        PH_CUDA(cudaFuncSetAttribute(near_tsqr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        near_tsqr_kernel<<<nn, 256, smem>>>(nbld, d_R);
+        PH_LAUNCH("near_tsqr_kernel");
+        // batched Jacobi SVD of all P x P factors: R_b = U S V^T, S descending
+        cusolverDnHandle_t sol;
+        PH_SOLVER(cusolverDnCreate(&sol));
+        gesvdjInfo_t params;
+        PH_SOLVER(cusolverDnCreateGesvdjInfo(&params));
+        PH_SOLVER(cusolverDnXgesvdjSetTolerance(params, 1e-15));
+        PH_SOLVER(cusolverDnXgesvdjSetMaxSweeps(params, 100));
+        PH_SOLVER(cusolverDnXgesvdjSetSortEig(params, 1));
+        int lwork = 0;
+        PH_SOLVER(cusolverDnDgesvdjBatched_bufferSize(sol, CUSOLVER_EIG_MODE_VECTOR, P, P, d_R, P, d_S, d_U, P,
+                                                      d_V, P, &lwork, params, nn));
+        double* d_work = (double*)dev_alloc(h, (size_t)std::max(lwork, 1) * sizeof(double));
+        int* d_info = (int*)dev_alloc(h, (size_t)nn * sizeof(int));
+        PH_SOLVER(cusolverDnDgesvdjBatched(sol, CUSOLVER_EIG_MODE_VECTOR, P, P, d_R, P, d_S, d_U, P, d_V, P,
+                                           d_work, lwork, d_info, params, nn));
+        std::vector<int> infos(nn);
+        PH_CUDA(cudaMemcpy(infos.data(), d_info, nn * sizeof(int), cudaMemcpyDeviceToHost));
+        cusolverDnDestroyGesvdjInfo(params);
+        cusolverDnDestroy(sol);
+        for (int b = 0; b < nn; ++b)
+            if (infos[b] != 0) throw Error(PH_ERR_CUDA, "batched Jacobi SVD did not converge");
+        std::vector<double> sv((size_t)nn * P), vecs((size_t)nn * P * P);
+        PH_CUDA(cudaMemcpy(sv.data(), d_S, sv.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        PH_CUDA(cudaMemcpy(vecs.data(), d_V, vecs.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        const double ntol = (o.near_tol >= 0) ? o.near_tol : o.tol;
+        long long off = 0, toff = 0;
+        for (int b = 0; b < nn; ++b) {
+            const double* s = &sv[(size_t)b * P];
+            double fro2 = 0.0;
+            for (int k = 0; k < P; ++k) fro2 += s[k] * s[k];
+            int r = choose_rank_sv(s, P, ntol * ntol * fro2 / dt, kMaxNearRank);
+            h->nb_rank[b] = r;
+            h->nb_off[b] = off;
+            h->nb_toff[b] = toff;
+            h->nb_woff[b + 1] = h->nb_woff[b] + r;
+            off += (long long)sn[b] * tn[b] * r;
+            toff += (long long)r * P;
+            // G_{b,2} = V_r^T, an r x P x 1 core (Fortran): [c + r t] = V[t, c]
+            const double* V = &vecs[(size_t)b * P * P];
+            near_theta.resize(near_theta.size() + (size_t)r * P, 0.0);
+            double* dst = &near_theta[toff - (long long)r * P];
+            for (int t = 0; t < P; ++t)
+                for (int c = 0; c < r; ++c) dst[c + r * t] = V[(size_t)c * P + t];
+        }
+        h->near_elems = off;
+        h->near_theta_elems = toff;
+        h->w_elems = h->nb_woff[nn];
+        int* d_rank = upload_vec(h, h->nb_rank);
+        long long* d_off = upload_vec(h, h->nb_off);
+        h->d_near = dev_alloc(h, (size_t)off * h->scalar);
+        size_t smem2 = ((size_t)kChunk * P + (size_t)P * P) * sizeof(double);
+        if (o.prec == PH_FP32) {
+            PH_CUDA(cudaFuncSetAttribute(near_project_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem2));
+            near_project_kernel<float><<<nn, 256, smem2>>>(nbld, d_V, d_rank, d_off, (float*)h->d_near);
+        } else {
+            PH_CUDA(cudaFuncSetAttribute(near_project_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem2));
+            near_project_kernel<double><<<nn, 256, smem2>>>(nbld, d_V, d_rank, d_off, (double*)h->d_near);
+        }
+        PH_LAUNCH("near_project_kernel");
+        PH_CUDA(cudaDeviceSynchronize());
+    }
+    h->d_near_theta = upload_vec(h, near_theta);
+
+    // ------------------------------------------------------------------- far field
+    const int nkeys = (int)plan.key_rep.size();
+    const int Delta = h->Delta;
+    h->key_ranks.assign((size_t)nkeys * (Delta + 1), 0);
+    h->key_off.assign((size_t)nkeys * Delta, 0);
+    h->key_hoff.assign(nkeys, 0);
+    std::vector<std::vector<std::vector<double>>> key_cores(nkeys);
+    std::vector<double> far_sp, far_th;
+    long long hoff = 0;
+    if (nkeys > 0) {
+        TTEngine eng;
+        eng.h = h;
+        PH_BLAS(cublasCreate(&eng.blas));
+        PH_SOLVER(cusolverDnCreate(&eng.solver));
+        const long long PD = h->PD;
+        const long long total = PD * P * PD;
+        eng.reserve(total, (size_t)std::sqrt((double)total) + 2);
+        double* d_nodes = (double*)dev_alloc(h, 2 * kMaxDim * kMaxPs * sizeof(double));
+        double* d_tn = upload_vec(h, h->theta_nodes);
+        int* d_pt = upload_vec(h, std::vector<int>(pt, pt + kMaxDim));
+        std::vector<int> dims;
+        for (int k = 0; k < d; ++k) dims.push_back(ps);
+        for (int k = 0; k < dt; ++k) dims.push_back(pt[k]);
+        for (int k = 0; k < d; ++k) dims.push_back(ps);
+        for (int key = 0; key < nkeys; ++key) {
+            const int fb = plan.key_rep[key];
+            const Node& s = plan.nodes[plan.far_s[fb]];
+            const Node& t = plan.nodes[plan.far_t[fb]];
+            std::vector<double> nodes(2 * kMaxDim * kMaxPs, 0.0);
+            for (int k = 0; k < d; ++k) {
+                cheb_nodes(s.lo[k], s.hi[k], ps, &nodes[k * ps]);
+                cheb_nodes(t.lo[k], t.hi[k], ps, &nodes[kMaxDim * kMaxPs + k * ps]);
+            }
+            PH_CUDA(cudaMemcpy(d_nodes, nodes.data(), nodes.size() * sizeof(double), cudaMemcpyHostToDevice));
+            // the engine swaps its two buffers; the tensor is evaluated into the current one
+            far_tensor_kernel<<<1024, 256>>>((int)h->kernel, d, dt, ps, d_pt, PD, P, d_nodes,
+                                              d_nodes + kMaxDim * kMaxPs, d_tn, eng.C);
+            PH_LAUNCH("far_tensor_kernel");
+            std::vector<int> ranks;
+            eng.run(dims, o.tol, o.rank_cap, key_cores[key], ranks);
+            for (int k = 0; k <= Delta; ++k) h->key_ranks[(size_t)key * (Delta + 1) + k] = ranks[k];
+            for (int k = 0; k < Delta; ++k) {
+                auto& core = key_cores[key][k];
+                bool theta_core = (k >= d && k < d + dt);
+                auto& arena = theta_core ? far_th : far_sp;
+                h->key_off[(size_t)key * Delta + k] = (long long)arena.size();
+                arena.insert(arena.end(), core.begin(), core.end());
+            }
+            h->key_hoff[key] = hoff;
+            hoff += (long long)ranks[d] * ranks[d + dt];
+        }
+        cublasDestroy(eng.blas);
+        cusolverDnDestroy(eng.solver);
+    }
+    h->far_elems = (long long)far_sp.size();
+    h->far_theta_elems = (long long)far_th.size();
+    h->H_elems = hoff;
+    if (o.prec == PH_FP32) h->d_far = upload_as<float>(h, far_sp);
+    else h->d_far = upload_as<double>(h, far_sp);
+    h->d_far_theta = upload_vec(h, far_th);
+    h->d_H = dev_alloc(h, std::max<long long>(1, hoff) * h->scalar);
+    h->d_w = dev_alloc(h, std::max<long long>(1, h->w_elems) * h->scalar);
+
+    // ---------------------------------------------------- leaf bases and transfers
+    // U[(row * d + k) * p_s + j] = ell_j^{(B_leaf, k)}(x_row,k)   (§3.3)
+    std::vector<double> U((size_t)n * d * ps);
+    for (int leaf : plan.leaves) {
+        const Node& c = plan.nodes[leaf];
+        double nodes[kMaxPs], w[kMaxPs];
+        for (int k = 0; k < d; ++k) {
+            cheb_nodes(c.lo[k], c.hi[k], ps, nodes);
+            bary_weights(nodes, ps, w);
+            for (int row = c.begin; row < c.end; ++row)
+                lagrange_bary(nodes, w, ps, pts[(size_t)row * d + k], &U[((size_t)row * d + k) * ps]);
+        }
+    }
+    // E_lo / E_hi: [j * p_s + i] = ell_i^{parent}(eta_j^{child}) for the low / high half (§3.6.1)
+    h->E64.assign(2 * ps * ps, 0.0);
+    {
+        double ref[kMaxPs], w[kMaxPs], half[kMaxPs];
+        cheb_nodes(-1.0, 1.0, ps, ref);
+        bary_weights(ref, ps, w);
+        for (int hi = 0; hi < 2; ++hi) {
+            cheb_nodes(hi ? 0.0 : -1.0, hi ? 1.0 : 0.0, ps, half);
+            for (int j = 0; j < ps; ++j) lagrange_bary(ref, w, ps, half[j], &h->E64[(size_t)hi * ps * ps + j * ps]);
+        }
+    }
+    if (o.prec == PH_FP32) {
+        h->d_U = upload_as<float>(h, U);
+        h->d_E = upload_as<float>(h, h->E64);
+    } else {
+        h->d_U = upload_as<double>(h, U);
+        h->d_E = upload_as<double>(h, h->E64);
+    }
+
+    // --------------------------------------------- H format: S_b and T_b (Phase 3)
+    const int nf = (int)plan.far_s.size();
+    h->fb_soff.assign(nf, 0);
+    h->fb_toff.assign(nf, 0);
+    if (o.fmt == PH_FMT_H && nf > 0) {
+        std::vector<double> st;
+        for (int b = 0; b < nf; ++b) {
+            const int key = plan.far_key[b];
+            const int* rk = &h->key_ranks[(size_t)key * (Delta + 1)];
+            const auto& cores = key_cores[key];
+            const Node& s = plan.nodes[plan.far_s[b]];
+            const Node& t = plan.nodes[plan.far_t[b]];
+            // U factors of an arbitrary (possibly inner) node, evaluated on its own box
+            auto factors = [&](const Node& c, int k, std::vector<double>& out) {
+                double nodes[kMaxPs], w[kMaxPs];
+                cheb_nodes(c.lo[k], c.hi[k], ps, nodes);
+                bary_weights(nodes, ps, w);
+                out.assign((size_t)c.size() * ps, 0.0);
+                for (int row = c.begin; row < c.end; ++row)
+                    lagrange_bary(nodes, w, ps, pts[(size_t)row * d + k], &out[(size_t)(row - c.begin) * ps]);
+            };
+            // S_b <- U_{s,1} G_1^{2};  S_b <- (U_{s,i} |x S_b) G_i^{2}
+            const int ns = s.size();
+            std::vector<double> S((size_t)ns * 1, 1.0), Uk;
+            int rprev = 1;
+            for (int k = 0; k < d; ++k) {
+                factors(s, k, Uk);
+                const int rn = rk[k + 1];
+                const auto& G = cores[k];  // (rprev, ps, rn) Fortran
+                std::vector<double> Sn((size_t)ns * rn, 0.0);
+                for (int x = 0; x < ns; ++x)
+                    for (int c = 0; c < rn; ++c) {
+                        double acc = 0.0;
+                        for (int j = 0; j < ps; ++j)
+                            for (int a = 0; a < rprev; ++a)
+                                acc += Uk[(size_t)x * ps + j] * S[(size_t)a * ns + x] * G[a + rprev * (j + ps * c)];
+                        Sn[(size_t)c * ns + x] = acc;
+                    }
+                S.swap(Sn);
+                rprev = rn;
+            }
+            // T_b from the right: Q <- sum_j U_{t,k}[y, j] G_{d+dt+k}[s, j, s'] Q[y, s']
+            const int ntt = t.size();
+            std::vector<double> Q((size_t)ntt, 1.0);
+            int rnext = 1;
+            for (int k = d - 1; k >= 0; --k) {
+                factors(t, k, Uk);
+                const int ci = d + dt + k;
+                const int rl = rk[ci];
+                const auto& G = cores[ci];  // (rl, ps, rnext)
+                std::vector<double> Qn((size_t)ntt * rl, 0.0);
+                for (int y = 0; y < ntt; ++y)
+                    for (int a = 0; a < rl; ++a) {
+                        double acc = 0.0;
+                        for (int j = 0; j < ps; ++j)
+                            for (int c = 0; c < rnext; ++c)
+                                acc += Uk[(size_t)y * ps + j] * G[a + rl * (j + ps * c)] * Q[(size_t)c * ntt + y];
+                        Qn[(size_t)a * ntt + y] = acc;
+                    }
+                Q.swap(Qn);
+                rnext = rl;
+            }
+            h->fb_soff[b] = (long long)st.size();
+            st.insert(st.end(), S.begin(), S.end());
+            h->fb_toff[b] = (long long)st.size();
+            st.insert(st.end(), Q.begin(), Q.end());
+        }
+        h->st_elems = (long long)st.size();
+        if (o.prec == PH_FP32) h->d_st = upload_as<float>(h, st);
+        else h->d_st = upload_as<double>(h, st);
+    }
+
+    h->offline_seconds =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return PH_OK;
+}
+
+}  // namespace ph

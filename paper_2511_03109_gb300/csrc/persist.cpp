@@ -1,0 +1,199 @@
+// ph_save / ph_load: the offline stage is the expensive part (minutes at large n),
+// so a built handle can be written to a file and mapped back onto a device.
+// Format: a magic word, the options, the plan, every host array and every
+// stored device arena, all little-endian binary.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "handle.h"
+
+namespace {
+
+const char kMagic[8] = {'P', 'H', 'L', 'I', 'B', '0', '0', '1'};
+
+struct Writer {
+    FILE* f;
+    void raw(const void* p, size_t n) {
+        if (n && fwrite(p, 1, n, f) != n) throw ph::Error(PH_ERR_IO, "write failed");
+    }
+    template <typename T> void val(const T& v) { raw(&v, sizeof(T)); }
+    template <typename T> void vec(const std::vector<T>& v) {
+        unsigned long long n = v.size();
+        val(n);
+        raw(v.data(), n * sizeof(T));
+    }
+    void dev(const void* p, size_t bytes) {
+        std::vector<unsigned char> tmp(bytes);
+        if (bytes) PH_CUDA(cudaMemcpy(tmp.data(), p, bytes, cudaMemcpyDeviceToHost));
+        vec(tmp);
+    }
+};
+
+struct Reader {
+    FILE* f;
+    void raw(void* p, size_t n) {
+        if (n && fread(p, 1, n, f) != n) throw ph::Error(PH_ERR_IO, "truncated file");
+    }
+    template <typename T> void val(T& v) { raw(&v, sizeof(T)); }
+    template <typename T> void vec(std::vector<T>& v) {
+        unsigned long long n = 0;
+        val(n);
+        if (n > (1ull << 40)) throw ph::Error(PH_ERR_IO, "corrupt file");
+        v.resize(n);
+        raw(v.data(), n * sizeof(T));
+    }
+    void* dev(ph_handle* h) {
+        std::vector<unsigned char> tmp;
+        vec(tmp);
+        void* p = ph::dev_alloc(h, tmp.size());
+        if (!tmp.empty()) PH_CUDA(cudaMemcpy(p, tmp.data(), tmp.size(), cudaMemcpyHostToDevice));
+        return p;
+    }
+};
+
+template <typename IO, typename P>
+void plan_io(IO& io, P& plan) {
+    io.val(plan.d);
+    io.val(plan.n);
+    io.val(plan.depth);
+    io.vec(plan.perm);
+    io.vec(plan.leaves);
+    io.vec(plan.near_s);
+    io.vec(plan.near_t);
+    io.vec(plan.far_s);
+    io.vec(plan.far_t);
+    io.vec(plan.far_key);
+    io.vec(plan.key_rep);
+    io.vec(plan.near_by_leaf);
+    io.vec(plan.far_targets);
+    io.vec(plan.far_by_target);
+}
+
+template <typename IO, typename H>
+void scalars_io(IO& io, H& h) {
+    io.val(h.kernel);
+    io.val(h.opts);
+    io.val(h.PD);
+    io.val(h.Delta);
+    io.val(h.p_theta_total);
+    io.val(h.scalar);
+    io.val(h.offline_seconds);
+    io.vec(h.nb_rank);
+    io.vec(h.nb_off);
+    io.vec(h.nb_toff);
+    io.vec(h.nb_woff);
+    io.vec(h.key_ranks);
+    io.vec(h.key_off);
+    io.vec(h.key_hoff);
+    io.vec(h.fb_soff);
+    io.vec(h.fb_toff);
+    io.val(h.near_elems);
+    io.val(h.near_theta_elems);
+    io.val(h.far_elems);
+    io.val(h.far_theta_elems);
+    io.val(h.H_elems);
+    io.val(h.st_elems);
+    io.val(h.w_elems);
+    io.vec(h.theta_nodes);
+    io.vec(h.theta_bw);
+    io.vec(h.E64);
+}
+
+}  // namespace
+
+extern "C" ph_status ph_save(const ph_handle* hc, const char* path) {
+    if (!hc || !path) return PH_ERR_INVALID_ARG;
+    ph_handle* h = const_cast<ph_handle*>(hc);
+    FILE* f = fopen(path, "wb");
+    if (!f) {
+        h->last_error = std::string("cannot open ") + path;
+        return PH_ERR_IO;
+    }
+    try {
+        PH_CUDA(cudaSetDevice(h->device));
+        PH_CUDA(cudaDeviceSynchronize());
+        Writer w{f};
+        w.raw(kMagic, 8);
+        scalars_io(w, *h);
+        plan_io(w, h->plan);
+        unsigned long long nn = h->plan.nodes.size();
+        w.val(nn);
+        for (const auto& nd : h->plan.nodes) {
+            w.val(nd.level); w.val(nd.parent); w.val(nd.halves); w.val(nd.begin); w.val(nd.end); w.val(nd.leaf);
+            w.raw(nd.lo, sizeof(nd.lo)); w.raw(nd.hi, sizeof(nd.hi));
+            w.vec(nd.children);
+        }
+        const size_t sc = h->scalar;
+        w.dev(h->d_near, h->near_elems * sc);
+        w.dev(h->d_near_theta, h->near_theta_elems * 8);
+        w.dev(h->d_far, h->far_elems * sc);
+        w.dev(h->d_far_theta, h->far_theta_elems * 8);
+        w.dev(h->d_st, h->st_elems * sc);
+        w.dev(h->d_U, (size_t)h->plan.n * h->plan.d * h->opts.p_s * sc);
+        w.dev(h->d_E, (size_t)2 * h->opts.p_s * h->opts.p_s * sc);
+    } catch (const ph::Error& e) {
+        fclose(f);
+        h->last_error = e.what();
+        return e.status;
+    }
+    if (fclose(f) != 0) return PH_ERR_IO;
+    return PH_OK;
+}
+
+extern "C" ph_status ph_load(const char* path, int device, ph_handle** out) {
+    if (!path || !out) return PH_ERR_INVALID_ARG;
+    *out = nullptr;
+    FILE* f = fopen(path, "rb");
+    if (!f) return PH_ERR_IO;
+    ph_handle* h = new ph_handle();
+    ph_status st = PH_OK;
+    try {
+        Reader r{f};
+        char magic[8];
+        r.raw(magic, 8);
+        if (std::memcmp(magic, kMagic, 8) != 0) throw ph::Error(PH_ERR_IO, "not a libph file");
+        scalars_io(r, *h);
+        h->device = device;
+        h->opts.device = device;
+        plan_io(r, h->plan);
+        unsigned long long nn = 0;
+        r.val(nn);
+        h->plan.nodes.resize(nn);
+        for (auto& nd : h->plan.nodes) {
+            r.val(nd.level); r.val(nd.parent); r.val(nd.halves); r.val(nd.begin); r.val(nd.end); r.val(nd.leaf);
+            r.raw(nd.lo, sizeof(nd.lo)); r.raw(nd.hi, sizeof(nd.hi));
+            r.vec(nd.children);
+        }
+        PH_CUDA(cudaSetDevice(device));
+        PH_CUDA(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+        PH_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+        PH_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+        h->d_near = r.dev(h);
+        h->d_near_theta = (double*)r.dev(h);
+        h->d_far = r.dev(h);
+        h->d_far_theta = (double*)r.dev(h);
+        h->d_st = r.dev(h);
+        h->d_U = r.dev(h);
+        h->d_E = r.dev(h);
+        h->d_H = ph::dev_alloc(h, (h->H_elems > 0 ? h->H_elems : 1) * h->scalar);
+        h->d_w = ph::dev_alloc(h, (h->w_elems > 0 ? h->w_elems : 1) * h->scalar);
+        ph::refresh_views(h);
+    } catch (const ph::Error& e) {
+        st = e.status;
+    } catch (...) {
+        st = PH_ERR_IO;
+    }
+    fclose(f);
+    if (st != PH_OK) {
+        ph::free_device(h);
+        delete h;
+        return st;
+    }
+    *out = h;
+    return PH_OK;
+}

@@ -1,0 +1,225 @@
+"""ctypes binding of libph (include/ph.h): the same entry points, argument marshalling only.
+
+Every computation runs in the CUDA library.  Importing this module loads
+``lib/libph.so`` and raises ImportError when it has not been built (run
+``__graft_entry__.build()``); there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libph.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libph is not built ({LIB_PATH} missing); run __graft_entry__.build()")
+_lib = C.CDLL(LIB_PATH)
+
+# ph_status
+PH_OK = 0
+PH_ERR_INVALID_ARG = 1
+PH_ERR_THETA_OUT_OF_BOX = 2
+PH_ERR_NOT_INSTANTIATED = 3
+PH_ERR_OOM = 4
+PH_ERR_CUDA = 5
+PH_ERR_NONFINITE = 6
+PH_ERR_TIMEOUT = 7
+PH_ERR_IO = 8
+PH_ERR_UNSUPPORTED = 9
+
+KERNELS = {"gauss": 0, "matern32": 1, "matern52": 2, "aniso_gauss": 3, "se": 4, "exponential": 5,
+           "mc": 6, "poly": 7, "polyxy": 8}
+FORMATS = {"h2": 0, "h": 1}
+PRECISIONS = {"fp64": 0, "fp32": 1}
+
+
+class BuildOpts(C.Structure):
+    _fields_ = [("d", C.c_int), ("dtheta", C.c_int), ("theta_lo", C.c_double * 3),
+                ("theta_hi", C.c_double * 3), ("degree", C.c_int * 3), ("p_s", C.c_int),
+                ("l_max", C.c_int), ("eta", C.c_double), ("tol", C.c_double),
+                ("near_tol", C.c_double), ("rank_cap", C.c_int), ("fmt", C.c_int),
+                ("prec", C.c_int), ("dedup", C.c_int), ("check_finite", C.c_int),
+                ("device", C.c_int)]
+
+
+class Info(C.Structure):
+    _fields_ = [("n", C.c_long), ("d", C.c_int), ("dtheta", C.c_int), ("p_s", C.c_int),
+                ("p_theta", C.c_int * 3), ("prec", C.c_int), ("fmt", C.c_int),
+                ("n_nodes", C.c_int), ("n_leaves", C.c_int), ("tree_depth", C.c_int),
+                ("n_near", C.c_long), ("n_far", C.c_long), ("n_far_keys", C.c_long),
+                ("near_entries", C.c_long), ("near_rank_sum", C.c_long),
+                ("near_rank_max", C.c_int), ("far_rank_max", C.c_int),
+                ("far_rank_mean", C.c_double), ("near_bytes", C.c_long),
+                ("near_theta_bytes", C.c_long), ("far_bytes", C.c_long),
+                ("basis_bytes", C.c_long), ("alg_bytes_per_call", C.c_double),
+                ("flops_per_rhs", C.c_double), ("offline_seconds", C.c_double)]
+
+    def as_dict(self):
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if isinstance(v, C.Array) else v
+        return out
+
+
+_H = C.c_void_p
+_P = C.c_void_p
+
+_SIGS = {
+    "ph_offline_build": (C.c_int, [C.POINTER(C.c_double), C.c_long, C.c_int, C.POINTER(BuildOpts),
+                                   C.POINTER(_H)]),
+    "ph_instantiate": (C.c_int, [_H, C.POINTER(C.c_double), _P]),
+    "ph_matvec": (C.c_int, [_H, _P, C.c_long, C.c_int, _P, C.c_long, _P]),
+    "ph_matvec_host": (C.c_int, [_H, _P, C.c_long, C.c_int, _P, C.c_long, _P]),
+    "ph_get_info": (C.c_int, [_H, C.POINTER(Info)]),
+    "ph_save": (C.c_int, [_H, C.c_char_p]),
+    "ph_load": (C.c_int, [C.c_char_p, C.c_int, C.POINTER(_H)]),
+    "ph_destroy": (None, [_H]),
+    "ph_last_error": (C.c_char_p, [_H]),
+    "ph_plan": (C.c_int, [C.POINTER(C.c_double), C.c_long, C.c_int, C.c_int, C.c_double,
+                          C.POINTER(C.c_long), C.POINTER(C.c_int)]),
+    "ph_version": (C.c_char_p, []),
+    "ph_profile_enable": (C.c_int, [_H, C.c_int]),
+    "ph_profile_read": (C.c_int, [_H, C.POINTER(C.c_double), C.POINTER(C.c_long)]),
+}
+
+for _name, (_res, _args) in _SIGS.items():
+    _fn = getattr(_lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+    globals()[_name] = _fn
+
+EXPORTED = tuple(_SIGS)
+
+PROF_KINDS = ("instantiate", "gather", "near", "upsweep_leaf", "transfer_up", "coupling",
+              "transfer_down", "far_h", "combine")
+
+
+class PHError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"libph status {status}: {msg}")
+        self.status = status
+
+
+def check(status, handle=None):
+    if status != PH_OK:
+        raise PHError(status, ph_last_error(handle).decode(errors="replace"))
+    return status
+
+
+def make_opts(d, theta_lo, theta_hi, degree, p_s, l_max, eta, tol, rank_cap=0, fmt="h2",
+              prec="fp32", dedup=True, check_finite=False, near_tol=-1.0, device=0) -> BuildOpts:
+    o = BuildOpts()
+    o.d = d
+    o.dtheta = len(theta_lo)
+    for k in range(len(theta_lo)):
+        o.theta_lo[k] = float(theta_lo[k])
+        o.theta_hi[k] = float(theta_hi[k])
+        o.degree[k] = int(degree[k])
+    o.p_s, o.l_max, o.eta, o.tol = int(p_s), int(l_max), float(eta), float(tol)
+    o.near_tol = float(near_tol)
+    o.rank_cap = int(rank_cap or 0)
+    o.fmt = FORMATS[fmt]
+    o.prec = PRECISIONS[prec]
+    o.dedup = 1 if dedup else 0
+    o.check_finite = 1 if check_finite else 0
+    o.device = int(device)
+    return o
+
+
+def plan(points, l_max, eta):
+    """Host-only tree / block tree sizes (ph_plan); returns (counts dict, perm)."""
+    import numpy as np
+    P = np.ascontiguousarray(points, dtype=np.float64)
+    n, d = P.shape
+    counts = (C.c_long * 8)()
+    perm = np.empty(n, dtype=np.int32)
+    check(ph_plan(P.ctypes.data_as(C.POINTER(C.c_double)), n, d, int(l_max), float(eta), counts,
+                  perm.ctypes.data_as(C.POINTER(C.c_int))))
+    keys = ["nodes", "leaves", "near", "far", "far_keys", "near_entries", "max_near_per_leaf", "depth"]
+    return dict(zip(keys, list(counts))), perm
+
+
+class ParametricMatrix:
+    """Owns one libph handle.  Device buffers are passed as raw pointers (torch's data_ptr())."""
+
+    def __init__(self, points, kernel, opts: BuildOpts):
+        import numpy as np
+        P = np.ascontiguousarray(points, dtype=np.float64)
+        self.n, self.d = P.shape
+        self.prec = "fp32" if opts.prec == 1 else "fp64"
+        self.dtheta = opts.dtheta
+        h = _H()
+        check(ph_offline_build(P.ctypes.data_as(C.POINTER(C.c_double)), self.n, KERNELS[kernel],
+                               C.byref(opts), C.byref(h)))
+        self.h = h
+
+    @classmethod
+    def load(cls, path, device=0):
+        self = cls.__new__(cls)
+        h = _H()
+        check(ph_load(path.encode(), device, C.byref(h)))
+        self.h = h
+        inf = self.info()
+        self.n, self.d, self.dtheta = inf["n"], inf["d"], inf["dtheta"]
+        self.prec = "fp32" if inf["prec"] == 1 else "fp64"
+        return self
+
+    def info(self) -> dict:
+        i = Info()
+        check(ph_get_info(self.h, C.byref(i)), self.h)
+        return i.as_dict()
+
+    def instantiate(self, theta, stream=0):
+        th = (C.c_double * 3)(*[float(t) for t in list(theta)[:3]])
+        return check(ph_instantiate(self.h, th, C.c_void_p(stream)), self.h)
+
+    def matvec_ptr(self, x_ptr, ldx, m, y_ptr, ldy, stream=0):
+        return check(ph_matvec(self.h, C.c_void_p(x_ptr), ldx, m, C.c_void_p(y_ptr), ldy,
+                               C.c_void_p(stream)), self.h)
+
+    def matvec_host_ptr(self, x_ptr, ldx, m, y_ptr, ldy, stream=0):
+        return check(ph_matvec_host(self.h, C.c_void_p(x_ptr), ldx, m, C.c_void_p(y_ptr), ldy,
+                                    C.c_void_p(stream)), self.h)
+
+    def matvec(self, X, Y=None, stream=None):
+        """Y = K_hat(theta) X for torch CUDA tensors X (n x m, column-major: X.t() contiguous)."""
+        import torch
+        if X.dim() == 1:
+            X = X[:, None]
+        n, m = X.shape
+        Xc = X.t().contiguous() if not _colmajor(X) else X
+        if Y is None:
+            Y = torch.empty((m, n), dtype=X.dtype, device=X.device).t()
+        s = torch.cuda.current_stream(X.device).cuda_stream if stream is None else stream
+        self.matvec_ptr(Xc.data_ptr(), n, m, Y.data_ptr(), n, s)
+        return Y
+
+    def profile(self, enable=True):
+        return check(ph_profile_enable(self.h, 1 if enable else 0), self.h)
+
+    def profile_read(self) -> dict:
+        """{kind: (milliseconds, launches)} since the last read (synchronises)."""
+        ms = (C.c_double * len(PROF_KINDS))()
+        la = (C.c_long * len(PROF_KINDS))()
+        check(ph_profile_read(self.h, ms, la), self.h)
+        return {k: (ms[i], la[i]) for i, k in enumerate(PROF_KINDS)}
+
+    def save(self, path):
+        return check(ph_save(self.h, path.encode()), self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            ph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _colmajor(X) -> bool:
+    return X.dim() == 2 and X.stride(0) == 1 and X.stride(1) == X.shape[0]

@@ -1,0 +1,160 @@
+"""GPU parity of the whole online stage (instantiate + matvec) against the FP64 oracle.
+
+Bar: relative 2-norm error per right-hand side <= 1e-10 on the FP64 path and <= 1e-5 on the
+FP32 path, on inputs that span several leaves, ragged leaf sizes, both formats and several m.
+"""
+import numpy as np
+import pytest
+
+from oracle import cheb, kernels
+from paper_2511_03109_gb300 import inputs
+
+from helpers import TOL, build_pair, device_apply, rel_err_rows, target_rows
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+CASES = [
+    # name, n, d, kernel, lo, hi, degree, p_s, l_max, eta, tol, cap, fmt, prec, m
+    ("h2_fp64_d2", 1000, 2, "gauss", [0.1], [1.0], [12], 6, 3, 1.0, 1e-8, 32, "h2", "fp64", 3),
+    ("h_fp64_d2", 1000, 2, "gauss", [0.1], [1.0], [12], 6, 3, 1.0, 1e-8, 32, "h", "fp64", 1),
+    ("h2_fp32_d2_m16", 1500, 2, "matern32", [0.05], [0.5], [20], 8, 3, 1.0, 1e-5, 64, "h2", "fp32", 16),
+    ("h_fp32_d2_m5", 1500, 2, "matern52", [0.05], [0.5], [16], 8, 3, np.sqrt(2.0), 1e-5, 64, "h", "fp32", 5),
+    ("h2_fp64_d1", 400, 1, "exponential", [0.2], [1.0], [10], 6, 4, 1.0, 1e-9, 0, "h2", "fp64", 2),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_parity_small(case):
+    name, n, d, kern, lo, hi, deg, ps, lmax, eta, tol, cap, fmt, prec, m = case
+    P = inputs.uniform_points(n, d, 1000 + n)
+    X = inputs.gaussian_rhs(n, m, 2000 + n)
+    A, M, _ = build_pair(P, kern, lo, hi, deg, ps, lmax, eta, tol, cap, fmt, prec)
+    for theta in ([lo[0] + 0.37 * (hi[0] - lo[0])], [lo[0]], [hi[0]]):
+        ref = M.matvec(M.instantiate(theta), X)
+        got = device_apply(A, theta, X, prec)
+        err = rel_err_rows(ref, got)
+        assert np.all(err <= TOL[prec]), (name, theta, err)
+    A.close()
+
+
+def test_parity_3d_h2_fp32_sampled_rows():
+    """3-D Matern 3/2, eta = sqrt(3), 16 right-hand sides; oracle on a sample of target leaves."""
+    n = 3000
+    P = inputs.uniform_points(n, 3, 77)
+    X = inputs.gaussian_rhs(n, 16, 78)
+    A, M, targets = build_pair(P, "matern32", [0.05], [0.5], [20], 5, 2, np.sqrt(3.0), 1e-5, 64,
+                               "h2", "fp32", targets_every=13)
+    rows = target_rows(targets)
+    theta = [0.211]
+    ref = M.matvec(M.instantiate(theta, targets), X, targets)
+    got = device_apply(A, theta, X, "fp32")
+    assert np.all(rel_err_rows(ref, got, rows) <= TOL["fp32"])
+    A.close()
+
+
+def test_theta_at_chebyshev_node_and_ragged_ld():
+    n = 800
+    P = inputs.uniform_points(n, 2, 31)
+    X = inputs.gaussian_rhs(n, 17, 32)  # 17 = one full chunk of 16 plus a ragged one
+    A, M, _ = build_pair(P, "gauss", [0.1], [1.0], [16], 8, 3, 1.0, 1e-7, 32, "h2", "fp64")
+    node = float(cheb.cheb_nodes(0.1, 1.0, 17)[5])
+    ref = M.matvec(M.instantiate([node]), X)
+    got = device_apply(A, [node], X, "fp64", ldx_pad=13)
+    assert np.all(rel_err_rows(ref, got) <= TOL["fp64"])
+    A.close()
+
+
+@pytest.mark.parametrize("fmt", ["h2", "h"])
+def test_polynomial_kernel_exact_against_dense(fmt):
+    """No truncation and a polynomial kernel of low degree: K_hat(theta) X = K(theta) X to rounding."""
+    n = 700
+    P = inputs.uniform_points(n, 2, 41)
+    X = inputs.gaussian_rhs(n, 2, 42)
+    A, _, _ = build_pair(P, "poly", [0.5], [2.0], [2], 5, 3, 1.0, 0.0, 0, fmt, "fp64")
+    for theta in ([0.5], [1.234], [2.0]):
+        exact = kernels.dense_apply("poly", P, theta, X)
+        assert np.all(rel_err_rows(exact, device_apply(A, theta, X, "fp64")) <= 1e-11)
+    A.close()
+
+
+def test_no_far_field_and_single_leaf():
+    P = inputs.uniform_points(300, 2, 51)
+    X = inputs.gaussian_rhs(300, 1, 52)
+    for lmax in (0, 1):
+        A, M, _ = build_pair(P, "gauss", [0.1], [1.0], [10], 4, lmax, 1.0, 1e-9, 0, "h2", "fp64")
+        assert A.info()["n_far"] == 0
+        ref = M.matvec(M.instantiate([0.3]), X)
+        assert np.all(rel_err_rows(ref, device_apply(A, [0.3], X, "fp64")) <= TOL["fp64"])
+        A.close()
+
+
+def test_dedup_matches_per_block_compression():
+    P = inputs.uniform_points(900, 2, 61)
+    X = inputs.gaussian_rhs(900, 2, 62)
+    A1, M, _ = build_pair(P, "matern52", [0.1], [0.6], [10], 6, 3, 1.0, 1e-9, 0, "h2", "fp64", dedup=True)
+    A2, _, _ = build_pair(P, "matern52", [0.1], [0.6], [10], 6, 3, 1.0, 1e-9, 0, "h2", "fp64", dedup=False)
+    assert A1.info()["n_far_keys"] < A2.info()["n_far_keys"] == A2.info()["n_far"]
+    y1 = device_apply(A1, [0.44], X, "fp64")
+    y2 = device_apply(A2, [0.44], X, "fp64")
+    assert np.all(rel_err_rows(y2, y1) <= 1e-11)
+    A1.close()
+    A2.close()
+
+
+def test_errors_are_status_codes():
+    from paper_2511_03109_gb300 import ph
+
+    P = inputs.uniform_points(200, 2, 71)
+    opts = ph.make_opts(2, [0.1], [1.0], [8], 4, 2, 1.0, 1e-6, prec="fp64", check_finite=True)
+    A = ph.ParametricMatrix(P, "gauss", opts)
+    X = torch.zeros((1, 200), dtype=torch.float64, device="cuda:0")
+    Y = torch.zeros_like(X)
+    with pytest.raises(ph.PHError) as e:
+        A.matvec_ptr(X.data_ptr(), 200, 1, Y.data_ptr(), 200)
+    assert e.value.status == ph.PH_ERR_NOT_INSTANTIATED
+    with pytest.raises(ph.PHError) as e:
+        A.instantiate([1.5])
+    assert e.value.status == ph.PH_ERR_THETA_OUT_OF_BOX
+    with pytest.raises(ph.PHError) as e:
+        A.instantiate([float("nan")])
+    assert e.value.status == ph.PH_ERR_NONFINITE
+    A.instantiate([0.5])
+    X[0, 17] = float("inf")
+    with pytest.raises(ph.PHError) as e:
+        A.matvec_ptr(X.data_ptr(), 200, 1, Y.data_ptr(), 200)
+    assert e.value.status == ph.PH_ERR_NONFINITE
+    with pytest.raises(ph.PHError) as e:
+        A.matvec_ptr(X.data_ptr(), 100, 1, Y.data_ptr(), 200)  # ldx < n
+    assert e.value.status == ph.PH_ERR_INVALID_ARG
+    A.close()
+
+
+def test_host_entry_point_and_save_load(tmp_path):
+    from paper_2511_03109_gb300 import ph
+
+    n = 600
+    P = inputs.uniform_points(n, 2, 81)
+    X = inputs.gaussian_rhs(n, 4, 82)
+    opts = ph.make_opts(2, [0.1], [1.0], [10], 6, 3, 1.0, 1e-7, rank_cap=32, prec="fp32")
+    A = ph.ParametricMatrix(P, "gauss", opts)
+    ref = device_apply(A, [0.6], X, "fp32")
+    Xh = np.asfortranarray(X, dtype=np.float32)
+    Yh = np.zeros_like(Xh)
+    A.matvec_host_ptr(Xh.ctypes.data, n, 4, Yh.ctypes.data, n)
+    assert np.array_equal(Yh, ref.astype(np.float32))
+    path = str(tmp_path / "a.ph")
+    A.save(path)
+    B = ph.ParametricMatrix.load(path)
+    assert B.info()["near_bytes"] == A.info()["near_bytes"]
+    assert np.array_equal(device_apply(B, [0.6], X, "fp32"), ref)
+    A.close()
+    B.close()
