@@ -66,8 +66,6 @@ def oracle_sample(P, X, theta, n_leaves=ORACLE_SAMPLE_LEAVES, seed=7):
     first with a spawn-started process pool and is not timed; the timed part is the oracle's
     instantiate + matvec for the sample rows.  Returns (seconds, rows, Y_rows, cores).
     """
-    import multiprocessing as mp
-
     from oracle import pmatrix
 
     M = pmatrix.ParametricMatrix(P, WL.kernel, WL.theta_lo, WL.theta_hi, WL.degree, WL.p_s,
@@ -75,9 +73,7 @@ def oracle_sample(P, X, theta, n_leaves=ORACLE_SAMPLE_LEAVES, seed=7):
     rng = np.random.default_rng(seed)
     pick = sorted(rng.choice(len(M.leaves), size=n_leaves, replace=False))
     targets = [M.leaves[i] for i in pick]
-    workers = max(1, (os.cpu_count() or 2))
-    ctx = mp.get_context("spawn")
-    with ctx.Pool(workers) as pool:
+    with _oracle_pool() as pool:
         M.offline(targets, pool=pool)
     t0 = time.perf_counter()
     inst = M.instantiate(theta, targets)
@@ -85,6 +81,26 @@ def oracle_sample(P, X, theta, n_leaves=ORACLE_SAMPLE_LEAVES, seed=7):
     dt = time.perf_counter() - t0
     rows = np.sort(np.concatenate([c.idx for c in targets]))
     return dt, rows, Y[rows], os.cpu_count() or 1, len(M.leaves)
+
+
+def _oracle_pool():
+    """Spawn-started pool for the oracle's per-block TT-SVDs, one single-threaded BLAS per worker."""
+    import multiprocessing as mp
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        return mp.get_context("spawn").Pool(max(1, os.cpu_count() or 2))
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+def log(msg):
+    print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
 
 
 # ------------------------------------------------------------------------ clock sampling
@@ -156,8 +172,15 @@ def run_gpu(args, rank, world, local_rank):
     m, n = WL.m, WL.n
     opts = ph.make_opts(WL.d, WL.theta_lo, WL.theta_hi, WL.degree, WL.p_s, WL.l_max, WL.eta, WL.tol,
                         rank_cap=WL.rank_cap, fmt=WL.fmt, prec=WL.precision, device=local_rank)
-    A = ph.ParametricMatrix(P, WL.kernel, opts)
+    if args.load:
+        A = ph.ParametricMatrix.load(args.load, device=local_rank)
+    else:
+        log(f"offline build n={n} on cuda:{local_rank}")
+        A = ph.ParametricMatrix(P, WL.kernel, opts)
+        if args.save:
+            A.save(args.save)
     info = A.info()
+    log(f"offline done in {info['offline_seconds']:.1f} s")
     total_steps = args.warmup + args.steps
     thetas_all = inputs.uniform_thetas(WL.theta_lo, WL.theta_hi, max(30, world * total_steps), WL.theta_seed)
     thetas = thetas_all[rank::world][:total_steps]
@@ -273,7 +296,9 @@ def run_gpu(args, rank, world, local_rank):
         A.matvec_ptr(X.data_ptr(), n, m, Y.data_ptr(), n, sp)
         torch.cuda.synchronize()
         Ygpu = Y.double().cpu().numpy().T
+        log("oracle sample")
         dt, rows, Yo, cores, nleaves = oracle_sample(P, Xh, th0)
+        log(f"oracle sample timed part {dt:.2f} s")
         frac = len(rows) / n
         out["cpu_baseline"] = {"value": m / (dt / frac), "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": f"rows of {ORACLE_SAMPLE_LEAVES} of {nleaves} target leaves "
@@ -299,15 +324,13 @@ def run_reference(args, rank, world):
     Xh = WL.rhs()
     m, n = WL.m, WL.n
     thetas = inputs.uniform_thetas(WL.theta_lo, WL.theta_hi, max(30, args.warmup + args.steps), WL.theta_seed)
-    import multiprocessing as mp
-
     from oracle import pmatrix
 
     M = pmatrix.ParametricMatrix(P, WL.kernel, WL.theta_lo, WL.theta_hi, WL.degree, WL.p_s, WL.l_max,
                                  WL.eta, WL.tol, rank_cap=WL.rank_cap, fmt=WL.fmt)
     rng = np.random.default_rng(7)
     targets = [M.leaves[i] for i in sorted(rng.choice(len(M.leaves), size=ORACLE_SAMPLE_LEAVES, replace=False))]
-    with mp.get_context("spawn").Pool(max(1, os.cpu_count() or 2)) as pool:
+    with _oracle_pool() as pool:
         M.offline(targets, pool=pool)
     rows = np.concatenate([c.idx for c in targets])
     frac = len(rows) / n
@@ -341,7 +364,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--save", default="", help="profiling only: write the built handle to this file")
+    ap.add_argument("--load", default="", help="profiling only: load a handle written by --save")
+    ap.add_argument("--n", type=int, default=0,
+                    help="profiling only: a smaller point count of the same workload (not a bench line)")
     args = ap.parse_args()
+    if args.n:
+        global WL
+        import dataclasses
+        WL = dataclasses.replace(WL, n=args.n, name=WL.name.replace(str(WL.n), str(args.n)))
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))

@@ -87,6 +87,13 @@ static void fill_view(ph_handle* h, DevView<T>& v, const std::vector<long>& io, 
     v.far_targets = I + io[16];
     v.far_by_target = I + io[17];
     v.level_slot = I + io[18];
+    v.n_items = (int)h->item_first.size();
+    v.item_first = I + io[20];
+    v.item_count = I + io[21];
+    v.item_leaf = I + io[22];
+    v.items_by_leaf = I + io[23];
+    v.part_stride = h->max_leaf;
+    v.partials = (T*)h->d_partials;
     v.nb_off = L + lo[0];
     v.nb_toff = L + lo[1];
     v.key_off = L + lo[2];
@@ -164,6 +171,22 @@ void refresh_views(ph_handle* h) {
         lvl_flat.insert(lvl_flat.end(), h->level_nodes[l].begin(), h->level_nodes[l].end());
         h->level_nodes_off[l + 1] = (int)lvl_flat.size();
     }
+    // near work items: up to kNearItemBlocks consecutive near blocks of one target leaf
+    constexpr int kNearItemBlocks = 4;
+    h->item_first.clear();
+    h->item_count.clear();
+    h->item_leaf.clear();
+    h->items_by_leaf.assign(plan.leaves.size() + 1, 0);
+    h->max_leaf = 1;
+    for (size_t l = 0; l < plan.leaves.size(); ++l) {
+        h->max_leaf = std::max(h->max_leaf, plan.nodes[plan.leaves[l]].size());
+        for (int b = plan.near_by_leaf[l]; b < plan.near_by_leaf[l + 1]; b += kNearItemBlocks) {
+            h->item_first.push_back(b);
+            h->item_count.push_back(std::min(kNearItemBlocks, plan.near_by_leaf[l + 1] - b));
+            h->item_leaf.push_back((int)l);
+        }
+        h->items_by_leaf[l + 1] = (int)h->item_first.size();
+    }
     std::vector<int> fbt = plan.far_by_target;
     if (fbt.empty()) fbt.push_back(0);
     put(plan.perm);                 // 0
@@ -186,6 +209,10 @@ void refresh_views(ph_handle* h) {
     put(fbt);                       // 17
     put(h->level_slot);             // 18
     put(lvl_flat);                  // 19
+    put(h->item_first);             // 20
+    put(h->item_count);             // 21
+    put(h->item_leaf);              // 22
+    put(h->items_by_leaf);          // 23
     std::vector<long long> lls;
     std::vector<long> lo;
     auto putl = [&](const std::vector<long long>& a) {
@@ -226,9 +253,10 @@ void ensure_workspace(ph_handle* h, int m) {
     if (S <= h->mcap) return;
     const Plan& plan = h->plan;
     const size_t sc = h->scalar;
-    for (void* p : {h->d_Xc, h->d_Ynear, h->d_yfar, h->d_xhat, h->d_yhat}) dev_free(h, p);
+    for (void* p : {h->d_Xc, h->d_Ynear, h->d_yfar, h->d_xhat, h->d_yhat, h->d_partials}) dev_free(h, p);
     h->d_Xc = dev_alloc(h, (size_t)plan.n * S * sc);
     h->d_Ynear = dev_alloc(h, (size_t)plan.n * S * sc);
+    h->d_partials = dev_alloc(h, std::max<size_t>(1, h->item_first.size()) * h->max_leaf * S * sc);
     h->d_yfar = nullptr;
     h->d_xhat = h->d_yhat = nullptr;
     if (h->opts.fmt == PH_FMT_H && h->n_far_levels > 0)

@@ -38,9 +38,16 @@ struct DevView {
     const long long* nb_off;    // element offset of G_{b,1} (r slabs of n_s x n_t) in near_cores
     const long long* nb_toff;   // offset of the theta cores in near_theta (FP64)
     const int* nb_woff;         // offset of w_b in w
-    const T* near_cores;
+    const T* near_cores;        // G_{b,1}, column-interleaved: (i, j, slab k) at [(j r + k) n_s + i]
     const double* near_theta;
     T* w;                       // instantiated near weights
+    int n_items;                // near work items: runs of consecutive near blocks of one target leaf
+    const int* item_first;
+    const int* item_count;
+    const int* item_leaf;
+    const int* items_by_leaf;   // CSR over leaves
+    int part_stride;            // rows per item in the partial buffer (max leaf size)
+    T* partials;                // n_items x part_stride x mcap
     // far field
     int n_keys, Delta;
     const int* key_ranks;       // (Delta + 1) per key
@@ -125,6 +132,9 @@ struct ph_handle {
     void* d_yfar = nullptr;
     void* d_xhat = nullptr;
     void* d_yhat = nullptr;
+    void* d_partials = nullptr;
+    std::vector<int> item_first, item_count, item_leaf, items_by_leaf;
+    int max_leaf = 1;
     DeviceBuffer ws;
     DeviceBuffer host_stage_x, host_stage_y;    // device staging for ph_matvec_host
     int n_far_levels = 0;

@@ -181,7 +181,8 @@ __global__ void near_tsqr_kernel(NearBuild a, double* Rout) {
     }
 }
 
-// G_{b,1} = A_b V_r written as r slabs of n_s x n_t (i fastest) in compute type T.
+// G_{b,1} = A_b V_r in compute type T, stored column-interleaved: entry (i, j) of slab c at
+// [(j r + c) n_s + i], so that one column j of all r slabs is one contiguous run.
 template <typename T>
 __global__ void near_project_kernel(NearBuild a, const double* vecs, const int* rank,
                                     const long long* off, T* out) {
@@ -197,13 +198,15 @@ __global__ void near_project_kernel(NearBuild a, const double* vecs, const int* 
         __syncthreads();
         eval_near_chunk(a, b, q0, nq, sA);
         __syncthreads();
+        const int ns = a.s_n[b];
         for (int e = threadIdx.x; e < kChunk * r; e += blockDim.x) {
             int row = e % kChunk, c = e / kChunk;
             long long q = q0 + row;
             if (q < nq) {
                 double s = 0.0;
                 for (int k = 0; k < a.P; ++k) s += sA[row * a.P + k] * sV[c * a.P + k];
-                G[(long long)c * nq + q] = (T)s;
+                const long long i = q % ns, j = q / ns;
+                G[(j * r + c) * ns + i] = (T)s;  // column-interleaved: (j, slab c, i)
             }
         }
     }

@@ -106,21 +106,26 @@ __global__ void gather_kernel(DevView<T> v, const T* __restrict__ X, long long l
 
 // -------------------------------------------------------------------------------- near field
 
-// One CTA per target leaf s.  Thread (row i, group g) walks the columns j = g, g + G, ... of
-// every near block (s, t): d_ij = sum_k w_k G_{b,1}[k][i + n_s j] (coalesced over i), then
-// acc[c] += d_ij x_t[j][c] with x_t staged in shared memory.  The instantiated block is never
-// written; the groups' partial sums are reduced in shared memory and Y_near written once.
+// One CTA per near work item (up to four consecutive near blocks (s, t) of one target leaf s).
+// Thread (row i, group g) walks the columns j = g, g + G, ... of each block:
+//   d_ij = sum_k w_k G_{b,1}[(j r + k) n_s + i]   (r loads, coalesced over i)
+//   acc[c] += d_ij x_t[j][c]                      (x_t staged in shared memory)
+// so the instantiated block D_b(theta) never exists in memory.  Groups are reduced in shared
+// memory and the item's partial sum Y_s^{item} is written once; combine_kernel adds the
+// partials of a leaf in a fixed order.
 template <typename T, int MC>
 __global__ void __launch_bounds__(kThreads) near_kernel(DevView<T> v, int S, int c0, int maxleaf) {
     extern __shared__ unsigned char smem_raw[];
+    constexpr int RK = 8;                                 // ranks up to RK use the unrolled path
     T* xs = reinterpret_cast<T*>(smem_raw);              // maxleaf x MC
     T* red = xs + (size_t)maxleaf * MC;                   // kThreads x MC
     T* sw = red + (size_t)kThreads * MC;                  // kMaxNearRank
-    const int leaf = blockIdx.x;
+    const int item = blockIdx.x;
+    const int leaf = v.item_leaf[item];
     const int snode = v.leaf_node[leaf];
-    const int row0 = v.node_begin[snode];
-    const int ns = v.node_end[snode] - row0;
-    const int b0 = v.near_by_leaf[leaf], b1 = v.near_by_leaf[leaf + 1];
+    const int ns = v.node_end[snode] - v.node_begin[snode];
+    const int b0 = v.item_first[item], b1 = b0 + v.item_count[item];
+    T* part = v.partials + (long long)item * v.part_stride * S;
     for (int rbase = 0; rbase < ns; rbase += kThreads) {
         const int nrows = min(kThreads, ns - rbase);
         const int RP = (nrows + 31) & ~31;
@@ -142,14 +147,43 @@ __global__ void __launch_bounds__(kThreads) near_kernel(DevView<T> v, int S, int
             }
             if (threadIdx.x < r) sw[threadIdx.x] = v.w[v.nb_woff[b] + threadIdx.x];
             __syncthreads();
-            if (active) {
-                const long long slab = (long long)ns * nt;
-                const T* Gp = v.near_cores + v.nb_off[b] + (rbase + i);
-#pragma unroll 4
-                for (int j = g; j < nt; j += G) {
-                    const T* gj = Gp + (long long)j * ns;
+            if (!active) continue;
+            const T* Gb = v.near_cores + v.nb_off[b] + (rbase + i);
+            const long long cstride = (long long)r * ns;  // one column j of all r slabs
+            if (r <= RK) {
+                T wr[RK];
+#pragma unroll
+                for (int k = 0; k < RK; ++k) wr[k] = (k < r) ? sw[k] : T(0);
+                int j = g;
+                for (; j + 3 * G < nt; j += 4 * G) {
+                    T val[4][RK];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int k = 0; k < RK; ++k)
+                            val[u][k] = (k < r) ? __ldg(Gb + (j + u * G) * cstride + (long long)k * ns) : T(0);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        T dij = T(0);
+#pragma unroll
+                        for (int k = 0; k < RK; ++k) dij += wr[k] * val[u][k];
+                        const T* xj = xs + (j + u * G) * MC;
+#pragma unroll
+                        for (int c = 0; c < MC; ++c) acc[c] += dij * xj[c];
+                    }
+                }
+                for (; j < nt; j += G) {
                     T dij = T(0);
-                    for (int k = 0; k < r; ++k) dij += sw[k] * __ldg(gj + k * slab);
+#pragma unroll
+                    for (int k = 0; k < RK; ++k)
+                        if (k < r) dij += wr[k] * __ldg(Gb + j * cstride + (long long)k * ns);
+#pragma unroll
+                    for (int c = 0; c < MC; ++c) acc[c] += dij * xs[j * MC + c];
+                }
+            } else {
+                for (int j = g; j < nt; j += G) {
+                    T dij = T(0);
+                    for (int k = 0; k < r; ++k) dij += sw[k] * __ldg(Gb + j * cstride + (long long)k * ns);
 #pragma unroll
                     for (int c = 0; c < MC; ++c) acc[c] += dij * xs[j * MC + c];
                 }
@@ -164,7 +198,7 @@ __global__ void __launch_bounds__(kThreads) near_kernel(DevView<T> v, int S, int
 #pragma unroll
                 for (int c = 0; c < MC; ++c) acc[c] += red[(gg * RP + i) * MC + c];
 #pragma unroll
-            for (int c = 0; c < MC; ++c) v.Ynear[(long long)(row0 + rbase + i) * S + c0 + c] = acc[c];
+            for (int c = 0; c < MC; ++c) part[(long long)(rbase + i) * S + c0 + c] = acc[c];
         }
     }
 }
@@ -228,38 +262,62 @@ __global__ void __launch_bounds__(kThreads) upsweep_leaf_kernel(DevView<T> v, in
     }
 }
 
-// One mode-k product of the tensor z (p^d x MC, little-endian) with a p x p matrix in shared
-// memory: out[.., a, ..] = sum_b A(a, b) z[.., b, ..], A(a, b) = E[b p + a] (transposed, up-sweep)
-// or E[a p + b] (down-sweep).
+// Loads CT consecutive values starting at p (p aligned to CT * sizeof(T) when CT is 2 or 4).
+template <typename T, int CT>
+__device__ __forceinline__ void load_ct(const T* p, T (&x)[CT]) {
+#pragma unroll
+    for (int c = 0; c < CT; ++c) x[c] = p[c];
+}
+template <>
+__device__ __forceinline__ void load_ct<float, 4>(const float* p, float (&x)[4]) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void load_ct<double, 4>(const double* p, double (&x)[4]) {
+    const double2 v0 = reinterpret_cast<const double2*>(p)[0];
+    const double2 v1 = reinterpret_cast<const double2*>(p)[1];
+    x[0] = v0.x; x[1] = v0.y; x[2] = v1.x; x[3] = v1.y;
+}
+
+// One mode-k product of the tensor z (p^d x MC, little-endian) with a p x p matrix:
+// out[.., a, ..] = sum_b A(a, b) z[.., b, ..] with A(a, b) = E[b p + a] (transposed, up-sweep)
+// or E[a p + b] (down-sweep).  Each thread owns whole fibres along mode k: it loads the p
+// inputs of a fibre once and writes its p outputs.
 template <typename T, int MC>
-__device__ void mode_product(const T* z, T* out, const T* E, int p, int d, int k, bool transpose) {
-    int stride = 1;
-    for (int q = 0; q < k; ++q) stride *= p;
-    int PD = 1;
-    for (int q = 0; q < d; ++q) PD *= p;
-    for (int e = threadIdx.x; e < PD * MC; e += blockDim.x) {
-        const int I = e / MC, c = e % MC;
-        const int a = (I / stride) % p;
-        const int base = I - a * stride;
-        T s = T(0);
-        for (int b = 0; b < p; ++b) {
-            const T m = transpose ? E[b * p + a] : E[a * p + b];
-            s += m * z[(base + b * stride) * MC + c];
+__device__ void mode_product(const T* z, T* out, const T* E, int p, int PD, int stride, bool transpose,
+                             bool accumulate) {
+    const int nfib = PD / p;
+    for (int e = threadIdx.x; e < nfib * MC; e += blockDim.x) {
+        const int c = e % MC, f = e / MC;
+        const int inner = f % stride, outer = f / stride;
+        const int base = inner + stride * p * outer;
+        T in[kMaxPs];
+#pragma unroll
+        for (int b = 0; b < kMaxPs; ++b)
+            if (b < p) in[b] = z[(base + b * stride) * MC + c];
+        for (int a = 0; a < p; ++a) {
+            T s = T(0);
+#pragma unroll
+            for (int b = 0; b < kMaxPs; ++b)
+                if (b < p) s += (transpose ? E[b * p + a] : E[a * p + b]) * in[b];
+            T* o = out + (base + a * stride) * MC + c;
+            if (accumulate) *o += s;
+            else *o = s;
         }
-        out[e] = s;
     }
 }
 
-// Up-sweep (transpose = true): xhat_s = sum over children s' of (E_{s',d} (x) .. (x) E_{s',1})^T xhat_s'.
-// Down-sweep (transpose = false): yhat_s' += (E_{s',d} (x) .. (x) E_{s',1}) yhat_s for each child s'.
-// FastKron (§3.6.3) applies the Kronecker factors one mode at a time.  One CTA per node of `level`.
+// Up-sweep (up = true): xhat_s = sum over children s' of (E_{s',d} (x) .. (x) E_{s',1})^T xhat_s'.
+// Down-sweep (up = false): yhat_s' += (E_{s',d} (x) .. (x) E_{s',1}) yhat_s for each child s'.
+// FastKron (§3.6.3) applies the Kronecker factors one mode at a time.  One CTA per node.
 template <typename T, int MC>
 __global__ void __launch_bounds__(kThreads) transfer_kernel(DevView<T> v, const int* nodes, int S, int c0,
                                                             bool up, T* src_all, T* dst_all) {
     extern __shared__ unsigned char smem_raw[];
     const int PD = v.PD, p = v.p_s, d = v.d;
-    T* sE = reinterpret_cast<T*>(smem_raw);  // 2 p^2
-    T* b0 = sE + 2 * p * p;
+    T* sE = reinterpret_cast<T*>(smem_raw);  // 2 p^2, padded to 4
+    T* b0 = sE + ((2 * p * p + 3) & ~3);
     T* b1 = b0 + (size_t)PD * MC;
     T* sacc = b1 + (size_t)PD * MC;
     for (int e = threadIdx.x; e < 2 * p * p; e += blockDim.x) sE[e] = v.E[e];
@@ -275,13 +333,15 @@ __global__ void __launch_bounds__(kThreads) transfer_kernel(DevView<T> v, const 
                 b0[e] = src_all[((long long)ch * PD + e / MC) * S + c0 + e % MC];
             T* in = b0;
             T* out = b1;
+            int stride = 1;
             for (int k = 0; k < d; ++k) {
                 __syncthreads();
-                mode_product<T, MC>(in, out, sE + ((halves >> k) & 1) * p * p, p, d, k, true);
+                const bool last = (k == d - 1);
+                mode_product<T, MC>(in, last ? sacc : out, sE + ((halves >> k) & 1) * p * p, p, PD, stride, true,
+                                    last);
                 T* t = in; in = out; out = t;
+                stride *= p;
             }
-            __syncthreads();
-            for (int e = threadIdx.x; e < PD * MC; e += blockDim.x) sacc[e] += in[e];
         }
         __syncthreads();
         for (int e = threadIdx.x; e < PD * MC; e += blockDim.x)
@@ -295,11 +355,13 @@ __global__ void __launch_bounds__(kThreads) transfer_kernel(DevView<T> v, const 
             const int halves = v.node_halves[ch];
             T* in = sacc;
             T* out = b0;
+            int stride = 1;
             for (int k = 0; k < d; ++k) {
                 __syncthreads();
-                mode_product<T, MC>(in, out, sE + ((halves >> k) & 1) * p * p, p, d, k, false);
+                mode_product<T, MC>(in, out, sE + ((halves >> k) & 1) * p * p, p, PD, stride, false, false);
                 in = out;
                 out = (out == b0) ? b1 : b0;
+                stride *= p;
             }
             __syncthreads();
             for (int e = threadIdx.x; e < PD * MC; e += blockDim.x)
@@ -308,83 +370,210 @@ __global__ void __launch_bounds__(kThreads) transfer_kernel(DevView<T> v, const 
     }
 }
 
+// Split of the contraction dimension K so that narrow steps still occupy the CTA.
+__device__ __forceinline__ int split_for(int items, int K) {
+    if (items >= kThreads || K < 16) return 1;
+    int s = (kThreads + items - 1) / items;
+    return min(s, K / 8);
+}
+
+// Right-core step of the chain: out[A + a s'][c] = sum_{K < p r_in} in[A + a K][c] G[s' + r_out K].
+// Work item = (A, quad of s', CT columns); the K loop is split when there are few items.
+template <typename T, int MC>
+__device__ void chain_rstep(const T* in, T* out, const T* __restrict__ G, int a, int K, int rout) {
+    constexpr int CT = MC < 4 ? MC : 4, CQ = MC / CT;
+    const int SQ = (rout + 3) >> 2;
+    const int items = a * SQ * CQ;
+    const int split = split_for(items, K);
+    const int kc = (K + split - 1) / split;
+    if (split > 1) {
+        for (int e = threadIdx.x; e < a * rout * MC; e += blockDim.x) out[e] = T(0);
+        __syncthreads();
+    }
+    for (int w = threadIdx.x; w < items * split; w += blockDim.x) {
+        const int item = w % items, ks = w / items;
+        const int cq = item % CQ, rest = item / CQ;
+        const int A = rest % a, sq = rest / a;
+        const int k0 = ks * kc, k1 = min(K, k0 + kc);
+        const int nso = min(4, rout - 4 * sq);
+        T acc[4][CT];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int c = 0; c < CT; ++c) acc[j][c] = T(0);
+        const T* ip = in + (long long)A * MC + cq * CT;
+        const T* gp = G + 4 * sq;
+        for (int k = k0; k < k1; ++k) {
+            T x[CT];
+            load_ct<T, CT>(ip + (long long)a * k * MC, x);
+            const T* gk = gp + (long long)rout * k;
+            T g[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) g[j] = (j < nso) ? __ldg(gk + j) : T(0);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int c = 0; c < CT; ++c) acc[j][c] += g[j] * x[c];
+        }
+        for (int j = 0; j < nso; ++j) {
+            T* o = out + (long long)(A + a * (4 * sq + j)) * MC + cq * CT;
+#pragma unroll
+            for (int c = 0; c < CT; ++c) {
+                if (split > 1) atomicAdd(o + c, acc[j][c]);
+                else o[c] = acc[j][c];
+            }
+        }
+    }
+}
+
+// Left-core (and H) step: out[row + rows B][c] = sum_{s < r_in} G[row + rows s] in[s + r_in B][c].
+// Work item = (quad of rows, B, CT columns).
+template <typename T, int MC>
+__device__ void chain_lstep(const T* in, T* out, const T* __restrict__ G, int rows, int rin, int bsz) {
+    constexpr int CT = MC < 4 ? MC : 4, CQ = MC / CT;
+    const int RQ = (rows + 3) >> 2;
+    const int items = RQ * bsz * CQ;
+    const int split = split_for(items, rin);
+    const int kc = (rin + split - 1) / split;
+    if (split > 1) {
+        for (int e = threadIdx.x; e < rows * bsz * MC; e += blockDim.x) out[e] = T(0);
+        __syncthreads();
+    }
+    for (int w = threadIdx.x; w < items * split; w += blockDim.x) {
+        const int item = w % items, ks = w / items;
+        const int cq = item % CQ, rest = item / CQ;
+        const int B = rest % bsz, rq = rest / bsz;
+        const int k0 = ks * kc, k1 = min(rin, k0 + kc);
+        const int nr = min(4, rows - 4 * rq);
+        T acc[4][CT];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int c = 0; c < CT; ++c) acc[j][c] = T(0);
+        const T* ip = in + (long long)rin * B * MC + cq * CT;
+        const T* gp = G + 4 * rq;
+        for (int k = k0; k < k1; ++k) {
+            T x[CT];
+            load_ct<T, CT>(ip + (long long)k * MC, x);
+            const T* gk = gp + (long long)rows * k;
+            T g[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) g[j] = (j < nr) ? __ldg(gk + j) : T(0);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int c = 0; c < CT; ++c) acc[j][c] += g[j] * x[c];
+        }
+        for (int j = 0; j < nr; ++j) {
+            T* o = out + (long long)(4 * rq + j + rows * B) * MC + cq * CT;
+#pragma unroll
+            for (int c = 0; c < CT; ++c) {
+                if (split > 1) atomicAdd(o + c, acc[j][c]);
+                else o[c] = acc[j][c];
+            }
+        }
+    }
+}
+
 // Multiplication stage of Alg. "Modified H^2-Matrix MVM": for every far block (s, t) with
 // compressed class k, z = xhat_t; d right-core steps z <- reshape(z, [p^{d-i-1}, p r]) G^{1}^T;
-// z <- H_k z; d left-core steps z <- G^{2} reshape(z, [r, p^i]); yhat_s += z.  One CTA per target.
-template <typename T, int MC>
+// z <- H_k z; d - 1 left-core steps z <- G^{2} reshape(z, [r, p^i]); the last left-core step
+// (G_1, r_0 = 1) is accumulated into registers, so yhat_s is written once.  One CTA per target.
+template <typename T, int MC, int NI>
 __global__ void __launch_bounds__(kThreads) coupling_kernel(DevView<T> v, int S, int c0) {
     extern __shared__ unsigned char smem_raw[];
+    constexpr int CT = MC < 4 ? MC : 4, CQ = MC / CT;
     const int PD = v.PD, p = v.p_s, d = v.d, Delta = v.Delta;
-    T* yacc = reinterpret_cast<T*>(smem_raw);
-    T* z0 = yacc + (size_t)PD * MC;
+    T* z0 = reinterpret_cast<T*>(smem_raw);
     T* z1 = z0 + (size_t)PD * MC;
     const int ti = blockIdx.x;
     const int s = v.far_targets[ti];
-    for (int e = threadIdx.x; e < PD * MC; e += blockDim.x) yacc[e] = T(0);
+    const int RQ0 = (p + 3) >> 2;
+    const int bsz_last = PD / p;
+    const int items_last = RQ0 * bsz_last * CQ;
+    T yreg[NI][4][CT];
+#pragma unroll
+    for (int u = 0; u < NI; ++u)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int c = 0; c < CT; ++c) yreg[u][j][c] = T(0);
     for (int fb = v.far_by_target[ti]; fb < v.far_by_target[ti + 1]; ++fb) {
         const int t = v.fb_t[fb], key = v.fb_key[fb];
         const int* rk = v.key_ranks + (size_t)key * (Delta + 1);
         const long long* off = v.key_off + (size_t)key * Delta;
         __syncthreads();
-        for (int e = threadIdx.x; e < PD * MC; e += blockDim.x)
-            z0[e] = v.xhat[((long long)t * PD + e / MC) * S + c0 + e % MC];
+        {
+            const T* src = v.xhat + (long long)t * PD * S + c0;
+            for (int e = threadIdx.x; e < PD * CQ; e += blockDim.x) {
+                const int I = e / CQ, cq = e % CQ;
+                T x[CT];
+                load_ct<T, CT>(src + (long long)I * S + cq * CT, x);
+#pragma unroll
+                for (int c = 0; c < CT; ++c) z0[I * MC + cq * CT + c] = x[c];
+            }
+        }
         T* in = z0;
         T* out = z1;
-        // right cores G_{Delta}, ..., G_{Delta-d+1}: out[A + a s'] = sum_K in[A + a K] G[s' + r' K]
         int a = PD / p;
-        for (int i = 0; i < d; ++i) {
-            const int core = Delta - 1 - i;  // 0-based
-            const int rin = rk[core + 1], rout = rk[core];
-            const int K = p * rin;
-            const T* G = v.far_cores + off[core];
+        for (int i = 0; i < d; ++i) {  // right cores G_Delta, ..., G_{Delta-d+1}
+            const int core = Delta - 1 - i;
             __syncthreads();
-            for (int e = threadIdx.x; e < a * rout * MC; e += blockDim.x) {
-                const int c = e % MC, q = e / MC;
-                const int A = q % a, so = q / a;
-                T acc = T(0);
-                for (int kk = 0; kk < K; ++kk) acc += in[(A + a * kk) * MC + c] * G[so + rout * kk];
-                out[e] = acc;
-            }
+            chain_rstep<T, MC>(in, out, v.far_cores + off[core], a, p * rk[core + 1], rk[core]);
             T* tmp = in; in = out; out = tmp;
             a /= p;
         }
-        // H step: out[x] = sum_y H[x + r_d y] in[y]
-        {
-            const int ra = rk[d], rb = rk[d + 1];
-            const T* H = v.H + v.key_hoff[key];
-            __syncthreads();
-            for (int e = threadIdx.x; e < ra * MC; e += blockDim.x) {
-                const int c = e % MC, x = e / MC;
-                T acc = T(0);
-                for (int y = 0; y < rb; ++y) acc += H[x + ra * y] * in[y * MC + c];
-                out[e] = acc;
-            }
-            T* tmp = in; in = out; out = tmp;
-        }
-        // left cores G_d, ..., G_1: out[(s' + r' I) + r' p B] = sum_S G[s' + r' I + r' p S] in[S + r B]
+        __syncthreads();
+        chain_lstep<T, MC>(in, out, v.H + v.key_hoff[key], rk[d], rk[d + 1], 1);  // H_k
+        { T* tmp = in; in = out; out = tmp; }
         int bsz = 1;
-        for (int i = 0; i < d; ++i) {
+        for (int i = 0; i + 1 < d; ++i) {  // left cores G_d, ..., G_2
             const int core = d - 1 - i;
-            const int rin = rk[core + 1], rout = rk[core];
-            const T* G = v.far_cores + off[core];
-            const int rows = rout * p;
             __syncthreads();
-            for (int e = threadIdx.x; e < rows * bsz * MC; e += blockDim.x) {
-                const int c = e % MC, q = e / MC;
-                const int row = q % rows, B = q / rows;
-                T acc = T(0);
-                for (int ss = 0; ss < rin; ++ss) acc += G[row + rows * ss] * in[(ss + rin * B) * MC + c];
-                out[e] = acc;
-            }
+            chain_lstep<T, MC>(in, out, v.far_cores + off[core], rk[core] * p, rk[core + 1], bsz);
             T* tmp = in; in = out; out = tmp;
             bsz *= p;
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < PD * MC; e += blockDim.x) yacc[e] += in[e];
+        // last left core G_1 (1 x p x r_1): fixed items per thread, accumulated in registers
+        {
+            const T* G = v.far_cores + off[0];
+            const int rin = rk[1];
+#pragma unroll
+            for (int u = 0; u < NI; ++u) {
+                const int item = threadIdx.x + u * kThreads;
+                if (item < items_last) {
+                    const int cq = item % CQ, rest = item / CQ;
+                    const int B = rest % bsz_last, rq = rest / bsz_last;
+                    const int nr = min(4, p - 4 * rq);
+                    const T* ip = in + (long long)rin * B * MC + cq * CT;
+                    for (int k = 0; k < rin; ++k) {
+                        T x[CT];
+                        load_ct<T, CT>(ip + (long long)k * MC, x);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const T g = (j < nr) ? __ldg(G + 4 * rq + j + p * k) : T(0);
+#pragma unroll
+                            for (int c = 0; c < CT; ++c) yreg[u][j][c] += g * x[c];
+                        }
+                    }
+                }
+            }
+        }
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < PD * MC; e += blockDim.x)
-        v.yhat[((long long)s * PD + e / MC) * S + c0 + e % MC] = yacc[e];
+    T* dst = v.yhat + (long long)s * PD * S + c0;
+#pragma unroll
+    for (int u = 0; u < NI; ++u) {
+        const int item = threadIdx.x + u * kThreads;
+        if (item < items_last) {
+            const int cq = item % CQ, rest = item / CQ;
+            const int B = rest % bsz_last, rq = rest / bsz_last;
+            const int nr = min(4, p - 4 * rq);
+            for (int j = 0; j < nr; ++j)
+#pragma unroll
+                for (int c = 0; c < CT; ++c) dst[(long long)(4 * rq + j + p * B) * S + cq * CT + c] = yreg[u][j][c];
+        }
+    }
 }
 
 // H format far field (§4.5): y_s += S_b (H_k (T_b^T x_t)) for every far block of target s.
@@ -451,8 +640,8 @@ __global__ void __launch_bounds__(kThreads) far_h_kernel(DevView<T> v, int S, in
         dst[(long long)(row0 + e / MC) * S + c0 + e % MC] = ys[e];
 }
 
-// Y[perm[i] + c ldy] = Y_near[i][c] + (U_s yhat_s)[i][c] (H^2, leaf stage of FastBackward)
-//                    or Y_near[i][c] + sum over levels of y_far (H).  One CTA per leaf.
+// Y[perm[i] + c ldy] = sum of the leaf's near partials + (U_s yhat_s)[i][c] (H^2, leaf stage of
+// FastBackward) or + sum over levels of y_far (H).  One CTA per leaf.
 template <typename T, int MC>
 __global__ void __launch_bounds__(kThreads) combine_kernel(DevView<T> v, T* __restrict__ Y, long long ldy,
                                                            int m, int S, int c0, int h2) {
@@ -471,7 +660,10 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(DevView<T> v, T* __re
         const long long row = row0 + i;
         T acc[MC];
 #pragma unroll
-        for (int c = 0; c < MC; ++c) acc[c] = v.Ynear[row * S + c0 + c];
+        for (int c = 0; c < MC; ++c) acc[c] = T(0);
+        for (int it = v.items_by_leaf[leaf]; it < v.items_by_leaf[leaf + 1]; ++it)
+#pragma unroll
+            for (int c = 0; c < MC; ++c) acc[c] += v.partials[((long long)it * v.part_stride + i) * S + c0 + c];
         if (h2) {
             const T* u = v.U + row * d * ps;
             for (int I = 0; I < PD; ++I) {
@@ -523,7 +715,7 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
         size_t smem = ((size_t)maxleaf * MC + (size_t)kThreads * MC + kMaxNearRank) * sizeof(T);
         set_smem<T, MC>((const void*)near_kernel<T, MC>, smem);
         ProfScope ps(h, 2, stream);
-        near_kernel<T, MC><<<nleaves, kThreads, smem, stream>>>(v, S, c0, maxleaf);
+        near_kernel<T, MC><<<std::max(1, v.n_items), kThreads, smem, stream>>>(v, S, c0, maxleaf);
         PH_LAUNCH("near_kernel");
     }
     if (!plan.far_targets.empty()) {
@@ -535,7 +727,7 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
                     upsweep_leaf_kernel<T, MC><<<nleaves, kThreads, sm_leaf, h->side>>>(v, S, c0);
                 }
                 PH_LAUNCH("upsweep_leaf_kernel");
-                size_t sm_tr = ((size_t)2 * v.p_s * v.p_s + 3 * (size_t)PD * MC) * sizeof(T);
+                size_t sm_tr = ((size_t)((2 * v.p_s * v.p_s + 3) & ~3) + 3 * (size_t)PD * MC) * sizeof(T);
                 set_smem<T, MC>((const void*)transfer_kernel<T, MC>, sm_tr);
                 for (int l = plan.depth - 1; l >= h->min_far_level; --l) {
                     int cnt = h->level_nodes_off[l + 1] - h->level_nodes_off[l];
@@ -545,11 +737,25 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
                         v, h->d_level_nodes + h->level_nodes_off[l], S, c0, true, v.xhat, v.xhat);
                     PH_LAUNCH("transfer_kernel(up)");
                 }
-                size_t sm_c = 3 * (size_t)PD * MC * sizeof(T);
-                set_smem<T, MC>((const void*)coupling_kernel<T, MC>, sm_c);
+                size_t sm_c = 2 * (size_t)PD * MC * sizeof(T);
+                const int CQ = MC < 4 ? 1 : MC / 4;
+                const int items_last = ((v.p_s + 3) / 4) * (PD / v.p_s) * CQ;
+                const int ni = (items_last + kThreads - 1) / kThreads;
                 {
                     ProfScope ps(h, 5, h->side);
-                    coupling_kernel<T, MC><<<(int)plan.far_targets.size(), kThreads, sm_c, h->side>>>(v, S, c0);
+                    const int nt = (int)plan.far_targets.size();
+                    if (ni <= 1) {
+                        set_smem<T, MC>((const void*)coupling_kernel<T, MC, 1>, sm_c);
+                        coupling_kernel<T, MC, 1><<<nt, kThreads, sm_c, h->side>>>(v, S, c0);
+                    } else if (ni <= 2) {
+                        set_smem<T, MC>((const void*)coupling_kernel<T, MC, 2>, sm_c);
+                        coupling_kernel<T, MC, 2><<<nt, kThreads, sm_c, h->side>>>(v, S, c0);
+                    } else if (ni <= 4) {
+                        set_smem<T, MC>((const void*)coupling_kernel<T, MC, 4>, sm_c);
+                        coupling_kernel<T, MC, 4><<<nt, kThreads, sm_c, h->side>>>(v, S, c0);
+                    } else {
+                        throw Error(PH_ERR_UNSUPPORTED, "p_s^d too large for the coupling kernel");
+                    }
                 }
                 PH_LAUNCH("coupling_kernel");
                 for (int l = h->min_far_level; l < plan.depth; ++l) {
