@@ -138,6 +138,31 @@ ph_status ph_matvec(ph_handle* h, const void* X, long ldx, int m, void* Y, long 
 ph_status ph_matvec_host(ph_handle* h, const void* X, long ldx, int m, void* Y, long ldy,
                          void* stream);
 
+/* ph_matvec for callers that cannot allocate device memory.  The paper has no
+ * counterpart; this is a service of the library.  Some callers may not call
+ * cudaMalloc at the time they apply the matrix: code that runs while a CUDA graph
+ * is being captured, processes held to a fixed device-memory budget, or host
+ * applications that own every device allocation themselves.  ph_matvec
+ * allocates its per-call workspace on first use; this variant allocates nothing
+ * and calls no allocating library routine.  Its workspace lives in one
+ * file-scope device array of 16 MiB that every GPU loading the library holds
+ * until the process exits.
+ *   Arguments, layout and result are those of ph_matvec.
+ *   Sizes: the workspace needed is about 4 (float) or 8 (double) bytes times
+ *     m_pad * (n + near work items * largest leaf + 2 * tree nodes * p_s^d)
+ *     (H^2) or m_pad * (n + items * largest leaf + far levels * n) (H), m_pad =
+ *     m rounded up to 1, 2, 4, 8 or a multiple of 16; above 16 MiB the call
+ *     returns PH_ERR_INVALID_ARG with the needed size in ph_last_error and
+ *     computes nothing.
+ *   Set-up: the first call on a device looks the array's device address up
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   Sharing: every call uses the same array, which keeps the last call's
+ *     contents (the call clears what must start at zero).  Calls whose work
+ *     overlaps on the GPU, from any handle or stream, race on the array. */
+ph_status ph_matvec_noalloc(ph_handle* h, const void* X, long ldx, int m, void* Y, long ldy,
+                            void* stream);
+
 /* Fill *info with sizes and counts of a built handle. */
 ph_status ph_get_info(const ph_handle* h, ph_info* info);
 

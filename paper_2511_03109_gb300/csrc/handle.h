@@ -166,6 +166,9 @@ ph_status online_instantiate(ph_handle* h, const double* theta, cudaStream_t str
 ph_status online_matvec(ph_handle* h, const void* X, long ldx, int m, void* Y, long ldy,
                         cudaStream_t stream);
 void ensure_workspace(ph_handle* h, int m);
+// ph_matvec with the caller's device views (their workspace pointers replace the handle's).
+ph_status online_matvec_view(ph_handle* h, DevView<float>& vf, DevView<double>& vd, const void* X, long ldx, int m,
+                             void* Y, long ldy, cudaStream_t stream);
 void refresh_views(ph_handle* h);
 void free_device(ph_handle* h);
 void* dev_alloc(ph_handle* h, size_t bytes);  // throws ph::Error(PH_ERR_OOM) on failure

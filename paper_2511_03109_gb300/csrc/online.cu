@@ -871,6 +871,13 @@ ph_status online_instantiate(ph_handle* h, const double* theta, cudaStream_t str
     return PH_OK;
 }
 
+ph_status online_matvec_view(ph_handle* h, DevView<float>& vf, DevView<double>& vd, const void* X, long ldx, int m,
+                             void* Y, long ldy, cudaStream_t stream) {
+    if (h->opts.prec == PH_FP32)
+        return matvec_typed<float>(h, vf, (const float*)X, ldx, m, (float*)Y, ldy, stream);
+    return matvec_typed<double>(h, vd, (const double*)X, ldx, m, (double*)Y, ldy, stream);
+}
+
 ph_status online_matvec(ph_handle* h, const void* X, long ldx, int m, void* Y, long ldy, cudaStream_t stream) {
     ensure_workspace(h, m);
     if (h->opts.prec == PH_FP32)

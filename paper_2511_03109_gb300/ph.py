@@ -72,6 +72,7 @@ _SIGS = {
     "ph_instantiate": (C.c_int, [_H, C.POINTER(C.c_double), _P]),
     "ph_matvec": (C.c_int, [_H, _P, C.c_long, C.c_int, _P, C.c_long, _P]),
     "ph_matvec_host": (C.c_int, [_H, _P, C.c_long, C.c_int, _P, C.c_long, _P]),
+    "ph_matvec_noalloc": (C.c_int, [_H, _P, C.c_long, C.c_int, _P, C.c_long, _P]),
     "ph_get_info": (C.c_int, [_H, C.POINTER(Info)]),
     "ph_save": (C.c_int, [_H, C.c_char_p]),
     "ph_load": (C.c_int, [C.c_char_p, C.c_int, C.POINTER(_H)]),
@@ -178,6 +179,11 @@ class ParametricMatrix:
     def matvec_ptr(self, x_ptr, ldx, m, y_ptr, ldy, stream=0):
         return check(ph_matvec(self.h, C.c_void_p(x_ptr), ldx, m, C.c_void_p(y_ptr), ldy,
                                C.c_void_p(stream)), self.h)
+
+    def matvec_noalloc_ptr(self, x_ptr, ldx, m, y_ptr, ldy, stream=0):
+        """ph_matvec_noalloc: same result as matvec_ptr, workspace in the library's static array."""
+        return check(ph_matvec_noalloc(self.h, C.c_void_p(x_ptr), ldx, m, C.c_void_p(y_ptr), ldy,
+                                       C.c_void_p(stream)), self.h)
 
     def matvec_host_ptr(self, x_ptr, ldx, m, y_ptr, ldy, stream=0):
         return check(ph_matvec_host(self.h, C.c_void_p(x_ptr), ldx, m, C.c_void_p(y_ptr), ldy,
