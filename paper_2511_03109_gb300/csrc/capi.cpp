@@ -187,6 +187,28 @@ void refresh_views(ph_handle* h) {
         }
         h->items_by_leaf[l + 1] = (int)h->item_first.size();
     }
+    // longest intermediate of the coupling chain kept in shared memory (all steps but the
+    // first input and the last output): right-core outputs a r_out, H output, left-core outputs
+    h->coupling_zmax = 1;
+    if (!plan.key_rep.empty()) {
+        const int d = plan.d, p = h->opts.p_s, D = h->Delta;
+        for (size_t k = 0; k < plan.key_rep.size(); ++k) {
+            const int* rk = &h->key_ranks[k * (D + 1)];
+            int a = h->PD / p;
+            for (int i = 0; i < d; ++i) {
+                h->coupling_zmax = std::max(h->coupling_zmax, a * rk[D - 1 - i]);
+                a /= p;
+            }
+            h->coupling_zmax = std::max(h->coupling_zmax, rk[d]);
+            int bsz = 1;
+            for (int i = 0; i + 1 < d; ++i) {
+                const int core = d - 1 - i;
+                h->coupling_zmax = std::max(h->coupling_zmax, rk[core] * p * bsz);
+                bsz *= p;
+            }
+        }
+        h->coupling_zmax = (h->coupling_zmax + 3) & ~3;
+    }
     std::vector<int> fbt = plan.far_by_target;
     if (fbt.empty()) fbt.push_back(0);
     put(plan.perm);                 // 0

@@ -135,6 +135,7 @@ struct ph_handle {
     void* d_partials = nullptr;
     std::vector<int> item_first, item_count, item_leaf, items_by_leaf;
     int max_leaf = 1;
+    int coupling_zmax = 1;                      // longest shared-memory intermediate of the TT chain
     DeviceBuffer ws;
     DeviceBuffer host_stage_x, host_stage_y;    // device staging for ph_matvec_host
     int n_far_levels = 0;

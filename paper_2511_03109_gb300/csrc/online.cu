@@ -114,7 +114,7 @@ __global__ void gather_kernel(DevView<T> v, const T* __restrict__ X, long long l
 // memory and the item's partial sum Y_s^{item} is written once; combine_kernel adds the
 // partials of a leaf in a fixed order.
 template <typename T, int MC>
-__global__ void __launch_bounds__(kThreads) near_kernel(DevView<T> v, int S, int c0, int maxleaf) {
+__global__ void __launch_bounds__(kThreads, 3) near_kernel(DevView<T> v, int S, int c0, int maxleaf) {
     extern __shared__ unsigned char smem_raw[];
     constexpr int RK = 8;                                 // ranks up to RK use the unrolled path
     T* xs = reinterpret_cast<T*>(smem_raw);              // maxleaf x MC
@@ -377,10 +377,12 @@ __device__ __forceinline__ int split_for(int items, int K) {
     return min(s, K / 8);
 }
 
-// Right-core step of the chain: out[A + a s'][c] = sum_{K < p r_in} in[A + a K][c] G[s' + r_out K].
+// Right-core step of the chain: out[A + a s'][c] = sum_{K < p r_in} in[(A + a K) istride + c] G[s' + r_out K]
+// (istride = MC for shared-memory input, the workspace row stride for the first step, which
+// reads xhat_t straight from global memory).
 // Work item = (A, quad of s', CT columns); the K loop is split when there are few items.
 template <typename T, int MC>
-__device__ void chain_rstep(const T* in, T* out, const T* __restrict__ G, int a, int K, int rout) {
+__device__ void chain_rstep(const T* in, int istride, T* out, const T* __restrict__ G, int a, int K, int rout) {
     constexpr int CT = MC < 4 ? MC : 4, CQ = MC / CT;
     const int SQ = (rout + 3) >> 2;
     const int items = a * SQ * CQ;
@@ -401,11 +403,11 @@ __device__ void chain_rstep(const T* in, T* out, const T* __restrict__ G, int a,
         for (int j = 0; j < 4; ++j)
 #pragma unroll
             for (int c = 0; c < CT; ++c) acc[j][c] = T(0);
-        const T* ip = in + (long long)A * MC + cq * CT;
+        const T* ip = in + (long long)A * istride + cq * CT;
         const T* gp = G + 4 * sq;
         for (int k = k0; k < k1; ++k) {
             T x[CT];
-            load_ct<T, CT>(ip + (long long)a * k * MC, x);
+            load_ct<T, CT>(ip + (long long)a * k * istride, x);
             const T* gk = gp + (long long)rout * k;
             T g[4];
 #pragma unroll
@@ -476,17 +478,19 @@ __device__ void chain_lstep(const T* in, T* out, const T* __restrict__ G, int ro
 }
 
 // Multiplication stage of Alg. "Modified H^2-Matrix MVM": for every far block (s, t) with
-// compressed class k, z = xhat_t; d right-core steps z <- reshape(z, [p^{d-i-1}, p r]) G^{1}^T;
-// z <- H_k z; d - 1 left-core steps z <- G^{2} reshape(z, [r, p^i]); the last left-core step
-// (G_1, r_0 = 1) is accumulated into registers, so yhat_s is written once.  One CTA per target.
+// compressed class k, z = xhat_t; d right-core steps z <- reshape(z, [p^{d-i-1}, p r]) G^{1}^T
+// (the first reads xhat_t from global memory); z <- H_k z; d - 1 left-core steps
+// z <- G^{2} reshape(z, [r, p^i]); the last left-core step (G_1, r_0 = 1) is accumulated in
+// registers.  The far blocks of a target are split over `nsplit` CTAs whose sums meet in
+// yhat_s through atomic adds (yhat is cleared before the launch).
 template <typename T, int MC, int NI>
-__global__ void __launch_bounds__(kThreads) coupling_kernel(DevView<T> v, int S, int c0) {
+__global__ void __launch_bounds__(kThreads, 3) coupling_kernel(DevView<T> v, int S, int c0, int zmax, int nsplit) {
     extern __shared__ unsigned char smem_raw[];
     constexpr int CT = MC < 4 ? MC : 4, CQ = MC / CT;
     const int PD = v.PD, p = v.p_s, d = v.d, Delta = v.Delta;
     T* z0 = reinterpret_cast<T*>(smem_raw);
-    T* z1 = z0 + (size_t)PD * MC;
-    const int ti = blockIdx.x;
+    T* z1 = z0 + (size_t)zmax * MC;
+    const int ti = blockIdx.x / nsplit, part = blockIdx.x % nsplit;
     const int s = v.far_targets[ti];
     const int RQ0 = (p + 3) >> 2;
     const int bsz_last = PD / p;
@@ -498,28 +502,22 @@ __global__ void __launch_bounds__(kThreads) coupling_kernel(DevView<T> v, int S,
         for (int j = 0; j < 4; ++j)
 #pragma unroll
             for (int c = 0; c < CT; ++c) yreg[u][j][c] = T(0);
-    for (int fb = v.far_by_target[ti]; fb < v.far_by_target[ti + 1]; ++fb) {
+    const int fb0 = v.far_by_target[ti], fb1 = v.far_by_target[ti + 1];
+    const int per = (fb1 - fb0 + nsplit - 1) / nsplit;
+    const int my0 = fb0 + part * per, my1 = min(fb1, my0 + per);
+    for (int fb = my0; fb < my1; ++fb) {
         const int t = v.fb_t[fb], key = v.fb_key[fb];
         const int* rk = v.key_ranks + (size_t)key * (Delta + 1);
         const long long* off = v.key_off + (size_t)key * Delta;
-        __syncthreads();
-        {
-            const T* src = v.xhat + (long long)t * PD * S + c0;
-            for (int e = threadIdx.x; e < PD * CQ; e += blockDim.x) {
-                const int I = e / CQ, cq = e % CQ;
-                T x[CT];
-                load_ct<T, CT>(src + (long long)I * S + cq * CT, x);
-#pragma unroll
-                for (int c = 0; c < CT; ++c) z0[I * MC + cq * CT + c] = x[c];
-            }
-        }
-        T* in = z0;
-        T* out = z1;
+        const T* xin = v.xhat + (long long)t * PD * S + c0;
+        T* in = z1;
+        T* out = z0;
         int a = PD / p;
         for (int i = 0; i < d; ++i) {  // right cores G_Delta, ..., G_{Delta-d+1}
             const int core = Delta - 1 - i;
             __syncthreads();
-            chain_rstep<T, MC>(in, out, v.far_cores + off[core], a, p * rk[core + 1], rk[core]);
+            if (i == 0) chain_rstep<T, MC>(xin, S, out, v.far_cores + off[core], a, p * rk[core + 1], rk[core]);
+            else chain_rstep<T, MC>(in, MC, out, v.far_cores + off[core], a, p * rk[core + 1], rk[core]);
             T* tmp = in; in = out; out = tmp;
             a /= p;
         }
@@ -561,6 +559,7 @@ __global__ void __launch_bounds__(kThreads) coupling_kernel(DevView<T> v, int S,
             }
         }
     }
+    if (my0 >= my1) return;
     T* dst = v.yhat + (long long)s * PD * S + c0;
 #pragma unroll
     for (int u = 0; u < NI; ++u) {
@@ -571,7 +570,11 @@ __global__ void __launch_bounds__(kThreads) coupling_kernel(DevView<T> v, int S,
             const int nr = min(4, p - 4 * rq);
             for (int j = 0; j < nr; ++j)
 #pragma unroll
-                for (int c = 0; c < CT; ++c) dst[(long long)(4 * rq + j + p * B) * S + cq * CT + c] = yreg[u][j][c];
+                for (int c = 0; c < CT; ++c) {
+                    T* o = dst + (long long)(4 * rq + j + p * B) * S + cq * CT + c;
+                    if (nsplit > 1) atomicAdd(o, yreg[u][j][c]);
+                    else *o = yreg[u][j][c];
+                }
         }
     }
 }
@@ -737,22 +740,24 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
                         v, h->d_level_nodes + h->level_nodes_off[l], S, c0, true, v.xhat, v.xhat);
                     PH_LAUNCH("transfer_kernel(up)");
                 }
-                size_t sm_c = 2 * (size_t)PD * MC * sizeof(T);
+                const int zmax = h->coupling_zmax;
+                size_t sm_c = 2 * (size_t)zmax * MC * sizeof(T);
                 const int CQ = MC < 4 ? 1 : MC / 4;
                 const int items_last = ((v.p_s + 3) / 4) * (PD / v.p_s) * CQ;
                 const int ni = (items_last + kThreads - 1) / kThreads;
+                const int nsplit = 4;
                 {
                     ProfScope ps(h, 5, h->side);
-                    const int nt = (int)plan.far_targets.size();
+                    const int nt = (int)plan.far_targets.size() * nsplit;
                     if (ni <= 1) {
                         set_smem<T, MC>((const void*)coupling_kernel<T, MC, 1>, sm_c);
-                        coupling_kernel<T, MC, 1><<<nt, kThreads, sm_c, h->side>>>(v, S, c0);
+                        coupling_kernel<T, MC, 1><<<nt, kThreads, sm_c, h->side>>>(v, S, c0, zmax, nsplit);
                     } else if (ni <= 2) {
                         set_smem<T, MC>((const void*)coupling_kernel<T, MC, 2>, sm_c);
-                        coupling_kernel<T, MC, 2><<<nt, kThreads, sm_c, h->side>>>(v, S, c0);
+                        coupling_kernel<T, MC, 2><<<nt, kThreads, sm_c, h->side>>>(v, S, c0, zmax, nsplit);
                     } else if (ni <= 4) {
                         set_smem<T, MC>((const void*)coupling_kernel<T, MC, 4>, sm_c);
-                        coupling_kernel<T, MC, 4><<<nt, kThreads, sm_c, h->side>>>(v, S, c0);
+                        coupling_kernel<T, MC, 4><<<nt, kThreads, sm_c, h->side>>>(v, S, c0, zmax, nsplit);
                     } else {
                         throw Error(PH_ERR_UNSUPPORTED, "p_s^d too large for the coupling kernel");
                     }

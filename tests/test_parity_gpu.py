@@ -150,11 +150,12 @@ def test_host_entry_point_and_save_load(tmp_path):
     Xh = np.asfortranarray(X, dtype=np.float32)
     Yh = np.zeros_like(Xh)
     A.matvec_host_ptr(Xh.ctypes.data, n, 4, Yh.ctypes.data, n)
-    assert np.array_equal(Yh, ref.astype(np.float32))
+    # far-field partial sums meet through atomic adds, so runs agree to rounding, not bitwise
+    assert np.all(rel_err_rows(ref, Yh.astype(np.float64)) <= 1e-6)
     path = str(tmp_path / "a.ph")
     A.save(path)
     B = ph.ParametricMatrix.load(path)
     assert B.info()["near_bytes"] == A.info()["near_bytes"]
-    assert np.array_equal(device_apply(B, [0.6], X, "fp32"), ref)
+    assert np.all(rel_err_rows(ref, device_apply(B, [0.6], X, "fp32")) <= 1e-6)
     A.close()
     B.close()
