@@ -434,7 +434,13 @@ ph_status offline_build(ph_handle* h, const double* points, long n) {
     build_plan(points, n, d, o.l_max, o.eta, dedup, plan);
 
     PH_CUDA(cudaSetDevice(h->device));
-    PH_CUDA(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+    // the far-field chain is the longer path of a matvec: its stream gets the highest priority so
+    // its blocks are scheduled ahead of the near-field blocks that fill the remaining SM slots
+    {
+        int lo = 0, hi = 0;
+        PH_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        PH_CUDA(cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, hi));
+    }
     PH_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
     PH_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
 

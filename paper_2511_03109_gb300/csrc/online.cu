@@ -370,33 +370,59 @@ __global__ void __launch_bounds__(kThreads) transfer_kernel(DevView<T> v, const 
     }
 }
 
-// Split of the contraction dimension K so that narrow steps still occupy the CTA.
+// Row stride (in elements) of the chain's shared-memory buffers: MC values padded by 4 when
+// MC >= 8, so that row-strided 16-byte accesses of a quarter warp fall in distinct banks.
+template <int MC>
+struct ChainRow {
+    static constexpr int value = (MC >= 8) ? MC + 4 : MC;
+};
+
+// Stores CT consecutive values (one 16-byte store for float x 4).
+template <typename T, int CT>
+__device__ __forceinline__ void store_ct(T* p, const T (&x)[CT]) {
+#pragma unroll
+    for (int c = 0; c < CT; ++c) p[c] = x[c];
+}
+template <>
+__device__ __forceinline__ void store_ct<float, 4>(float* p, const float (&x)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
+}
+
+// Split of the contraction dimension over 1, 2, 4 or 8 adjacent lanes so that narrow steps still
+// occupy the CTA; the lanes' partial sums are combined with warp shuffles.
 __device__ __forceinline__ int split_for(int items, int K) {
-    if (items >= kThreads || K < 16) return 1;
-    int s = (kThreads + items - 1) / items;
-    return min(s, K / 8);
+    int s = 1;
+    while (s < 8 && items * s < kThreads && K >= 16 * s) s <<= 1;
+    return s;
+}
+
+template <typename T, int CT>
+__device__ __forceinline__ void reduce_split(T (&acc)[4][CT], int split) {
+    for (int o = 1; o < split; o <<= 1)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int c = 0; c < CT; ++c) acc[j][c] += __shfl_xor_sync(0xffffffffu, acc[j][c], o);
 }
 
 // Right-core step of the chain: out[A + a s'][c] = sum_{K < p r_in} in[(A + a K) istride + c] G[s' + r_out K]
-// (istride = MC for shared-memory input, the workspace row stride for the first step, which
-// reads xhat_t straight from global memory).
-// Work item = (A, quad of s', CT columns); the K loop is split when there are few items.
+// (istride = the shared row stride, or the workspace row stride for the first step, which
+// reads xhat_t straight from global memory).  Work item = (A, quad of s', CT columns); the
+// K loop is split over adjacent lanes when there are few items.
 template <typename T, int MC>
 __device__ void chain_rstep(const T* in, int istride, T* out, const T* __restrict__ G, int a, int K, int rout) {
-    constexpr int CT = MC < 4 ? MC : 4, CQ = MC / CT;
+    constexpr int CT = MC < 4 ? MC : 4, CQ = MC / CT, RS = ChainRow<MC>::value;
     const int SQ = (rout + 3) >> 2;
     const int items = a * SQ * CQ;
     const int split = split_for(items, K);
     const int kc = (K + split - 1) / split;
-    if (split > 1) {
-        for (int e = threadIdx.x; e < a * rout * MC; e += blockDim.x) out[e] = T(0);
-        __syncthreads();
-    }
-    for (int w = threadIdx.x; w < items * split; w += blockDim.x) {
-        const int item = w % items, ks = w / items;
+    const int total = ((items * split + 31) / 32) * 32;  // whole warps, so shuffles see every lane
+    for (int w = threadIdx.x; w < total; w += blockDim.x) {
+        const int ks = w % split, item = w / split;
+        const bool live = item < items;
         const int cq = item % CQ, rest = item / CQ;
         const int A = rest % a, sq = rest / a;
-        const int k0 = ks * kc, k1 = min(K, k0 + kc);
+        const int k0 = ks * kc, k1 = live ? min(K, k0 + kc) : k0;
         const int nso = min(4, rout - 4 * sq);
         T acc[4][CT];
 #pragma unroll
@@ -417,14 +443,9 @@ __device__ void chain_rstep(const T* in, int istride, T* out, const T* __restric
 #pragma unroll
                 for (int c = 0; c < CT; ++c) acc[j][c] += g[j] * x[c];
         }
-        for (int j = 0; j < nso; ++j) {
-            T* o = out + (long long)(A + a * (4 * sq + j)) * MC + cq * CT;
-#pragma unroll
-            for (int c = 0; c < CT; ++c) {
-                if (split > 1) atomicAdd(o + c, acc[j][c]);
-                else o[c] = acc[j][c];
-            }
-        }
+        if (split > 1) reduce_split<T, CT>(acc, split);
+        if (live && ks == 0)
+            for (int j = 0; j < nso; ++j) store_ct<T, CT>(out + (long long)(A + a * (4 * sq + j)) * RS + cq * CT, acc[j]);
     }
 }
 
@@ -432,31 +453,29 @@ __device__ void chain_rstep(const T* in, int istride, T* out, const T* __restric
 // Work item = (quad of rows, B, CT columns).
 template <typename T, int MC>
 __device__ void chain_lstep(const T* in, T* out, const T* __restrict__ G, int rows, int rin, int bsz) {
-    constexpr int CT = MC < 4 ? MC : 4, CQ = MC / CT;
+    constexpr int CT = MC < 4 ? MC : 4, CQ = MC / CT, RS = ChainRow<MC>::value;
     const int RQ = (rows + 3) >> 2;
     const int items = RQ * bsz * CQ;
     const int split = split_for(items, rin);
     const int kc = (rin + split - 1) / split;
-    if (split > 1) {
-        for (int e = threadIdx.x; e < rows * bsz * MC; e += blockDim.x) out[e] = T(0);
-        __syncthreads();
-    }
-    for (int w = threadIdx.x; w < items * split; w += blockDim.x) {
-        const int item = w % items, ks = w / items;
+    const int total = ((items * split + 31) / 32) * 32;
+    for (int w = threadIdx.x; w < total; w += blockDim.x) {
+        const int ks = w % split, item = w / split;
+        const bool live = item < items;
         const int cq = item % CQ, rest = item / CQ;
         const int B = rest % bsz, rq = rest / bsz;
-        const int k0 = ks * kc, k1 = min(rin, k0 + kc);
+        const int k0 = ks * kc, k1 = live ? min(rin, k0 + kc) : k0;
         const int nr = min(4, rows - 4 * rq);
         T acc[4][CT];
 #pragma unroll
         for (int j = 0; j < 4; ++j)
 #pragma unroll
             for (int c = 0; c < CT; ++c) acc[j][c] = T(0);
-        const T* ip = in + (long long)rin * B * MC + cq * CT;
+        const T* ip = in + (long long)rin * B * RS + cq * CT;
         const T* gp = G + 4 * rq;
         for (int k = k0; k < k1; ++k) {
             T x[CT];
-            load_ct<T, CT>(ip + (long long)k * MC, x);
+            load_ct<T, CT>(ip + (long long)k * RS, x);
             const T* gk = gp + (long long)rows * k;
             T g[4];
 #pragma unroll
@@ -466,14 +485,9 @@ __device__ void chain_lstep(const T* in, T* out, const T* __restrict__ G, int ro
 #pragma unroll
                 for (int c = 0; c < CT; ++c) acc[j][c] += g[j] * x[c];
         }
-        for (int j = 0; j < nr; ++j) {
-            T* o = out + (long long)(4 * rq + j + rows * B) * MC + cq * CT;
-#pragma unroll
-            for (int c = 0; c < CT; ++c) {
-                if (split > 1) atomicAdd(o + c, acc[j][c]);
-                else o[c] = acc[j][c];
-            }
-        }
+        if (split > 1) reduce_split<T, CT>(acc, split);
+        if (live && ks == 0)
+            for (int j = 0; j < nr; ++j) store_ct<T, CT>(out + (long long)(4 * rq + j + rows * B) * RS + cq * CT, acc[j]);
     }
 }
 
@@ -486,10 +500,10 @@ __device__ void chain_lstep(const T* in, T* out, const T* __restrict__ G, int ro
 template <typename T, int MC, int NI>
 __global__ void __launch_bounds__(kThreads, 3) coupling_kernel(DevView<T> v, int S, int c0, int zmax, int nsplit) {
     extern __shared__ unsigned char smem_raw[];
-    constexpr int CT = MC < 4 ? MC : 4, CQ = MC / CT;
+    constexpr int CT = MC < 4 ? MC : 4, CQ = MC / CT, RS = ChainRow<MC>::value;
     const int PD = v.PD, p = v.p_s, d = v.d, Delta = v.Delta;
     T* z0 = reinterpret_cast<T*>(smem_raw);
-    T* z1 = z0 + (size_t)zmax * MC;
+    T* z1 = z0 + (size_t)zmax * RS;
     const int ti = blockIdx.x / nsplit, part = blockIdx.x % nsplit;
     const int s = v.far_targets[ti];
     const int RQ0 = (p + 3) >> 2;
@@ -517,7 +531,7 @@ __global__ void __launch_bounds__(kThreads, 3) coupling_kernel(DevView<T> v, int
             const int core = Delta - 1 - i;
             __syncthreads();
             if (i == 0) chain_rstep<T, MC>(xin, S, out, v.far_cores + off[core], a, p * rk[core + 1], rk[core]);
-            else chain_rstep<T, MC>(in, MC, out, v.far_cores + off[core], a, p * rk[core + 1], rk[core]);
+            else chain_rstep<T, MC>(in, RS, out, v.far_cores + off[core], a, p * rk[core + 1], rk[core]);
             T* tmp = in; in = out; out = tmp;
             a /= p;
         }
@@ -544,10 +558,10 @@ __global__ void __launch_bounds__(kThreads, 3) coupling_kernel(DevView<T> v, int
                     const int cq = item % CQ, rest = item / CQ;
                     const int B = rest % bsz_last, rq = rest / bsz_last;
                     const int nr = min(4, p - 4 * rq);
-                    const T* ip = in + (long long)rin * B * MC + cq * CT;
+                    const T* ip = in + (long long)rin * B * RS + cq * CT;
                     for (int k = 0; k < rin; ++k) {
                         T x[CT];
-                        load_ct<T, CT>(ip + (long long)k * MC, x);
+                        load_ct<T, CT>(ip + (long long)k * RS, x);
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
                             const T g = (j < nr) ? __ldg(G + 4 * rq + j + p * k) : T(0);
@@ -741,7 +755,7 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
                     PH_LAUNCH("transfer_kernel(up)");
                 }
                 const int zmax = h->coupling_zmax;
-                size_t sm_c = 2 * (size_t)zmax * MC * sizeof(T);
+                size_t sm_c = 2 * (size_t)zmax * ChainRow<MC>::value * sizeof(T);
                 const int CQ = MC < 4 ? 1 : MC / 4;
                 const int items_last = ((v.p_s + 3) / 4) * (PD / v.p_s) * CQ;
                 const int ni = (items_last + kThreads - 1) / kThreads;

@@ -170,7 +170,13 @@ extern "C" ph_status ph_load(const char* path, int device, ph_handle** out) {
             r.vec(nd.children);
         }
         PH_CUDA(cudaSetDevice(device));
-        PH_CUDA(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+        // the far-field chain is the longer path of a matvec: its stream gets the highest priority so
+        // its blocks are scheduled ahead of the near-field blocks that fill the remaining SM slots
+        {
+            int lo = 0, hi = 0;
+            PH_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+            PH_CUDA(cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, hi));
+        }
         PH_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
         PH_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
         h->d_near = r.dev(h);
