@@ -92,6 +92,7 @@ static void fill_view(ph_handle* h, DevView<T>& v, const std::vector<long>& io, 
     v.item_count = I + io[21];
     v.item_leaf = I + io[22];
     v.items_by_leaf = I + io[23];
+    v.node_parent = I + io[24];
     v.part_stride = h->max_leaf;
     v.partials = (T*)h->d_partials;
     v.nb_off = L + lo[0];
@@ -165,6 +166,10 @@ void refresh_views(ph_handle* h) {
     h->level_nodes.assign(plan.depth + 1, {});
     for (int i = 0; i < nn; ++i)
         if (!plan.nodes[i].children.empty()) h->level_nodes[plan.nodes[i].level].push_back(i);
+    h->level_has_inner_child.assign(plan.depth + 1, 0);
+    for (int i = 0; i < nn; ++i)
+        for (int c : plan.nodes[i].children)
+            if (!plan.nodes[c].children.empty()) h->level_has_inner_child[plan.nodes[i].level] = 1;
     std::vector<int> lvl_flat;
     h->level_nodes_off.assign(plan.depth + 2, 0);
     for (int l = 0; l <= plan.depth; ++l) {
@@ -235,6 +240,9 @@ void refresh_views(ph_handle* h) {
     put(h->item_count);             // 21
     put(h->item_leaf);              // 22
     put(h->items_by_leaf);          // 23
+    std::vector<int> par(nn);
+    for (int i = 0; i < nn; ++i) par[i] = plan.nodes[i].parent;
+    put(par);                       // 24
     std::vector<long long> lls;
     std::vector<long> lo;
     auto putl = [&](const std::vector<long long>& a) {

@@ -24,6 +24,7 @@ struct DevView {
     const int* node_child_off;
     const int* leaf_node;       // leaf -> node id
     const int* node_leaf;       // node -> leaf index or -1
+    const int* node_parent;     // parent node id, -1 at the root
     // theta
     int dtheta;
     int p_theta[3];
@@ -144,6 +145,7 @@ struct ph_handle {
     int* d_level_nodes = nullptr;
     std::vector<int> level_nodes_off;
     int min_far_level = 0;
+    std::vector<char> level_has_inner_child;    // level -> some node on it has a non-leaf child
     // streams
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;

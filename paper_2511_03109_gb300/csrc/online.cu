@@ -205,17 +205,41 @@ __global__ void __launch_bounds__(kThreads, 3) near_kernel(DevView<T> v, int S, 
 
 // --------------------------------------------------------------------------------- H^2 sweeps
 
-// xhat_s[I][c] = sum_{j in s} prod_k U_k[j][i_k] X[j][c]  (leaf stage of Alg. FastForward)
 template <typename T, int MC>
-__global__ void __launch_bounds__(kThreads) upsweep_leaf_kernel(DevView<T> v, int S, int c0) {
+__device__ void mode_product(const T* z, T* out, const T* E, int p, int PD, int stride, bool transpose,
+                             bool accumulate);
+
+// xhat_s[I][c] = sum_{j in s} prod_k U_k[j][i_k] X[j][c]  (leaf stage of Alg. FastForward)
+// Adds val into *p atomically (vector form for float x 4 on global memory).
+template <typename T, int CT>
+__device__ __forceinline__ void atomic_add_ct(T* p, const T (&val)[CT]) {
+#pragma unroll
+    for (int c = 0; c < CT; ++c) atomicAdd(p + c, val[c]);
+}
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 900
+template <>
+__device__ __forceinline__ void atomic_add_ct<float, 4>(float* p, const float (&val)[4]) {
+    atomicAdd(reinterpret_cast<float4*>(p), make_float4(val[0], val[1], val[2], val[3]));
+}
+#endif
+
+// Leaf stage of Alg. FastForward: xhat_s[I][c] = sum_{j in s} prod_k U_k[j][i_k] X[j][c].  When
+// `push` is set the leaf also applies its transfer matrix, (E_{s,d} (x) .. (x) E_{s,1})^T xhat_s,
+// and adds the result into its parent's xhat (which starts at zero), so the up-sweep needs no
+// separate pass over the leaves' parents.  One CTA per leaf.
+template <typename T, int MC>
+__global__ void __launch_bounds__(kThreads) upsweep_leaf_kernel(DevView<T> v, int S, int c0, int push_level) {
     extern __shared__ unsigned char smem_raw[];
     constexpr int CH = 32;
     T* su = reinterpret_cast<T*>(smem_raw);               // CH x d x p_s
     T* sx = su + CH * kMaxDim * kMaxPs;                    // CH x MC
+    T* sE = sx + CH * MC;                                  // 2 p^2 (padded to 4)
     const int leaf = blockIdx.x;
     const int node = v.leaf_node[leaf];
     const int row0 = v.node_begin[node], ns = v.node_end[node] - row0;
     const int ps = v.p_s, d = v.d, PD = v.PD;
+    T* b0 = sE + ((2 * ps * ps + 3) & ~3);                 // PD x MC
+    T* b1 = b0 + (size_t)PD * MC;                          // PD x MC
     constexpr int OPT = 4;  // outputs per thread: PD <= 4 * kThreads
     T acc[OPT][MC];
 #pragma unroll
@@ -259,6 +283,36 @@ __global__ void __launch_bounds__(kThreads) upsweep_leaf_kernel(DevView<T> v, in
         if (I < PD)
 #pragma unroll
             for (int c = 0; c < MC; ++c) v.xhat[((long long)node * PD + I) * S + c0 + c] = acc[o][c];
+    }
+    const int parent = v.node_parent[node];
+    if (parent < 0 || v.node_level[parent] < push_level) return;
+    for (int e = threadIdx.x; e < 2 * ps * ps; e += blockDim.x) sE[e] = v.E[e];
+#pragma unroll
+    for (int o = 0; o < OPT; ++o) {
+        const int I = threadIdx.x + o * kThreads;
+        if (I < PD)
+#pragma unroll
+            for (int c = 0; c < MC; ++c) b0[I * MC + c] = acc[o][c];
+    }
+    const int halves = v.node_halves[node];
+    T* in = b0;
+    T* out = b1;
+    int stride = 1;
+    for (int k = 0; k < d; ++k) {
+        __syncthreads();
+        mode_product<T, MC>(in, out, sE + ((halves >> k) & 1) * ps * ps, ps, PD, stride, true, false);
+        T* t = in; in = out; out = t;
+        stride *= ps;
+    }
+    __syncthreads();
+    constexpr int CT = MC < 4 ? MC : 4;
+    T* dst = v.xhat + (long long)parent * PD * S + c0;
+    for (int e = threadIdx.x; e < PD * (MC / CT); e += blockDim.x) {
+        const int I = e / (MC / CT), cq = e % (MC / CT);
+        T val[CT];
+#pragma unroll
+        for (int c = 0; c < CT; ++c) val[c] = in[I * MC + cq * CT + c];
+        atomic_add_ct<T, CT>(dst + (long long)I * S + cq * CT, val);
     }
 }
 
@@ -308,8 +362,9 @@ __device__ void mode_product(const T* z, T* out, const T* E, int p, int PD, int 
     }
 }
 
-// Up-sweep (up = true): xhat_s = sum over children s' of (E_{s',d} (x) .. (x) E_{s',1})^T xhat_s'.
-// Down-sweep (up = false): yhat_s' += (E_{s',d} (x) .. (x) E_{s',1}) yhat_s for each child s'.
+// Up-sweep (up = true): xhat_s += sum over inner children s' of (E_{s',d} (x) .. (x) E_{s',1})^T xhat_s'.
+// Down-sweep (up = false): yhat_s' += (E_{s',d} (x) .. (x) E_{s',1}) yhat_s for each inner child s'.
+// Leaf children are handled by upsweep_leaf_kernel and combine_kernel.
 // FastKron (§3.6.3) applies the Kronecker factors one mode at a time.  One CTA per node.
 template <typename T, int MC>
 __global__ void __launch_bounds__(kThreads) transfer_kernel(DevView<T> v, const int* nodes, int S, int c0,
@@ -324,9 +379,12 @@ __global__ void __launch_bounds__(kThreads) transfer_kernel(DevView<T> v, const 
     const int node = nodes[blockIdx.x];
     const int cb = v.node_child_off[node], ce = v.node_child_off[node + 1];
     if (up) {
-        for (int e = threadIdx.x; e < PD * MC; e += blockDim.x) sacc[e] = T(0);
+        // leaf children have already added their share (upsweep_leaf_kernel)
+        for (int e = threadIdx.x; e < PD * MC; e += blockDim.x)
+            sacc[e] = dst_all[((long long)node * PD + e / MC) * S + c0 + e % MC];
         for (int q = cb; q < ce; ++q) {
             const int ch = v.node_children[q];
+            if (v.node_leaf[ch] >= 0) continue;
             const int halves = v.node_halves[ch];
             __syncthreads();
             for (int e = threadIdx.x; e < PD * MC; e += blockDim.x)
@@ -352,6 +410,7 @@ __global__ void __launch_bounds__(kThreads) transfer_kernel(DevView<T> v, const 
             sacc[e] = src_all[((long long)node * PD + e / MC) * S + c0 + e % MC];
         for (int q = cb; q < ce; ++q) {
             const int ch = v.node_children[q];
+            if (v.node_leaf[ch] >= 0) continue;  // leaves pull their share in combine_kernel
             const int halves = v.node_halves[ch];
             T* in = sacc;
             T* out = b0;
@@ -661,7 +720,7 @@ __global__ void __launch_bounds__(kThreads) far_h_kernel(DevView<T> v, int S, in
 // FastBackward) or + sum over levels of y_far (H).  One CTA per leaf.
 template <typename T, int MC>
 __global__ void __launch_bounds__(kThreads) combine_kernel(DevView<T> v, T* __restrict__ Y, long long ldy,
-                                                           int m, int S, int c0, int h2) {
+                                                           int m, int S, int c0, int h2, int pull_level) {
     extern __shared__ unsigned char smem_raw[];
     T* sy = reinterpret_cast<T*>(smem_raw);  // PD x MC
     const int leaf = blockIdx.x;
@@ -671,6 +730,28 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(DevView<T> v, T* __re
     if (h2) {
         for (int e = threadIdx.x; e < PD * MC; e += blockDim.x)
             sy[e] = v.yhat[((long long)node * PD + e / MC) * S + c0 + e % MC];
+        const int parent = v.node_parent[node];
+        if (parent >= 0 && v.node_level[parent] >= pull_level) {
+            // last level of Alg. FastBackward: yhat_s += (E_{s,d} (x) .. (x) E_{s,1}) yhat_parent
+            T* sE = sy + (size_t)PD * MC;
+            T* b0 = sE + ((2 * ps * ps + 3) & ~3);
+            T* b1 = b0 + (size_t)PD * MC;
+            for (int e = threadIdx.x; e < 2 * ps * ps; e += blockDim.x) sE[e] = v.E[e];
+            for (int e = threadIdx.x; e < PD * MC; e += blockDim.x)
+                b0[e] = v.yhat[((long long)parent * PD + e / MC) * S + c0 + e % MC];
+            const int halves = v.node_halves[node];
+            T* in = b0;
+            T* out = b1;
+            int stride = 1;
+            for (int k = 0; k < d; ++k) {
+                __syncthreads();
+                const bool last = (k == d - 1);
+                mode_product<T, MC>(in, last ? sy : out, sE + ((halves >> k) & 1) * ps * ps, ps, PD, stride, false,
+                                    last);
+                T* t = in; in = out; out = t;
+                stride *= ps;
+            }
+        }
         __syncthreads();
     }
     for (int i = threadIdx.x; i < ns; i += blockDim.x) {
@@ -738,15 +819,19 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
     if (!plan.far_targets.empty()) {
         for (int c0 = 0; c0 < S; c0 += MC) {
             if (h2) {
-                size_t sm_leaf = ((size_t)32 * kMaxDim * kMaxPs + 32 * MC) * sizeof(T);
+                PH_CUDA(cudaMemsetAsync(v.xhat, 0, (size_t)v.n_nodes * PD * S * sizeof(T), h->side));
+                size_t sm_leaf = ((size_t)32 * kMaxDim * kMaxPs + 32 * MC + ((2 * v.p_s * v.p_s + 3) & ~3) +
+                                  2 * (size_t)PD * MC) * sizeof(T);
+                set_smem<T, MC>((const void*)upsweep_leaf_kernel<T, MC>, sm_leaf);
                 {
                     ProfScope ps(h, 3, h->side);
-                    upsweep_leaf_kernel<T, MC><<<nleaves, kThreads, sm_leaf, h->side>>>(v, S, c0);
+                    upsweep_leaf_kernel<T, MC><<<nleaves, kThreads, sm_leaf, h->side>>>(v, S, c0, h->min_far_level);
                 }
                 PH_LAUNCH("upsweep_leaf_kernel");
                 size_t sm_tr = ((size_t)((2 * v.p_s * v.p_s + 3) & ~3) + 3 * (size_t)PD * MC) * sizeof(T);
                 set_smem<T, MC>((const void*)transfer_kernel<T, MC>, sm_tr);
                 for (int l = plan.depth - 1; l >= h->min_far_level; --l) {
+                    if (!h->level_has_inner_child[l]) continue;
                     int cnt = h->level_nodes_off[l + 1] - h->level_nodes_off[l];
                     if (cnt == 0) continue;
                     ProfScope ps(h, 4, h->side);
@@ -778,6 +863,7 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
                 }
                 PH_LAUNCH("coupling_kernel");
                 for (int l = h->min_far_level; l < plan.depth; ++l) {
+                    if (!h->level_has_inner_child[l]) continue;
                     int cnt = h->level_nodes_off[l + 1] - h->level_nodes_off[l];
                     if (cnt == 0) continue;
                     ProfScope ps(h, 6, h->side);
@@ -803,11 +889,12 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
     PH_CUDA(cudaEventRecord(h->ev_join, h->side));
     PH_CUDA(cudaStreamWaitEvent(stream, h->ev_join, 0));
     for (int c0 = 0; c0 < S; c0 += MC) {
-        size_t sm = (size_t)PD * MC * sizeof(T);
+        size_t sm = ((size_t)3 * PD * MC + ((2 * v.p_s * v.p_s + 3) & ~3)) * sizeof(T);
         set_smem<T, MC>((const void*)combine_kernel<T, MC>, sm);
         ProfScope ps(h, 8, stream);
         combine_kernel<T, MC><<<nleaves, kThreads, sm, stream>>>(v, Y, ldy, m, S, c0,
-                                                                 (h2 && !plan.far_targets.empty()) ? 1 : 0);
+                                                                 (h2 && !plan.far_targets.empty()) ? 1 : 0,
+                                                                 h->min_far_level);
         PH_LAUNCH("combine_kernel");
     }
 }
