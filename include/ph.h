@@ -82,6 +82,10 @@ typedef struct {
                               forced off for kernels that are not translation-invariant */
     int check_finite;      /* 1: ph_matvec checks X for non-finite entries (synchronises) */
     int device;            /* CUDA device ordinal */
+    int coupling;          /* H^2 coupling stage: 0 = explicit factors L_k, R_k per translation class
+                              applied as two matrix products (the alternative §4.5 mentions),
+                              1 = the TT chain of Alg. "Modified H^2-Matrix MVM"; mode 0 needs
+                              r_d, r_{d+d_theta} <= 64 and falls back to 1 otherwise */
 } ph_build_opts;
 
 /* Sizes and counts of a built handle; all byte counts are of stored data. */
@@ -149,8 +153,9 @@ ph_status ph_matvec_host(ph_handle* h, const void* X, long ldx, int m, void* Y, 
  * until the process exits.
  *   Arguments, layout and result are those of ph_matvec.
  *   Sizes: the workspace needed is about 4 (float) or 8 (double) bytes times
- *     m_pad * (n + near work items * largest leaf + 2 * tree nodes * p_s^d)
- *     (H^2) or m_pad * (n + items * largest leaf + far levels * n) (H), m_pad =
+ *     m_pad * (n + near work items * largest leaf + 2 * tree nodes * p_s^d
+ *     + far blocks * largest r_d) (H^2) or m_pad * (n + items * largest leaf +
+ *     far levels * n) (H), m_pad =
  *     m rounded up to 1, 2, 4, 8 or a multiple of 16; above 16 MiB the call
  *     returns PH_ERR_INVALID_ARG with the needed size in ph_last_error and
  *     computes nothing.
@@ -194,11 +199,12 @@ ph_status ph_plan(const double* points, long n, int d, int l_max, double eta,
  * handle's streams and returns, for each of the PH_PROF_KINDS kernel kinds in
  * the order
  *   0 instantiate, 1 gather, 2 near, 3 upsweep_leaf, 4 transfer_up,
- *   5 coupling, 6 transfer_down, 7 far_h, 8 combine,
+ *   5 coupling (the TT chain, or phase 1 of the explicit coupling), 6 transfer_down,
+ *   7 far_h, 8 combine, 9 coupling phase 2 (explicit coupling),
  * the summed milliseconds and the number of launches since the last read (or
  * since enabling), then starts a new count.  ms and launches are host arrays of
  * PH_PROF_KINDS elements. */
-#define PH_PROF_KINDS 9
+#define PH_PROF_KINDS 10
 ph_status ph_profile_enable(ph_handle* h, int enable);
 ph_status ph_profile_read(ph_handle* h, double* ms, long* launches);
 

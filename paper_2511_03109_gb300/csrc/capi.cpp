@@ -93,6 +93,16 @@ static void fill_view(ph_handle* h, DevView<T>& v, const std::vector<long>& io, 
     v.item_leaf = I + io[22];
     v.items_by_leaf = I + io[23];
     v.node_parent = I + io[24];
+    v.far_lr = (const T*)h->d_lr;
+    v.key_lroff = L + lo[6];
+    v.kb_off = I + io[25];
+    v.kb_list = I + io[26];
+    v.n_citems = (int)h->citem_key.size();
+    v.citem_key = I + io[27];
+    v.citem_first = I + io[28];
+    v.citem_count = I + io[29];
+    v.zstride = h->zstride;
+    v.zbuf = (T*)h->d_zbuf;
     v.part_stride = h->max_leaf;
     v.partials = (T*)h->d_partials;
     v.nb_off = L + lo[0];
@@ -243,6 +253,39 @@ void refresh_views(ph_handle* h) {
     std::vector<int> par(nn);
     for (int i = 0; i < nn; ++i) par[i] = plan.nodes[i].parent;
     put(par);                       // 24
+    // far blocks grouped by translation class, and the key-grouped items of the explicit coupling
+    // (up to kCouplingItemBlocks blocks of one key per item)
+    constexpr int kCouplingItemBlocks = 4;
+    const int nkeys = (int)plan.key_rep.size();
+    h->kb_off.assign(nkeys + 1, 0);
+    for (int k : plan.far_key) h->kb_off[k + 1]++;
+    for (int k = 0; k < nkeys; ++k) h->kb_off[k + 1] += h->kb_off[k];
+    h->kb_list.assign(plan.far_key.size(), 0);
+    {
+        std::vector<int> fill(h->kb_off.begin(), h->kb_off.end() - (nkeys > 0 ? 1 : 0));
+        if (nkeys == 0) fill.clear();
+        for (size_t b = 0; b < plan.far_key.size(); ++b) h->kb_list[fill[plan.far_key[b]]++] = (int)b;
+    }
+    h->citem_key.clear();
+    h->citem_first.clear();
+    h->citem_count.clear();
+    h->zstride = 1;
+    h->rank_max_lr = 1;
+    for (int k = 0; k < nkeys; ++k) {
+        h->zstride = std::max(h->zstride, h->key_ranks[(size_t)k * (h->Delta + 1) + plan.d]);
+        h->rank_max_lr = std::max(h->rank_max_lr, std::max(h->key_ranks[(size_t)k * (h->Delta + 1) + plan.d],
+                                                           h->key_ranks[(size_t)k * (h->Delta + 1) + plan.d + 1]));
+        for (int i = h->kb_off[k]; i < h->kb_off[k + 1]; i += kCouplingItemBlocks) {
+            h->citem_key.push_back(k);
+            h->citem_first.push_back(i);
+            h->citem_count.push_back(std::min(kCouplingItemBlocks, h->kb_off[k + 1] - i));
+        }
+    }
+    put(h->kb_off);                 // 25
+    put(h->kb_list);                // 26
+    put(h->citem_key);              // 27
+    put(h->citem_first);            // 28
+    put(h->citem_count);            // 29
     std::vector<long long> lls;
     std::vector<long> lo;
     auto putl = [&](const std::vector<long long>& a) {
@@ -256,6 +299,7 @@ void refresh_views(ph_handle* h) {
     putl(h->key_hoff);
     putl(h->fb_soff);
     putl(h->fb_toff);
+    putl(h->key_lroff);
     dev_free(h, h->d_int);
     dev_free(h, h->d_ll);
     dev_free(h, h->d_dbl);
@@ -283,7 +327,8 @@ void ensure_workspace(ph_handle* h, int m) {
     if (S <= h->mcap) return;
     const Plan& plan = h->plan;
     const size_t sc = h->scalar;
-    for (void* p : {h->d_Xc, h->d_Ynear, h->d_yfar, h->d_xhat, h->d_yhat, h->d_partials}) dev_free(h, p);
+    for (void* p : {h->d_Xc, h->d_Ynear, h->d_yfar, h->d_xhat, h->d_yhat, h->d_partials, h->d_zbuf}) dev_free(h, p);
+    h->d_zbuf = nullptr;
     h->d_Xc = dev_alloc(h, (size_t)plan.n * S * sc);
     h->d_Ynear = dev_alloc(h, (size_t)plan.n * S * sc);
     h->d_partials = dev_alloc(h, std::max<size_t>(1, h->item_first.size()) * h->max_leaf * S * sc);
@@ -294,6 +339,7 @@ void ensure_workspace(ph_handle* h, int m) {
     if (h->opts.fmt == PH_FMT_H2 && !plan.far_targets.empty()) {
         h->d_xhat = dev_alloc(h, (size_t)plan.nodes.size() * h->PD * S * sc);
         h->d_yhat = dev_alloc(h, (size_t)plan.nodes.size() * h->PD * S * sc);
+        if (h->opts.coupling == 0) h->d_zbuf = dev_alloc(h, plan.far_s.size() * (size_t)h->zstride * S * sc);
     }
     h->mcap = S;
     fill_view<float>(h, h->vf, h->view_io, h->view_lo);
@@ -493,6 +539,8 @@ ph_status ph_get_info(const ph_handle* h, ph_info* info) {
         if (h->opts.fmt == PH_FMT_H) {
             fl += 2.0 * (plan.nodes[plan.far_s[b]].size() * (double)rk[d] +
                          plan.nodes[plan.far_t[b]].size() * (double)rk[d + 1] + (double)rk[d] * rk[d + 1]);
+        } else if (h->opts.coupling == 0) {
+            fl += 2.0 * PD * ((double)rk[d + 1] + rk[d]) + 2.0 * rk[d] * rk[d + 1];
         } else {
             double a = PD / p, chain = 0;
             for (int i = 0; i < d; ++i) {  // right cores

@@ -58,6 +58,16 @@ struct DevView {
     const T* far_cores;
     const double* far_theta;
     T* H;
+    const T* far_lr;            // explicit L_k^T (r_d x PD) then R_k^T (r_{d+1} x PD) per key, row-major
+    const long long* key_lroff; // offset of L_k^T in far_lr (R_k^T follows)
+    const int* kb_off;          // CSR over keys: far blocks of each key
+    const int* kb_list;
+    int n_citems;               // key-grouped work items of the explicit coupling
+    const int* citem_key;
+    const int* citem_first;     // index into kb_list
+    const int* citem_count;
+    int zstride;                // rows per far block in zbuf (max r_d)
+    T* zbuf;                    // n_far x zstride x mcap: z_b = H_k R_k^T xhat_t
     int n_far;
     const int* fb_t;            // source node per far block
     const int* fb_key;
@@ -106,6 +116,13 @@ struct ph_handle {
     std::vector<int> key_ranks;
     std::vector<long long> key_off, key_hoff;
     std::vector<long long> fb_soff, fb_toff;
+    std::vector<long long> key_lroff;
+    long long lr_elems = 0;
+    void* d_lr = nullptr;
+    std::vector<int> kb_off, kb_list, citem_key, citem_first, citem_count;
+    int zstride = 1;
+    int rank_max_lr = 1;                        // max over keys of r_d and r_{d+d_theta}
+    void* d_zbuf = nullptr;
     long long near_elems = 0, near_theta_elems = 0, far_elems = 0, far_theta_elems = 0, H_elems = 0,
               st_elems = 0, w_elems = 0;
     std::vector<double> theta_nodes, theta_bw;  // dtheta x 32

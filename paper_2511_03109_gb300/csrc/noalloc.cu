@@ -62,14 +62,16 @@ extern "C" ph_status ph_matvec_noalloc(ph_handle* h, const void* X, long ldx, in
     const size_t items = std::max<size_t>(1, h->item_first.size());
     const bool h2 = (h->opts.fmt == PH_FMT_H2) && !h->plan.far_targets.empty();
     const bool hfar = (h->opts.fmt == PH_FMT_H) && h->n_far_levels > 0;
-    // layout of the scratch array: Xc | partials | xhat | yhat  (H^2)  or  Xc | partials | yfar (H)
+    // layout of the scratch array: Xc | partials | xhat | yhat | zbuf (H^2)  or  Xc | partials | yfar (H)
     const size_t o_xc = 0;
     const size_t o_part = align256(o_xc + n * S * sc);
     const size_t o_xhat = align256(o_part + items * h->max_leaf * S * sc);
     const size_t node_bytes = h2 ? h->plan.nodes.size() * (size_t)h->PD * S * sc : 0;
     const size_t o_yhat = align256(o_xhat + node_bytes);
     const size_t o_yfar = align256(o_yhat + node_bytes);
-    const size_t need = o_yfar + (hfar ? (size_t)h->n_far_levels * n * S * sc : 0);
+    const size_t o_zbuf = align256(o_yfar + (hfar ? (size_t)h->n_far_levels * n * S * sc : 0));
+    const bool zb = h2 && h->opts.coupling == 0;
+    const size_t need = o_zbuf + (zb ? h->plan.far_s.size() * (size_t)h->zstride * S * sc : 0);
     if (need > kNoAllocScratchBytes) {
         h->last_error = "ph_matvec_noalloc: this problem needs " + std::to_string(need) +
                         " bytes of scratch; the limit is " + std::to_string(kNoAllocScratchBytes) +
@@ -88,6 +90,7 @@ extern "C" ph_status ph_matvec_noalloc(ph_handle* h, const void* X, long ldx, in
             v.xhat = h2 ? reinterpret_cast<T*>(base + o_xhat) : nullptr;
             v.yhat = h2 ? reinterpret_cast<T*>(base + o_yhat) : nullptr;
             v.yfar = hfar ? reinterpret_cast<T*>(base + o_yfar) : nullptr;
+            v.zbuf = zb ? reinterpret_cast<T*>(base + o_zbuf) : nullptr;
             v.Ynear = nullptr;
             v.mcap = (int)S;
         };

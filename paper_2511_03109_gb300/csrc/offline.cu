@@ -625,6 +625,68 @@ ph_status offline_build(ph_handle* h, const double* points, long n) {
         cublasDestroy(eng.blas);
         cusolverDnDestroy(eng.solver);
     }
+    // explicit factors per key (coupling mode 0, H^2): L_k^T and R_k^T, both r x PD row-major.
+    // L[(i_1..i_k), s_k] = sum L[(i_1..i_{k-1}), s_{k-1}] G_k[s_{k-1}, i_k, s_k] from the left cores;
+    // R[(j_1..j_d), s] from the right cores, innermost index first (App. A.4).
+    std::vector<double> lr;
+    h->key_lroff.assign(nkeys, 0);
+    // the explicit coupling kernels tile r_d and r_{d+d_theta} by at most 64 rows; larger ranks
+    // (only possible without a rank cap) use the TT chain
+    for (int key = 0; key < nkeys && h->opts.coupling == 0; ++key) {
+        const int* rk = &h->key_ranks[(size_t)key * (Delta + 1)];
+        if (rk[d] > 64 || rk[d + dt] > 64) h->opts.coupling = 1;
+    }
+    if (o.fmt == PH_FMT_H2 && h->opts.coupling == 0) {
+        for (int key = 0; key < nkeys; ++key) {
+            const int* rk = &h->key_ranks[(size_t)key * (Delta + 1)];
+            const auto& cores = key_cores[key];
+            std::vector<double> L(1, 1.0);
+            long long rows = 1;
+            int rp = 1;
+            for (int k = 0; k < d; ++k) {
+                const int rn = rk[k + 1];
+                const auto& G = cores[k];
+                std::vector<double> Ln((size_t)rows * ps * rn, 0.0);
+                for (int sn = 0; sn < rn; ++sn)
+                    for (int i = 0; i < ps; ++i)
+                        for (int a = 0; a < rp; ++a) {
+                            const double g = G[a + (size_t)rp * (i + (size_t)ps * sn)];
+                            if (g == 0.0) continue;
+                            for (long long row = 0; row < rows; ++row)
+                                Ln[(size_t)(row + rows * i) + (size_t)rows * ps * sn] += L[(size_t)row + rows * a] * g;
+                        }
+                L.swap(Ln);
+                rows *= ps;
+                rp = rn;
+            }
+            std::vector<double> Q(1, 1.0);
+            rows = 1;
+            int rr = 1;
+            for (int k = d - 1; k >= 0; --k) {
+                const int ci = d + dt + k;
+                const int rl = rk[ci];
+                const auto& G = cores[ci];
+                std::vector<double> Qn((size_t)rows * ps * rl, 0.0);
+                for (int a = 0; a < rl; ++a)
+                    for (int j = 0; j < ps; ++j)
+                        for (int c = 0; c < rr; ++c) {
+                            const double g = G[a + (size_t)rl * (j + (size_t)ps * c)];
+                            if (g == 0.0) continue;
+                            for (long long rest = 0; rest < rows; ++rest)
+                                Qn[(size_t)(j + ps * rest) + (size_t)rows * ps * a] += g * Q[(size_t)rest + rows * c];
+                        }
+                Q.swap(Qn);
+                rows *= ps;
+                rr = rl;
+            }
+            h->key_lroff[key] = (long long)lr.size();
+            lr.insert(lr.end(), L.begin(), L.end());  // PD x r_d column-major == L^T row-major
+            lr.insert(lr.end(), Q.begin(), Q.end());  // PD x r_{d+1} column-major == R^T row-major
+        }
+    }
+    h->lr_elems = (long long)lr.size();
+    if (o.prec == PH_FP32) h->d_lr = upload_as<float>(h, lr);
+    else h->d_lr = upload_as<double>(h, lr);
     h->far_elems = (long long)far_sp.size();
     h->far_theta_elems = (long long)far_th.size();
     h->H_elems = hoff;

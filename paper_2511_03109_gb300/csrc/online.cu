@@ -652,6 +652,272 @@ __global__ void __launch_bounds__(kThreads, 3) coupling_kernel(DevView<T> v, int
     }
 }
 
+// Explicit coupling, phase 1 (grouped by translation class k): for the far blocks b of one item
+// (up to four blocks of class k), P = R_k^T xhat_t(b) and z_b = H_k P.  R_k^T is the
+// p_s^d-long side of C_k = L_k H_k R_k^T (§4.2), so this is a matrix product with K = p_s^d
+// whose A operand is shared by all N = blocks x MC columns of the item.
+template <typename T, int MC>
+__global__ void __launch_bounds__(kThreads, 2) coupling_a_kernel(DevView<T> v, int S, int c0) {
+    constexpr int KC = 32, NMAX = 4 * MC, BS = NMAX + 4, AS = KC + 1;
+    extern __shared__ unsigned char smem_raw[];
+    T* As = reinterpret_cast<T*>(smem_raw);  // 64 x AS
+    T* Bs = As + 64 * AS;                     // KC x BS
+    T* Ps = Bs + KC * BS;                     // 64 x BS
+    const int item = blockIdx.x;
+    const int key = v.citem_key[item], first = v.citem_first[item], cnt = v.citem_count[item];
+    const int* rk = v.key_ranks + (size_t)key * (v.Delta + 1);
+    const int rd = rk[v.d], rp = rk[v.d + 1];
+    const int PD = v.PD, N = cnt * MC;
+    const T* Rt = v.far_lr + v.key_lroff[key] + (long long)rd * PD;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    T acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[u][j] = T(0);
+    for (int k0 = 0; k0 < PD; k0 += KC) {
+        const int kn = min(KC, PD - k0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < rp * KC; e += blockDim.x) {
+            const int row = e / KC, kk = e % KC;
+            As[row * AS + kk] = (kk < kn) ? Rt[(long long)row * PD + k0 + kk] : T(0);
+        }
+        for (int e = threadIdx.x; e < KC * N; e += blockDim.x) {
+            const int kk = e / N, col = e % N;
+            const int b = col / MC, c = col % MC;
+            const int t = v.fb_t[v.kb_list[first + b]];
+            Bs[kk * BS + col] = (kk < kn) ? v.xhat[((long long)t * PD + k0 + kk) * S + c0 + c] : T(0);
+        }
+        __syncthreads();
+        if (4 * tx < N) {
+#pragma unroll 4
+            for (int kk = 0; kk < KC; ++kk) {
+                T bv[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) bv[j] = Bs[kk * BS + 4 * tx + j];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const T av = As[(ty + 16 * u) * AS + kk];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[u][j] += av * bv[j];
+                }
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        if (ty + 16 * u < rp)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (4 * tx + j < N) Ps[(ty + 16 * u) * BS + 4 * tx + j] = acc[u][j];
+    __syncthreads();
+    const T* H = v.H + v.key_hoff[key];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int r = ty + 16 * u;
+        if (r >= rd) continue;
+        T z[4] = {T(0), T(0), T(0), T(0)};
+        for (int q = 0; q < rp; ++q) {
+            const T hv = H[r + rd * q];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) z[j] += hv * Ps[q * BS + 4 * tx + j];
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int col = 4 * tx + j;
+            if (col < N) {
+                const int fb = v.kb_list[first + col / MC];
+                v.zbuf[((long long)fb * v.zstride + r) * S + c0 + col % MC] = z[j];
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// Phase 1 of the explicit coupling, staged path (p_s^d a multiple of 32, MC >= 4): the chunks of
+// R_k^T (r' x 32) and of the item's xhat_t columns (32 x N) are copied into shared memory with
+// 16-byte asynchronous copies, two chunks in flight, so the copy of chunk c + 1 overlaps the
+// products of chunk c.  Same result as coupling_a_kernel.
+template <typename T, int MC>
+__global__ void __launch_bounds__(kThreads, 2) coupling_a_staged_kernel(DevView<T> v, int S, int c0) {
+    constexpr int KC = 32, NMAX = 4 * MC, BS = NMAX + 4, AS = KC + 4;
+    constexpr int EV = 16 / sizeof(T);  // elements per 16-byte copy
+    extern __shared__ unsigned char smem_raw[];
+    T* As = reinterpret_cast<T*>(smem_raw);  // 2 x 64 x AS
+    T* Bs = As + 2 * 64 * AS;                 // 2 x KC x BS
+    T* Ps = Bs + 2 * KC * BS;                 // 64 x BS
+    __shared__ long long colbase[4];
+    const int item = blockIdx.x;
+    const int key = v.citem_key[item], first = v.citem_first[item], cnt = v.citem_count[item];
+    const int* rk = v.key_ranks + (size_t)key * (v.Delta + 1);
+    const int rd = rk[v.d], rp = rk[v.d + 1];
+    const int PD = v.PD, N = cnt * MC;
+    const T* Rt = v.far_lr + v.key_lroff[key] + (long long)rd * PD;
+    if (threadIdx.x < cnt) colbase[threadIdx.x] = (long long)v.fb_t[v.kb_list[first + threadIdx.x]] * PD * S + c0;
+    __syncthreads();
+    auto issue = [&](int chunk, int buf) {
+        const int k0 = chunk * KC;
+        T* A = As + buf * 64 * AS;
+        T* B = Bs + buf * KC * BS;
+        for (int e = threadIdx.x; e < rp * (KC / EV); e += blockDim.x) {
+            const int row = e / (KC / EV), q = e % (KC / EV);
+            cp_async16(A + row * AS + q * EV, Rt + (long long)row * PD + k0 + q * EV);
+        }
+        for (int e = threadIdx.x; e < cnt * KC * (MC / EV); e += blockDim.x) {
+            const int b = e / (KC * (MC / EV)), rest = e % (KC * (MC / EV));
+            const int kk = rest / (MC / EV), q = rest % (MC / EV);
+            cp_async16(B + kk * BS + b * MC + q * EV, v.xhat + colbase[b] + (long long)(k0 + kk) * S + q * EV);
+        }
+        cp_async_commit();
+    };
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    T acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[u][j] = T(0);
+    const int nchunks = PD / KC;
+    issue(0, 0);
+    for (int c = 0; c < nchunks; ++c) {
+        if (c + 1 < nchunks) {
+            issue(c + 1, (c + 1) & 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const T* A = As + (c & 1) * 64 * AS;
+        const T* B = Bs + (c & 1) * KC * BS;
+        if (4 * tx < N) {
+#pragma unroll 8
+            for (int kk = 0; kk < KC; ++kk) {
+                T bv[4];
+                load_ct<T, 4>(B + kk * BS + 4 * tx, bv);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const T av = A[(ty + 16 * u) * AS + kk];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[u][j] += av * bv[j];
+                }
+            }
+        }
+        __syncthreads();  // the buffer of chunk c is refilled by the issue of chunk c + 2
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        if (ty + 16 * u < rp)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (4 * tx + j < N) Ps[(ty + 16 * u) * BS + 4 * tx + j] = acc[u][j];
+    __syncthreads();
+    const T* H = v.H + v.key_hoff[key];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int r = ty + 16 * u;
+        if (r >= rd) continue;
+        T z[4] = {T(0), T(0), T(0), T(0)};
+        for (int q = 0; q < rp; ++q) {
+            const T hv = H[r + rd * q];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) z[j] += hv * Ps[q * BS + 4 * tx + j];
+        }
+        if (4 * tx < N) {
+            const int fb = v.kb_list[first + (4 * tx) / MC];
+            store_ct<T, 4>(v.zbuf + ((long long)fb * v.zstride + r) * S + c0 + (4 * tx) % MC, z);
+        }
+    }
+}
+
+// Explicit coupling, phase 2 (grouped by target s): yhat_s += sum over far blocks b of s of
+// L_k z_b, L_k = (I (x) G_1^{2}) ... G_d^{2} formed offline (App. A.4).  Thread tile: 8
+// consecutive rows of yhat_s x CT right-hand sides; z_b staged in shared memory eight blocks at a
+// time.  The far blocks of a target are split over `nsplit` CTAs that meet in yhat via atomics.
+template <typename T, int MC, int NIB>
+__global__ void __launch_bounds__(kThreads, 2) coupling_b_kernel(DevView<T> v, int S, int c0, int nsplit) {
+    constexpr int CT = MC < 4 ? MC : 4, CQ = MC / CT, RPT = 8, ZB = 8;
+    extern __shared__ unsigned char smem_raw[];
+    T* zs = reinterpret_cast<T*>(smem_raw);  // ZB x zstride x MC
+    const int PD = v.PD, zst = v.zstride;
+    const int ti = blockIdx.x / nsplit, part = blockIdx.x % nsplit;
+    const int s = v.far_targets[ti];
+    const int fb0 = v.far_by_target[ti], fb1 = v.far_by_target[ti + 1];
+    const int per = (fb1 - fb0 + nsplit - 1) / nsplit;
+    const int my0 = fb0 + part * per, my1 = min(fb1, my0 + per);
+    if (my0 >= my1) return;
+    const int RG = (PD + RPT - 1) / RPT;
+    const int items = RG * CQ;
+    const bool vec = (PD % 4) == 0;
+    T acc[NIB][RPT][CT];
+#pragma unroll
+    for (int u = 0; u < NIB; ++u)
+#pragma unroll
+        for (int i = 0; i < RPT; ++i)
+#pragma unroll
+            for (int c = 0; c < CT; ++c) acc[u][i][c] = T(0);
+    for (int g0 = my0; g0 < my1; g0 += ZB) {
+        const int nb = min(ZB, my1 - g0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < nb * zst * MC; e += blockDim.x) {
+            const int bi = e / (zst * MC), rest = e % (zst * MC);
+            zs[e] = v.zbuf[((long long)(g0 + bi) * zst + rest / MC) * S + c0 + rest % MC];
+        }
+        __syncthreads();
+        for (int bi = 0; bi < nb; ++bi) {
+            const int key = v.fb_key[g0 + bi];
+            const int rd = v.key_ranks[(size_t)key * (v.Delta + 1) + v.d];
+            const T* Lt = v.far_lr + v.key_lroff[key];
+            const T* zb = zs + bi * zst * MC;
+#pragma unroll
+            for (int u = 0; u < NIB; ++u) {
+                const int it = threadIdx.x + u * kThreads;
+                if (it >= items) continue;
+                const int cq = it % CQ, rg = it / CQ;
+                const int I0 = rg * RPT;
+                const bool full = vec && (I0 + RPT <= PD);
+                for (int q = 0; q < rd; ++q) {
+                    T l[RPT];
+                    const T* lp = Lt + (long long)q * PD + I0;
+                    if (full) {
+                        load_ct<T, 4>(lp, *reinterpret_cast<T(*)[4]>(&l[0]));
+                        load_ct<T, 4>(lp + 4, *reinterpret_cast<T(*)[4]>(&l[4]));
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < RPT; ++i) l[i] = (I0 + i < PD) ? lp[i] : T(0);
+                    }
+                    T x[CT];
+                    load_ct<T, CT>(zb + q * MC + cq * CT, x);
+#pragma unroll
+                    for (int i = 0; i < RPT; ++i)
+#pragma unroll
+                        for (int c = 0; c < CT; ++c) acc[u][i][c] += l[i] * x[c];
+                }
+            }
+        }
+    }
+    T* dst = v.yhat + (long long)s * PD * S + c0;
+#pragma unroll
+    for (int u = 0; u < NIB; ++u) {
+        const int it = threadIdx.x + u * kThreads;
+        if (it >= items) continue;
+        const int cq = it % CQ, rg = it / CQ;
+        for (int i = 0; i < RPT; ++i) {
+            const int I = rg * RPT + i;
+            if (I >= PD) break;
+            T* o = dst + (long long)I * S + cq * CT;
+            if (nsplit > 1) atomic_add_ct<T, CT>(o, acc[u][i]);
+            else store_ct<T, CT>(o, acc[u][i]);
+        }
+    }
+}
+
 // H format far field (§4.5): y_s += S_b (H_k (T_b^T x_t)) for every far block of target s.
 template <typename T, int MC>
 __global__ void __launch_bounds__(kThreads) far_h_kernel(DevView<T> v, int S, int c0, int rmax) {
@@ -839,29 +1105,70 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
                         v, h->d_level_nodes + h->level_nodes_off[l], S, c0, true, v.xhat, v.xhat);
                     PH_LAUNCH("transfer_kernel(up)");
                 }
-                const int zmax = h->coupling_zmax;
-                size_t sm_c = 2 * (size_t)zmax * ChainRow<MC>::value * sizeof(T);
-                const int CQ = MC < 4 ? 1 : MC / 4;
-                const int items_last = ((v.p_s + 3) / 4) * (PD / v.p_s) * CQ;
-                const int ni = (items_last + kThreads - 1) / kThreads;
-                const int nsplit = 4;
-                {
-                    ProfScope ps(h, 5, h->side);
-                    const int nt = (int)plan.far_targets.size() * nsplit;
-                    if (ni <= 1) {
-                        set_smem<T, MC>((const void*)coupling_kernel<T, MC, 1>, sm_c);
-                        coupling_kernel<T, MC, 1><<<nt, kThreads, sm_c, h->side>>>(v, S, c0, zmax, nsplit);
-                    } else if (ni <= 2) {
-                        set_smem<T, MC>((const void*)coupling_kernel<T, MC, 2>, sm_c);
-                        coupling_kernel<T, MC, 2><<<nt, kThreads, sm_c, h->side>>>(v, S, c0, zmax, nsplit);
-                    } else if (ni <= 4) {
-                        set_smem<T, MC>((const void*)coupling_kernel<T, MC, 4>, sm_c);
-                        coupling_kernel<T, MC, 4><<<nt, kThreads, sm_c, h->side>>>(v, S, c0, zmax, nsplit);
-                    } else {
-                        throw Error(PH_ERR_UNSUPPORTED, "p_s^d too large for the coupling kernel");
+                if (h->opts.coupling == 0) {
+                    {
+                        ProfScope ps(h, 5, h->side);
+                        constexpr int NMAX = 4 * MC;
+                        const bool staged = (MC >= 4) && (PD % 32 == 0) && (h->rank_max_lr <= 64);
+                        if (staged) {
+                            size_t sm_a = ((size_t)2 * 64 * 36 + 2 * 32 * (NMAX + 4) + 64 * (NMAX + 4)) * sizeof(T);
+                            set_smem<T, MC>((const void*)coupling_a_staged_kernel<T, MC>, sm_a);
+                            coupling_a_staged_kernel<T, MC><<<std::max(1, v.n_citems), kThreads, sm_a, h->side>>>(
+                                v, S, c0);
+                        } else {
+                            size_t sm_a = ((size_t)64 * 33 + 32 * (NMAX + 4) + 64 * (NMAX + 4)) * sizeof(T);
+                            set_smem<T, MC>((const void*)coupling_a_kernel<T, MC>, sm_a);
+                            coupling_a_kernel<T, MC><<<std::max(1, v.n_citems), kThreads, sm_a, h->side>>>(v, S, c0);
+                        }
+                        PH_LAUNCH("coupling_a_kernel");
                     }
+                    {
+                        ProfScope ps(h, 9, h->side);
+                        constexpr int CQB = (MC < 4) ? 1 : MC / 4;
+                        const int itemsb = ((PD + 7) / 8) * CQB;
+                        const int nib = (itemsb + kThreads - 1) / kThreads;
+                        const int nsplit = 4;
+                        size_t sm_b = (size_t)8 * v.zstride * MC * sizeof(T);
+                        const int nt = (int)plan.far_targets.size() * nsplit;
+                        if (nib <= 1) {
+                            set_smem<T, MC>((const void*)coupling_b_kernel<T, MC, 1>, sm_b);
+                            coupling_b_kernel<T, MC, 1><<<nt, kThreads, sm_b, h->side>>>(v, S, c0, nsplit);
+                        } else if (nib <= 2) {
+                            set_smem<T, MC>((const void*)coupling_b_kernel<T, MC, 2>, sm_b);
+                            coupling_b_kernel<T, MC, 2><<<nt, kThreads, sm_b, h->side>>>(v, S, c0, nsplit);
+                        } else if (nib <= 4) {
+                            set_smem<T, MC>((const void*)coupling_b_kernel<T, MC, 4>, sm_b);
+                            coupling_b_kernel<T, MC, 4><<<nt, kThreads, sm_b, h->side>>>(v, S, c0, nsplit);
+                        } else {
+                            throw Error(PH_ERR_UNSUPPORTED, "p_s^d too large for the coupling kernel");
+                        }
+                        PH_LAUNCH("coupling_b_kernel");
+                    }
+                } else {
+                    const int zmax = h->coupling_zmax;
+                    size_t sm_c = 2 * (size_t)zmax * ChainRow<MC>::value * sizeof(T);
+                    const int CQ = MC < 4 ? 1 : MC / 4;
+                    const int items_last = ((v.p_s + 3) / 4) * (PD / v.p_s) * CQ;
+                    const int ni = (items_last + kThreads - 1) / kThreads;
+                    const int nsplit = 4;
+                    {
+                        ProfScope ps(h, 5, h->side);
+                        const int nt = (int)plan.far_targets.size() * nsplit;
+                        if (ni <= 1) {
+                            set_smem<T, MC>((const void*)coupling_kernel<T, MC, 1>, sm_c);
+                            coupling_kernel<T, MC, 1><<<nt, kThreads, sm_c, h->side>>>(v, S, c0, zmax, nsplit);
+                        } else if (ni <= 2) {
+                            set_smem<T, MC>((const void*)coupling_kernel<T, MC, 2>, sm_c);
+                            coupling_kernel<T, MC, 2><<<nt, kThreads, sm_c, h->side>>>(v, S, c0, zmax, nsplit);
+                        } else if (ni <= 4) {
+                            set_smem<T, MC>((const void*)coupling_kernel<T, MC, 4>, sm_c);
+                            coupling_kernel<T, MC, 4><<<nt, kThreads, sm_c, h->side>>>(v, S, c0, zmax, nsplit);
+                        } else {
+                            throw Error(PH_ERR_UNSUPPORTED, "p_s^d too large for the coupling kernel");
+                        }
+                    }
+                    PH_LAUNCH("coupling_kernel");
                 }
-                PH_LAUNCH("coupling_kernel");
                 for (int l = h->min_far_level; l < plan.depth; ++l) {
                     if (!h->level_has_inner_child[l]) continue;
                     int cnt = h->level_nodes_off[l + 1] - h->level_nodes_off[l];

@@ -46,6 +46,23 @@ def test_parity_small(case):
     A.close()
 
 
+@pytest.mark.parametrize("coupling", ["explicit", "chain"])
+@pytest.mark.parametrize("d,prec,m", [(2, "fp64", 2), (3, "fp32", 16)])
+def test_coupling_modes(coupling, d, prec, m):
+    """Both H^2 coupling stages: explicit L_k / R_k products and the TT chain (§4.5)."""
+    n = 1200 if d == 2 else 2500
+    P = inputs.uniform_points(n, d, 55 + d)
+    X = inputs.gaussian_rhs(n, m, 56 + d)
+    lmax, eta, ps = (3, 1.0, 6) if d == 2 else (2, np.sqrt(3.0), 4)
+    A, M, targets = build_pair(P, "matern52", [0.1], [0.6], [12], ps, lmax, eta, 1e-7, 0, "h2", prec,
+                               coupling=coupling, targets_every=None if d == 2 else 9)
+    rows = None if targets is None else target_rows(targets)
+    ref = M.matvec(M.instantiate([0.31], targets), X, targets)
+    got = device_apply(A, [0.31], X, prec)
+    assert np.all(rel_err_rows(ref, got, rows) <= TOL[prec])
+    A.close()
+
+
 def test_parity_3d_h2_fp32_sampled_rows():
     """3-D Matern 3/2, eta = sqrt(3), 16 right-hand sides; oracle on a sample of target leaves."""
     n = 3000
