@@ -29,7 +29,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_2511_03109_gb300 import inputs  # noqa: E402
+from paper_2511_03109_gb300 import inputs, sharding  # noqa: E402
 
 WL = inputs.LARGE_3D_MATERN_H2
 METRIC = "online instantiate+H-MVM (theta*RHS)/s and % HBM roofline at rel.err vs FP64 oracle"
@@ -47,6 +47,36 @@ def workload_config():
         "l2": "no flush: the near-field cores streamed every step (> 4 GB) exceed the 129 MB L2",
         "parallelism": "theta-sharded replicas, one process per GPU",
     }
+
+
+KERNEL_OF_KIND = {"near": "near_kernel", "coupling": "coupling_a_staged_kernel", "coupling_b": "coupling_b_kernel",
+                  "combine": "combine_kernel", "upsweep_leaf": "upsweep_leaf_kernel"}
+
+
+def kernel_source_hash(name):
+    """sha256 (16 hex digits) of a kernel's template definition in csrc/online.cu."""
+    import hashlib
+    import re
+    src = open(os.path.join(ROOT, "paper_2511_03109_gb300", "csrc", "online.cu")).read()
+    m = re.search(r"__global__[^\n]*\n?[^\n]*\b" + re.escape(name) + r"\(", src)
+    if not m:
+        return None
+    start = src.rfind("template", 0, m.start())
+    end = src.index("\n}\n", m.end()) + 3
+    return hashlib.sha256(src[start:end].encode()).hexdigest()[:16]
+
+
+def measured_traffic(kind):
+    """ncu DRAM bytes per launch of the kernel, or None if it changed since the capture."""
+    name = KERNEL_OF_KIND.get(kind)
+    try:
+        with open(os.path.join(ROOT, "profiles", "kernel_traffic.json")) as f:
+            rec = json.load(f).get(name)
+    except Exception:
+        return None
+    if not rec or rec.get("source_sha256") != kernel_source_hash(name):
+        return None
+    return rec["bytes_per_launch"]
 
 
 def load_peaks():
@@ -183,7 +213,7 @@ def run_gpu(args, rank, world, local_rank):
     log(f"offline done in {info['offline_seconds']:.1f} s")
     total_steps = args.warmup + args.steps
     thetas_all = inputs.uniform_thetas(WL.theta_lo, WL.theta_hi, max(30, world * total_steps), WL.theta_seed)
-    thetas = thetas_all[rank::world][:total_steps]
+    thetas = sharding.shard(thetas_all, rank, world)[:total_steps]
     stream = torch.cuda.current_stream(dev)
     sp = stream.cuda_stream
     X = torch.tensor(Xh.T, dtype=torch.float32, device=dev).contiguous()  # column-major n x m
@@ -215,11 +245,9 @@ def run_gpu(args, rank, world, local_rank):
     ms = ev0.elapsed_time(ev1)
     clocks = sampler.stop()
     prof = A.profile_read()
+    kinds = {k: v for k, v in prof.items() if v[1] > 0}
     A.profile(False)
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = sharding.max_over_ranks(ms, dist)
 
     # end to end through the host entry point: pinned host X in, Y out every step
     Xp = torch.tensor(Xh.T, dtype=torch.float32).contiguous().pin_memory()
@@ -239,10 +267,7 @@ def run_gpu(args, rank, world, local_rank):
         step_host(thetas[args.warmup + k])
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = sharding.max_over_ranks(e2e_s, dist)
 
     if rank != 0:
         if dist:
@@ -253,10 +278,22 @@ def run_gpu(args, rank, world, local_rank):
 
     value = world * args.steps * m / (ms / 1e3)
     peaks, peak_kind = load_peaks()
-    # dominant kernel by device time
-    kinds = {k: v for k, v in prof.items() if v[1] > 0}
-    dom = max(kinds, key=lambda k: kinds[k][0])
-    dom_ms, dom_launches = kinds[dom]
+    # roofline pass: the same steps with the far and near paths serialised on one stream, so that
+    # each kernel's CUDA-event time is its own (in the timed region they overlap)
+    A.set_overlap(False)
+    A.profile(True)
+    for k in range(2):
+        step(thetas[k])
+    A.profile_read()
+    nprof = min(args.steps, 10)
+    for k in range(nprof):
+        step(thetas[args.warmup + k % args.steps])
+    torch.cuda.synchronize()
+    alone = {k: v for k, v in A.profile_read().items() if v[1] > 0}
+    A.profile(False)
+    A.set_overlap(True)
+    dom = max(alone, key=lambda k: alone[k][0])
+    dom_ms, dom_launches = alone[dom]
     avg_ms = dom_ms / dom_launches
     sc = 4
     if dom == "near":
@@ -264,15 +301,18 @@ def run_gpu(args, rank, world, local_rank):
         roof = {"bound": "hbm", "achieved": alg / (avg_ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "per_launch_bytes": alg}
     else:
-        # FP32 SIMT flops of the far path: the coupling chain and sweeps
-        fl = (info["flops_per_rhs"] - 2.0 * info["near_entries"]) * m
+        # FP32 CUDA-core flops of the kernel (flop counts of the built structure, per launch)
+        per_rhs = {"coupling": info["coupling_a_flops_per_rhs"], "coupling_b": info["coupling_b_flops_per_rhs"]}
+        fl = per_rhs.get(dom, info["flops_per_rhs"] - 2.0 * info["near_entries"]) * m
         alu_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) / 1e6
         roof = {"bound": "alu", "achieved": fl / (avg_ms / 1e3) / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
-                "per_launch_flops": fl}
+                "per_launch_flops": fl,
+                "peak_note": "FP32 FMA lanes: 152 SMs x 128 x 2 flops x max SM clock"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["kernel"] = dom + "_kernel"
+    roof["kernel"] = KERNEL_OF_KIND.get(dom, dom)
     roof["peak_source"] = peak_kind
-    roof["traffic"] = None
+    roof["traffic"] = measured_traffic(dom)
+    roof["timing"] = "CUDA events around each launch, far and near paths serialised (roofline pass)"
     gpu_launches = int(sum(v[1] for v in prof.values()))
     # whole-step bytes over the step time, for context
     step_bytes = info["alg_bytes_per_call"] + 2.0 * n * m * sc
@@ -283,6 +323,7 @@ def run_gpu(args, rank, world, local_rank):
         "config": workload_config(), "roofline": roof,
         "step_hbm_fraction": step_bytes / (ms / args.steps / 1e3) / 1e9 / peaks["hbm_gbs"],
         "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kinds.items()},
+        "kernels_ms_alone": {k: v[0] / v[1] for k, v in alone.items()},
         "gpu_launches": gpu_launches, "clocks": clocks,
         "e2e": {"value": world * args.steps * m / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": n * m * sc + 8 * WL.d, "d2h_bytes_per_step": n * m * sc},

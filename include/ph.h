@@ -107,6 +107,8 @@ typedef struct {
                                     (excluding X / Y); add 2 * n * m * scalar for X and Y */
     double flops_per_rhs;    /* online flops per right-hand side (instantiate excluded) */
     double offline_seconds;  /* wall time of ph_offline_build */
+    double coupling_a_flops_per_rhs;  /* explicit coupling phase 1 (H_k R_k^T xhat), or the whole TT chain */
+    double coupling_b_flops_per_rhs;  /* explicit coupling phase 2 (sum L_k z_b); 0 for the TT chain */
 } ph_info;
 
 /* Build the parametric matrix (offline stage).
@@ -205,6 +207,12 @@ ph_status ph_plan(const double* points, long n, int d, int l_max, double eta,
  * since enabling), then starts a new count.  ms and launches are host arrays of
  * PH_PROF_KINDS elements. */
 #define PH_PROF_KINDS 10
+
+/* ph_matvec runs its far-field chain on a second, high-priority stream concurrently with the
+ * near field (enable = 1, the default).  enable = 0 runs every kernel in order on the caller's
+ * stream, so that per-kernel times measured with ph_profile_read are those of each kernel on
+ * its own (used for roofline reports; the result is the same). */
+ph_status ph_set_overlap(ph_handle* h, int enable);
 ph_status ph_profile_enable(ph_handle* h, int enable);
 ph_status ph_profile_read(ph_handle* h, double* ms, long* launches);
 

@@ -540,7 +540,10 @@ ph_status ph_get_info(const ph_handle* h, ph_info* info) {
             fl += 2.0 * (plan.nodes[plan.far_s[b]].size() * (double)rk[d] +
                          plan.nodes[plan.far_t[b]].size() * (double)rk[d + 1] + (double)rk[d] * rk[d + 1]);
         } else if (h->opts.coupling == 0) {
-            fl += 2.0 * PD * ((double)rk[d + 1] + rk[d]) + 2.0 * rk[d] * rk[d + 1];
+            const double fa = 2.0 * PD * rk[d + 1] + 2.0 * rk[d] * rk[d + 1], fbb = 2.0 * PD * rk[d];
+            r.coupling_a_flops_per_rhs += fa;
+            r.coupling_b_flops_per_rhs += fbb;
+            fl += fa + fbb;
         } else {
             double a = PD / p, chain = 0;
             for (int i = 0; i < d; ++i) {  // right cores
@@ -556,6 +559,7 @@ ph_status ph_get_info(const ph_handle* h, ph_info* info) {
                 bsz *= p;
             }
             fl += chain;
+            r.coupling_a_flops_per_rhs += chain;
         }
     }
     if (h->opts.fmt == PH_FMT_H2 && !plan.far_s.empty()) {
@@ -565,6 +569,12 @@ ph_status ph_get_info(const ph_handle* h, ph_info* info) {
     r.flops_per_rhs = fl;
     r.offline_seconds = h->offline_seconds;
     *info = r;
+    return PH_OK;
+}
+
+ph_status ph_set_overlap(ph_handle* h, int enable) {
+    if (!h) return fail(nullptr, PH_ERR_INVALID_ARG, "ph_set_overlap: NULL handle");
+    h->overlap = enable != 0;
     return PH_OK;
 }
 

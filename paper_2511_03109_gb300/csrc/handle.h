@@ -167,6 +167,7 @@ struct ph_handle {
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool instantiated = false;
+    bool overlap = true;                        // far path on the side stream (ph_set_overlap)
     // per-kernel timing (ph_profile_enable / ph_profile_read)
     bool prof = false;
     std::vector<cudaEvent_t> prof_pool;

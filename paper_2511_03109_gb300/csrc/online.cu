@@ -1020,33 +1020,56 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(DevView<T> v, T* __re
         }
         __syncthreads();
     }
-    for (int i = threadIdx.x; i < ns; i += blockDim.x) {
-        const long long row = row0 + i;
-        T acc[MC];
-#pragma unroll
-        for (int c = 0; c < MC; ++c) acc[c] = T(0);
-        for (int it = v.items_by_leaf[leaf]; it < v.items_by_leaf[leaf + 1]; ++it)
-#pragma unroll
-            for (int c = 0; c < MC; ++c) acc[c] += v.partials[((long long)it * v.part_stride + i) * S + c0 + c];
+    constexpr int CT = MC < 4 ? MC : 4, CQ = MC / CT;
+    // thread item = (row i, CT columns); U factors of the rows staged per chunk of rows
+    T* su = sy + (size_t)PD * MC;  // reuses the transfer scratch: kThreads rows x d x p_s
+    const int p1 = ps, p2 = d > 1 ? ps : 1, p3 = d > 2 ? ps : 1;
+    for (int r0 = 0; r0 < ns; r0 += kThreads) {
+        const int nr = min(kThreads, ns - r0);
         if (h2) {
-            const T* u = v.U + row * d * ps;
-            for (int I = 0; I < PD; ++I) {
-                int r = I;
-                T w = u[r % ps];
-                if (d > 1) { r /= ps; w *= u[ps + r % ps]; }
-                if (d > 2) { r /= ps; w *= u[2 * ps + r % ps]; }
-#pragma unroll
-                for (int c = 0; c < MC; ++c) acc[c] += w * sy[I * MC + c];
-            }
-        } else {
-            for (int sl = 0; sl < v.n_far_levels; ++sl)
-#pragma unroll
-                for (int c = 0; c < MC; ++c) acc[c] += v.yfar[((long long)sl * v.n + row) * S + c0 + c];
+            __syncthreads();
+            for (int e = threadIdx.x; e < nr * d * ps; e += blockDim.x)
+                su[e] = v.U[(long long)(row0 + r0) * d * ps + e];
+            __syncthreads();
         }
-        const int orig = v.perm[row];
+        for (int it = threadIdx.x; it < nr * CQ; it += blockDim.x) {
+            const int i = r0 + it / CQ, cq = it % CQ;
+            const long long row = row0 + i;
+            T acc[CT];
 #pragma unroll
-        for (int c = 0; c < MC; ++c)
-            if (c0 + c < m) Y[orig + (long long)(c0 + c) * ldy] = acc[c];
+            for (int c = 0; c < CT; ++c) acc[c] = T(0);
+            for (int q = v.items_by_leaf[leaf]; q < v.items_by_leaf[leaf + 1]; ++q) {
+                T x[CT];
+                load_ct<T, CT>(v.partials + ((long long)q * v.part_stride + i) * S + c0 + cq * CT, x);
+#pragma unroll
+                for (int c = 0; c < CT; ++c) acc[c] += x[c];
+            }
+            if (h2) {
+                const T* u = su + (it / CQ) * d * ps;
+                int I = 0;
+                for (int i3 = 0; i3 < p3; ++i3) {
+                    const T w3 = d > 2 ? u[2 * ps + i3] : T(1);
+                    for (int i2 = 0; i2 < p2; ++i2) {
+                        const T w23 = d > 1 ? w3 * u[ps + i2] : w3;
+                        for (int i1 = 0; i1 < p1; ++i1, ++I) {
+                            const T w = w23 * u[i1];
+                            T yv[CT];
+                            load_ct<T, CT>(sy + I * MC + cq * CT, yv);
+#pragma unroll
+                            for (int c = 0; c < CT; ++c) acc[c] += w * yv[c];
+                        }
+                    }
+                }
+            } else {
+                for (int sl = 0; sl < v.n_far_levels; ++sl)
+#pragma unroll
+                    for (int c = 0; c < CT; ++c) acc[c] += v.yfar[((long long)sl * v.n + row) * S + c0 + cq * CT + c];
+            }
+            const int orig = v.perm[row];
+#pragma unroll
+            for (int c = 0; c < CT; ++c)
+                if (c0 + cq * CT + c < m) Y[orig + (long long)(c0 + cq * CT + c) * ldy] = acc[c];
+        }
     }
 }
 
@@ -1073,8 +1096,11 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
     const bool h2 = (h->opts.fmt == PH_FMT_H2);
     const int PD = v.PD;
     // fork: the far path runs on the side stream, concurrently with the near field
-    PH_CUDA(cudaEventRecord(h->ev_fork, stream));
-    PH_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+    cudaStream_t far = h->overlap ? h->side : stream;
+    if (h->overlap) {
+        PH_CUDA(cudaEventRecord(h->ev_fork, stream));
+        PH_CUDA(cudaStreamWaitEvent(far, h->ev_fork, 0));
+    }
     for (int c0 = 0; c0 < S; c0 += MC) {
         size_t smem = ((size_t)maxleaf * MC + (size_t)kThreads * MC + kMaxNearRank) * sizeof(T);
         set_smem<T, MC>((const void*)near_kernel<T, MC>, smem);
@@ -1085,13 +1111,13 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
     if (!plan.far_targets.empty()) {
         for (int c0 = 0; c0 < S; c0 += MC) {
             if (h2) {
-                PH_CUDA(cudaMemsetAsync(v.xhat, 0, (size_t)v.n_nodes * PD * S * sizeof(T), h->side));
+                PH_CUDA(cudaMemsetAsync(v.xhat, 0, (size_t)v.n_nodes * PD * S * sizeof(T), far));
                 size_t sm_leaf = ((size_t)32 * kMaxDim * kMaxPs + 32 * MC + ((2 * v.p_s * v.p_s + 3) & ~3) +
                                   2 * (size_t)PD * MC) * sizeof(T);
                 set_smem<T, MC>((const void*)upsweep_leaf_kernel<T, MC>, sm_leaf);
                 {
-                    ProfScope ps(h, 3, h->side);
-                    upsweep_leaf_kernel<T, MC><<<nleaves, kThreads, sm_leaf, h->side>>>(v, S, c0, h->min_far_level);
+                    ProfScope ps(h, 3, far);
+                    upsweep_leaf_kernel<T, MC><<<nleaves, kThreads, sm_leaf, far>>>(v, S, c0, h->min_far_level);
                 }
                 PH_LAUNCH("upsweep_leaf_kernel");
                 size_t sm_tr = ((size_t)((2 * v.p_s * v.p_s + 3) & ~3) + 3 * (size_t)PD * MC) * sizeof(T);
@@ -1100,30 +1126,30 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
                     if (!h->level_has_inner_child[l]) continue;
                     int cnt = h->level_nodes_off[l + 1] - h->level_nodes_off[l];
                     if (cnt == 0) continue;
-                    ProfScope ps(h, 4, h->side);
-                    transfer_kernel<T, MC><<<cnt, kThreads, sm_tr, h->side>>>(
+                    ProfScope ps(h, 4, far);
+                    transfer_kernel<T, MC><<<cnt, kThreads, sm_tr, far>>>(
                         v, h->d_level_nodes + h->level_nodes_off[l], S, c0, true, v.xhat, v.xhat);
                     PH_LAUNCH("transfer_kernel(up)");
                 }
                 if (h->opts.coupling == 0) {
                     {
-                        ProfScope ps(h, 5, h->side);
+                        ProfScope ps(h, 5, far);
                         constexpr int NMAX = 4 * MC;
                         const bool staged = (MC >= 4) && (PD % 32 == 0) && (h->rank_max_lr <= 64);
                         if (staged) {
                             size_t sm_a = ((size_t)2 * 64 * 36 + 2 * 32 * (NMAX + 4) + 64 * (NMAX + 4)) * sizeof(T);
                             set_smem<T, MC>((const void*)coupling_a_staged_kernel<T, MC>, sm_a);
-                            coupling_a_staged_kernel<T, MC><<<std::max(1, v.n_citems), kThreads, sm_a, h->side>>>(
+                            coupling_a_staged_kernel<T, MC><<<std::max(1, v.n_citems), kThreads, sm_a, far>>>(
                                 v, S, c0);
                         } else {
                             size_t sm_a = ((size_t)64 * 33 + 32 * (NMAX + 4) + 64 * (NMAX + 4)) * sizeof(T);
                             set_smem<T, MC>((const void*)coupling_a_kernel<T, MC>, sm_a);
-                            coupling_a_kernel<T, MC><<<std::max(1, v.n_citems), kThreads, sm_a, h->side>>>(v, S, c0);
+                            coupling_a_kernel<T, MC><<<std::max(1, v.n_citems), kThreads, sm_a, far>>>(v, S, c0);
                         }
                         PH_LAUNCH("coupling_a_kernel");
                     }
                     {
-                        ProfScope ps(h, 9, h->side);
+                        ProfScope ps(h, 9, far);
                         constexpr int CQB = (MC < 4) ? 1 : MC / 4;
                         const int itemsb = ((PD + 7) / 8) * CQB;
                         const int nib = (itemsb + kThreads - 1) / kThreads;
@@ -1132,13 +1158,13 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
                         const int nt = (int)plan.far_targets.size() * nsplit;
                         if (nib <= 1) {
                             set_smem<T, MC>((const void*)coupling_b_kernel<T, MC, 1>, sm_b);
-                            coupling_b_kernel<T, MC, 1><<<nt, kThreads, sm_b, h->side>>>(v, S, c0, nsplit);
+                            coupling_b_kernel<T, MC, 1><<<nt, kThreads, sm_b, far>>>(v, S, c0, nsplit);
                         } else if (nib <= 2) {
                             set_smem<T, MC>((const void*)coupling_b_kernel<T, MC, 2>, sm_b);
-                            coupling_b_kernel<T, MC, 2><<<nt, kThreads, sm_b, h->side>>>(v, S, c0, nsplit);
+                            coupling_b_kernel<T, MC, 2><<<nt, kThreads, sm_b, far>>>(v, S, c0, nsplit);
                         } else if (nib <= 4) {
                             set_smem<T, MC>((const void*)coupling_b_kernel<T, MC, 4>, sm_b);
-                            coupling_b_kernel<T, MC, 4><<<nt, kThreads, sm_b, h->side>>>(v, S, c0, nsplit);
+                            coupling_b_kernel<T, MC, 4><<<nt, kThreads, sm_b, far>>>(v, S, c0, nsplit);
                         } else {
                             throw Error(PH_ERR_UNSUPPORTED, "p_s^d too large for the coupling kernel");
                         }
@@ -1152,17 +1178,17 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
                     const int ni = (items_last + kThreads - 1) / kThreads;
                     const int nsplit = 4;
                     {
-                        ProfScope ps(h, 5, h->side);
+                        ProfScope ps(h, 5, far);
                         const int nt = (int)plan.far_targets.size() * nsplit;
                         if (ni <= 1) {
                             set_smem<T, MC>((const void*)coupling_kernel<T, MC, 1>, sm_c);
-                            coupling_kernel<T, MC, 1><<<nt, kThreads, sm_c, h->side>>>(v, S, c0, zmax, nsplit);
+                            coupling_kernel<T, MC, 1><<<nt, kThreads, sm_c, far>>>(v, S, c0, zmax, nsplit);
                         } else if (ni <= 2) {
                             set_smem<T, MC>((const void*)coupling_kernel<T, MC, 2>, sm_c);
-                            coupling_kernel<T, MC, 2><<<nt, kThreads, sm_c, h->side>>>(v, S, c0, zmax, nsplit);
+                            coupling_kernel<T, MC, 2><<<nt, kThreads, sm_c, far>>>(v, S, c0, zmax, nsplit);
                         } else if (ni <= 4) {
                             set_smem<T, MC>((const void*)coupling_kernel<T, MC, 4>, sm_c);
-                            coupling_kernel<T, MC, 4><<<nt, kThreads, sm_c, h->side>>>(v, S, c0, zmax, nsplit);
+                            coupling_kernel<T, MC, 4><<<nt, kThreads, sm_c, far>>>(v, S, c0, zmax, nsplit);
                         } else {
                             throw Error(PH_ERR_UNSUPPORTED, "p_s^d too large for the coupling kernel");
                         }
@@ -1173,8 +1199,8 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
                     if (!h->level_has_inner_child[l]) continue;
                     int cnt = h->level_nodes_off[l + 1] - h->level_nodes_off[l];
                     if (cnt == 0) continue;
-                    ProfScope ps(h, 6, h->side);
-                    transfer_kernel<T, MC><<<cnt, kThreads, sm_tr, h->side>>>(
+                    ProfScope ps(h, 6, far);
+                    transfer_kernel<T, MC><<<cnt, kThreads, sm_tr, far>>>(
                         v, h->d_level_nodes + h->level_nodes_off[l], S, c0, false, v.yhat, v.yhat);
                     PH_LAUNCH("transfer_kernel(down)");
                 }
@@ -1187,16 +1213,19 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
                 }
                 size_t sm_h = ((size_t)maxnode * MC + 2 * (size_t)rmax * MC) * sizeof(T);
                 set_smem<T, MC>((const void*)far_h_kernel<T, MC>, sm_h);
-                ProfScope ps(h, 7, h->side);
-                far_h_kernel<T, MC><<<(int)plan.far_targets.size(), kThreads, sm_h, h->side>>>(v, S, c0, rmax);
+                ProfScope ps(h, 7, far);
+                far_h_kernel<T, MC><<<(int)plan.far_targets.size(), kThreads, sm_h, far>>>(v, S, c0, rmax);
                 PH_LAUNCH("far_h_kernel");
             }
         }
     }
-    PH_CUDA(cudaEventRecord(h->ev_join, h->side));
-    PH_CUDA(cudaStreamWaitEvent(stream, h->ev_join, 0));
+    if (h->overlap) {
+        PH_CUDA(cudaEventRecord(h->ev_join, far));
+        PH_CUDA(cudaStreamWaitEvent(stream, h->ev_join, 0));
+    }
     for (int c0 = 0; c0 < S; c0 += MC) {
-        size_t sm = ((size_t)3 * PD * MC + ((2 * v.p_s * v.p_s + 3) & ~3)) * sizeof(T);
+        size_t sm = ((size_t)PD * MC + std::max((size_t)2 * PD * MC + ((2 * v.p_s * v.p_s + 3) & ~3),
+                                                (size_t)kThreads * v.d * v.p_s)) * sizeof(T);
         set_smem<T, MC>((const void*)combine_kernel<T, MC>, sm);
         ProfScope ps(h, 8, stream);
         combine_kernel<T, MC><<<nleaves, kThreads, sm, stream>>>(v, Y, ldy, m, S, c0,

@@ -53,7 +53,8 @@ class Info(C.Structure):
                 ("far_rank_mean", C.c_double), ("near_bytes", C.c_long),
                 ("near_theta_bytes", C.c_long), ("far_bytes", C.c_long),
                 ("basis_bytes", C.c_long), ("alg_bytes_per_call", C.c_double),
-                ("flops_per_rhs", C.c_double), ("offline_seconds", C.c_double)]
+                ("flops_per_rhs", C.c_double), ("offline_seconds", C.c_double),
+                ("coupling_a_flops_per_rhs", C.c_double), ("coupling_b_flops_per_rhs", C.c_double)]
 
     def as_dict(self):
         out = {}
@@ -82,6 +83,7 @@ _SIGS = {
                           C.POINTER(C.c_long), C.POINTER(C.c_int)]),
     "ph_version": (C.c_char_p, []),
     "ph_profile_enable": (C.c_int, [_H, C.c_int]),
+    "ph_set_overlap": (C.c_int, [_H, C.c_int]),
     "ph_profile_read": (C.c_int, [_H, C.POINTER(C.c_double), C.POINTER(C.c_long)]),
 }
 
@@ -203,6 +205,9 @@ class ParametricMatrix:
         s = torch.cuda.current_stream(X.device).cuda_stream if stream is None else stream
         self.matvec_ptr(Xc.data_ptr(), n, m, Y.data_ptr(), n, s)
         return Y
+
+    def set_overlap(self, enable=True):
+        return check(ph_set_overlap(self.h, 1 if enable else 0), self.h)
 
     def profile(self, enable=True):
         return check(ph_profile_enable(self.h, 1 if enable else 0), self.h)
