@@ -255,7 +255,7 @@ void refresh_views(ph_handle* h) {
     put(par);                       // 24
     // far blocks grouped by translation class, and the key-grouped items of the explicit coupling
     // (up to kCouplingItemBlocks blocks of one key per item)
-    constexpr int kCouplingItemBlocks = 4;
+    constexpr int kCouplingItemBlocks = 16;
     const int nkeys = (int)plan.key_rep.size();
     h->kb_off.assign(nkeys + 1, 0);
     for (int k : plan.far_key) h->kb_off[k + 1]++;
@@ -275,10 +275,13 @@ void refresh_views(ph_handle* h) {
         h->zstride = std::max(h->zstride, h->key_ranks[(size_t)k * (h->Delta + 1) + plan.d]);
         h->rank_max_lr = std::max(h->rank_max_lr, std::max(h->key_ranks[(size_t)k * (h->Delta + 1) + plan.d],
                                                            h->key_ranks[(size_t)k * (h->Delta + 1) + plan.d + 1]));
-        for (int i = h->kb_off[k]; i < h->kb_off[k + 1]; i += kCouplingItemBlocks) {
+        // blocks per item: about 4096 outputs of P = R_k^T X per CTA at 16 right-hand sides
+        const int rp4 = (h->key_ranks[(size_t)k * (h->Delta + 1) + plan.d + 1] + 3) & ~3;
+        const int nb = std::max(1, std::min(kCouplingItemBlocks, 256 / std::max(4, rp4)));
+        for (int i = h->kb_off[k]; i < h->kb_off[k + 1]; i += nb) {
             h->citem_key.push_back(k);
             h->citem_first.push_back(i);
-            h->citem_count.push_back(std::min(kCouplingItemBlocks, h->kb_off[k + 1] - i));
+            h->citem_count.push_back(std::min(nb, h->kb_off[k + 1] - i));
         }
     }
     put(h->kb_off);                 // 25

@@ -681,7 +681,12 @@ ph_status offline_build(ph_handle* h, const double* points, long n) {
             }
             h->key_lroff[key] = (long long)lr.size();
             lr.insert(lr.end(), L.begin(), L.end());  // PD x r_d column-major == L^T row-major
-            lr.insert(lr.end(), Q.begin(), Q.end());  // PD x r_{d+1} column-major == R^T row-major
+            // R_k row-major, rows padded to a multiple of 4: [J * rp4 + s], zero beyond r_{d+1}
+            const int rpr = rk[d + dt], rp4 = (rpr + 3) & ~3;
+            const size_t base = lr.size();
+            lr.resize(base + (size_t)h->PD * rp4, 0.0);
+            for (int sidx = 0; sidx < rpr; ++sidx)
+                for (long long J = 0; J < h->PD; ++J) lr[base + (size_t)J * rp4 + sidx] = Q[(size_t)J + (size_t)h->PD * sidx];
         }
     }
     h->lr_elems = (long long)lr.size();

@@ -658,7 +658,7 @@ __global__ void __launch_bounds__(kThreads, 3) coupling_kernel(DevView<T> v, int
 // whose A operand is shared by all N = blocks x MC columns of the item.
 template <typename T, int MC>
 __global__ void __launch_bounds__(kThreads, 2) coupling_a_kernel(DevView<T> v, int S, int c0) {
-    constexpr int KC = 32, NMAX = 4 * MC, BS = NMAX + 4, AS = KC + 1;
+    constexpr int KC = 32, NMAX = 64, BS = NMAX + 4, AS = KC + 1;
     extern __shared__ unsigned char smem_raw[];
     T* As = reinterpret_cast<T*>(smem_raw);  // 64 x AS
     T* Bs = As + 64 * AS;                     // KC x BS
@@ -667,68 +667,73 @@ __global__ void __launch_bounds__(kThreads, 2) coupling_a_kernel(DevView<T> v, i
     const int key = v.citem_key[item], first = v.citem_first[item], cnt = v.citem_count[item];
     const int* rk = v.key_ranks + (size_t)key * (v.Delta + 1);
     const int rd = rk[v.d], rp = rk[v.d + 1];
-    const int PD = v.PD, N = cnt * MC;
-    const T* Rt = v.far_lr + v.key_lroff[key] + (long long)rd * PD;
+    const int PD = v.PD, Ntot = cnt * MC;
+    const int rp4 = (rp + 3) & ~3;
+    const T* Rk = v.far_lr + v.key_lroff[key] + (long long)rd * PD;  // R_k row-major [J * rp4 + s]
+    const T* H = v.H + v.key_hoff[key];
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    T acc[4][4];
+    for (int n0 = 0; n0 < Ntot; n0 += NMAX) {  // columns in passes of 64
+        const int N = min(NMAX, Ntot - n0);
+        T acc[4][4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[u][j] = T(0);
-    for (int k0 = 0; k0 < PD; k0 += KC) {
-        const int kn = min(KC, PD - k0);
-        __syncthreads();
-        for (int e = threadIdx.x; e < rp * KC; e += blockDim.x) {
-            const int row = e / KC, kk = e % KC;
-            As[row * AS + kk] = (kk < kn) ? Rt[(long long)row * PD + k0 + kk] : T(0);
-        }
-        for (int e = threadIdx.x; e < KC * N; e += blockDim.x) {
-            const int kk = e / N, col = e % N;
-            const int b = col / MC, c = col % MC;
-            const int t = v.fb_t[v.kb_list[first + b]];
-            Bs[kk * BS + col] = (kk < kn) ? v.xhat[((long long)t * PD + k0 + kk) * S + c0 + c] : T(0);
-        }
-        __syncthreads();
-        if (4 * tx < N) {
+            for (int j = 0; j < 4; ++j) acc[u][j] = T(0);
+        for (int k0 = 0; k0 < PD; k0 += KC) {
+            const int kn = min(KC, PD - k0);
+            __syncthreads();
+            for (int e = threadIdx.x; e < rp * KC; e += blockDim.x) {
+                const int row = e / KC, kk = e % KC;
+                As[row * AS + kk] = (kk < kn) ? Rk[(long long)(k0 + kk) * rp4 + row] : T(0);
+            }
+            for (int e = threadIdx.x; e < KC * N; e += blockDim.x) {
+                const int kk = e / N, col = n0 + e % N;
+                const int b = col / MC, c = col % MC;
+                const int t = v.fb_t[v.kb_list[first + b]];
+                Bs[kk * BS + (col - n0)] = (kk < kn) ? v.xhat[((long long)t * PD + k0 + kk) * S + c0 + c] : T(0);
+            }
+            __syncthreads();
+            if (4 * tx < N) {
 #pragma unroll 4
-            for (int kk = 0; kk < KC; ++kk) {
-                T bv[4];
+                for (int kk = 0; kk < KC; ++kk) {
+                    T bv[4];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) bv[j] = Bs[kk * BS + 4 * tx + j];
+                    for (int j = 0; j < 4; ++j) bv[j] = Bs[kk * BS + 4 * tx + j];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const T av = As[(ty + 16 * u) * AS + kk];
+                    for (int u = 0; u < 4; ++u) {
+                        const T av = As[(ty + 16 * u) * AS + kk];
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[u][j] += av * bv[j];
+                        for (int j = 0; j < 4; ++j) acc[u][j] += av * bv[j];
+                    }
                 }
             }
         }
-    }
-    __syncthreads();
+        __syncthreads();
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
-        if (ty + 16 * u < rp)
+        for (int u = 0; u < 4; ++u)
+            if (ty + 16 * u < rp)
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (4 * tx + j < N) Ps[(ty + 16 * u) * BS + 4 * tx + j] = acc[u][j];
-    __syncthreads();
-    const T* H = v.H + v.key_hoff[key];
+                for (int j = 0; j < 4; ++j)
+                    if (4 * tx + j < N) Ps[(ty + 16 * u) * BS + 4 * tx + j] = acc[u][j];
+        __syncthreads();
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const int r = ty + 16 * u;
-        if (r >= rd) continue;
-        T z[4] = {T(0), T(0), T(0), T(0)};
-        for (int q = 0; q < rp; ++q) {
-            const T hv = H[r + rd * q];
+        for (int u = 0; u < 4; ++u) {
+            const int r = ty + 16 * u;
+            if (r >= rd) continue;
+            T z[4] = {T(0), T(0), T(0), T(0)};
+            for (int q = 0; q < rp; ++q) {
+                const T hv = H[r + rd * q];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) z[j] += hv * Ps[q * BS + 4 * tx + j];
-        }
+                for (int j = 0; j < 4; ++j) z[j] += hv * Ps[q * BS + 4 * tx + j];
+            }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int col = 4 * tx + j;
-            if (col < N) {
-                const int fb = v.kb_list[first + col / MC];
-                v.zbuf[((long long)fb * v.zstride + r) * S + c0 + col % MC] = z[j];
+            for (int j = 0; j < 4; ++j) {
+                const int col = 4 * tx + j;
+                if (col < N) {
+                    const int gcol = n0 + col;
+                    const int fb = v.kb_list[first + gcol / MC];
+                    v.zbuf[((long long)fb * v.zstride + r) * S + c0 + gcol % MC] = z[j];
+                }
             }
         }
     }
@@ -742,34 +747,36 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-// Phase 1 of the explicit coupling, staged path (p_s^d a multiple of 32, MC >= 4): the chunks of
-// R_k^T (r' x 32) and of the item's xhat_t columns (32 x N) are copied into shared memory with
-// 16-byte asynchronous copies, two chunks in flight, so the copy of chunk c + 1 overlaps the
-// products of chunk c.  Same result as coupling_a_kernel.
+// Phase 1 of the explicit coupling, staged path (p_s^d a multiple of 32, MC >= 4): for an item of
+// nb far blocks of class k (nb chosen so that r'_4 x nb MC ~ 4096 outputs, r'_4 = r_{d+1}
+// rounded up to 4), P = R_k^T X with X the items' xhat_t columns, then z_b = H_k P.  Chunks of
+// R_k (32 x r'_4, row-major) and of X (32 x N) are copied into shared memory with 16-byte
+// asynchronous copies, two chunks in flight, so the copy of chunk c + 1 overlaps the products of
+// chunk c.  Thread tile: 4 rows of P x 4 columns.
 template <typename T, int MC>
 __global__ void __launch_bounds__(kThreads, 2) coupling_a_staged_kernel(DevView<T> v, int S, int c0) {
-    constexpr int KC = 32, NMAX = 4 * MC, BS = NMAX + 4, AS = KC + 4;
+    constexpr int KC = 32, NMAX = 256, BS = NMAX + 4;
     constexpr int EV = 16 / sizeof(T);  // elements per 16-byte copy
     extern __shared__ unsigned char smem_raw[];
-    T* As = reinterpret_cast<T*>(smem_raw);  // 2 x 64 x AS
-    T* Bs = As + 2 * 64 * AS;                 // 2 x KC x BS
-    T* Ps = Bs + 2 * KC * BS;                 // 64 x BS
-    __shared__ long long colbase[4];
+    T* As = reinterpret_cast<T*>(smem_raw);  // 2 x KC x 64
+    T* Bs = As + 2 * KC * 64;                 // 2 x KC x BS; reused for P (64 x BS) after the K loop
+    __shared__ long long colbase[16];
     const int item = blockIdx.x;
     const int key = v.citem_key[item], first = v.citem_first[item], cnt = v.citem_count[item];
     const int* rk = v.key_ranks + (size_t)key * (v.Delta + 1);
-    const int rd = rk[v.d], rp = rk[v.d + 1];
+    const int rd = rk[v.d], rp = rk[v.d + 1], rp4 = (rp + 3) & ~3;
     const int PD = v.PD, N = cnt * MC;
-    const T* Rt = v.far_lr + v.key_lroff[key] + (long long)rd * PD;
+    const T* Rk = v.far_lr + v.key_lroff[key] + (long long)rd * PD;  // [J * rp4 + s]
     if (threadIdx.x < cnt) colbase[threadIdx.x] = (long long)v.fb_t[v.kb_list[first + threadIdx.x]] * PD * S + c0;
     __syncthreads();
     auto issue = [&](int chunk, int buf) {
         const int k0 = chunk * KC;
-        T* A = As + buf * 64 * AS;
+        T* A = As + buf * KC * 64;
         T* B = Bs + buf * KC * BS;
-        for (int e = threadIdx.x; e < rp * (KC / EV); e += blockDim.x) {
-            const int row = e / (KC / EV), q = e % (KC / EV);
-            cp_async16(A + row * AS + q * EV, Rt + (long long)row * PD + k0 + q * EV);
+        const T* src = Rk + (long long)k0 * rp4;  // KC x rp4 contiguous
+        for (int e = threadIdx.x; e < KC * rp4 / EV; e += blockDim.x) {
+            const int kk = (e * EV) / rp4, q = (e * EV) % rp4;
+            cp_async16(A + kk * 64 + q, src + e * EV);
         }
         for (int e = threadIdx.x; e < cnt * KC * (MC / EV); e += blockDim.x) {
             const int b = e / (KC * (MC / EV)), rest = e % (KC * (MC / EV));
@@ -778,7 +785,10 @@ __global__ void __launch_bounds__(kThreads, 2) coupling_a_staged_kernel(DevView<
         }
         cp_async_commit();
     };
-    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int TR = rp4 / 4;              // row quads of P
+    const int TC = (N + 3) / 4;          // column quads
+    const int tr = threadIdx.x % TR, tc = threadIdx.x / TR;
+    const bool active = tc < TC;
     T acc[4][4];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
@@ -794,44 +804,42 @@ __global__ void __launch_bounds__(kThreads, 2) coupling_a_staged_kernel(DevView<
             cp_async_wait<0>();
         }
         __syncthreads();
-        const T* A = As + (c & 1) * 64 * AS;
-        const T* B = Bs + (c & 1) * KC * BS;
-        if (4 * tx < N) {
+        const T* A = As + (c & 1) * KC * 64 + 4 * tr;
+        const T* B = Bs + (c & 1) * KC * BS + 4 * tc;
+        if (active) {
 #pragma unroll 8
             for (int kk = 0; kk < KC; ++kk) {
-                T bv[4];
-                load_ct<T, 4>(B + kk * BS + 4 * tx, bv);
+                T av[4], bv[4];
+                load_ct<T, 4>(A + kk * 64, av);
+                load_ct<T, 4>(B + kk * BS, bv);
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const T av = A[(ty + 16 * u) * AS + kk];
+                for (int u = 0; u < 4; ++u)
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[u][j] += av * bv[j];
-                }
+                    for (int j = 0; j < 4; ++j) acc[u][j] += av[u] * bv[j];
             }
         }
         __syncthreads();  // the buffer of chunk c is refilled by the issue of chunk c + 2
     }
+    T* Ps = Bs;  // 64 x BS
+    if (active)
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
-        if (ty + 16 * u < rp)
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (4 * tx + j < N) Ps[(ty + 16 * u) * BS + 4 * tx + j] = acc[u][j];
+        for (int u = 0; u < 4; ++u) store_ct<T, 4>(Ps + (4 * tr + u) * BS + 4 * tc, acc[u]);
     __syncthreads();
     const T* H = v.H + v.key_hoff[key];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const int r = ty + 16 * u;
-        if (r >= rd) continue;
+    for (int e = threadIdx.x; e < rd * TC; e += blockDim.x) {
+        const int r = e / TC, cq = e % TC;
         T z[4] = {T(0), T(0), T(0), T(0)};
         for (int q = 0; q < rp; ++q) {
             const T hv = H[r + rd * q];
+            T pv[4];
+            load_ct<T, 4>(Ps + q * BS + 4 * cq, pv);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) z[j] += hv * Ps[q * BS + 4 * tx + j];
+            for (int j = 0; j < 4; ++j) z[j] += hv * pv[j];
         }
-        if (4 * tx < N) {
-            const int fb = v.kb_list[first + (4 * tx) / MC];
-            store_ct<T, 4>(v.zbuf + ((long long)fb * v.zstride + r) * S + c0 + (4 * tx) % MC, z);
+        const int col = 4 * cq;
+        if (col < N) {
+            const int fb = v.kb_list[first + col / MC];
+            store_ct<T, 4>(v.zbuf + ((long long)fb * v.zstride + r) * S + c0 + col % MC, z);
         }
     }
 }
@@ -1134,15 +1142,14 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
                 if (h->opts.coupling == 0) {
                     {
                         ProfScope ps(h, 5, far);
-                        constexpr int NMAX = 4 * MC;
                         const bool staged = (MC >= 4) && (PD % 32 == 0) && (h->rank_max_lr <= 64);
                         if (staged) {
-                            size_t sm_a = ((size_t)2 * 64 * 36 + 2 * 32 * (NMAX + 4) + 64 * (NMAX + 4)) * sizeof(T);
+                            size_t sm_a = ((size_t)2 * 32 * 64 + 2 * 32 * 260) * sizeof(T);
                             set_smem<T, MC>((const void*)coupling_a_staged_kernel<T, MC>, sm_a);
                             coupling_a_staged_kernel<T, MC><<<std::max(1, v.n_citems), kThreads, sm_a, far>>>(
                                 v, S, c0);
                         } else {
-                            size_t sm_a = ((size_t)64 * 33 + 32 * (NMAX + 4) + 64 * (NMAX + 4)) * sizeof(T);
+                            size_t sm_a = ((size_t)64 * 33 + 32 * 68 + 64 * 68) * sizeof(T);
                             set_smem<T, MC>((const void*)coupling_a_kernel<T, MC>, sm_a);
                             coupling_a_kernel<T, MC><<<std::max(1, v.n_citems), kThreads, sm_a, far>>>(v, S, c0);
                         }
