@@ -61,14 +61,25 @@ def kernel_source_hash(name):
     m = re.search(r"__global__[^\n]*\n?[^\n]*\b" + re.escape(name) + r"\(", src)
     if not m:
         return None
-    start = src.rfind("template", 0, m.start())
+    line0 = src.rfind("\n", 0, m.start()) + 1
+    tmpl = src.rfind("template", 0, m.start())
+    # the template line directly above the definition, else the definition itself
+    start = tmpl if tmpl >= 0 and src.count("\n", tmpl, line0) <= 1 and "}" not in src[tmpl:line0] else line0
     end = src.index("\n}\n", m.end()) + 3
     return hashlib.sha256(src[start:end].encode()).hexdigest()[:16]
 
 
-def measured_traffic(kind):
+def kernel_of(kind, info):
+    """The kernel behind a profiling kind; phase 1 of the coupling runs on the tensor cores when
+    the handle reports it."""
+    if kind == "coupling" and info.get("tensor_core_phase1"):
+        return "coupling_a_tc_kernel"
+    return KERNEL_OF_KIND.get(kind, kind)
+
+
+def measured_traffic(kind, info):
     """ncu DRAM bytes per launch of the kernel, or None if it changed since the capture."""
-    name = KERNEL_OF_KIND.get(kind)
+    name = kernel_of(kind, info)
     try:
         with open(os.path.join(ROOT, "profiles", "kernel_traffic.json")) as f:
             rec = json.load(f).get(name)
@@ -304,14 +315,21 @@ def run_gpu(args, rank, world, local_rank):
         # FP32 CUDA-core flops of the kernel (flop counts of the built structure, per launch)
         per_rhs = {"coupling": info["coupling_a_flops_per_rhs"], "coupling_b": info["coupling_b_flops_per_rhs"]}
         fl = per_rhs.get(dom, info["flops_per_rhs"] - 2.0 * info["near_entries"]) * m
-        alu_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) / 1e6
-        roof = {"bound": "alu", "achieved": fl / (avg_ms / 1e3) / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
-                "per_launch_flops": fl,
-                "peak_note": "FP32 FMA lanes: 152 SMs x 128 x 2 flops x max SM clock"}
+        if kernel_of(dom, info) == "coupling_a_tc_kernel":
+            tf32_peak = peaks["bf16_tflops"] * 1.1 / 2.25  # burst: the kernel runs for about a millisecond
+            roof = {"bound": "tensor", "achieved": fl / (avg_ms / 1e3) / 1e12, "peak": tf32_peak,
+                    "unit": "TFLOP/s", "per_launch_flops": fl,
+                    "peak_note": "dense TF32 = measured bf16 x nominal TF32/bf16 ratio 1.1/2.25; the 3xTF32 "
+                                 "split issues three MMAs per product, so algorithmic flops top out at peak/3"}
+        else:
+            alu_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) / 1e6
+            roof = {"bound": "alu", "achieved": fl / (avg_ms / 1e3) / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
+                    "per_launch_flops": fl,
+                    "peak_note": "FP32 FMA lanes: 152 SMs x 128 x 2 flops x max SM clock"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["kernel"] = KERNEL_OF_KIND.get(dom, dom)
+    roof["kernel"] = kernel_of(dom, info)
     roof["peak_source"] = peak_kind
-    roof["traffic"] = measured_traffic(dom)
+    roof["traffic"] = measured_traffic(dom, info)
     roof["timing"] = "CUDA events around each launch, far and near paths serialised (roofline pass)"
     gpu_launches = int(sum(v[1] for v in prof.values()))
     # whole-step bytes over the step time, for context

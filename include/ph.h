@@ -39,7 +39,8 @@ typedef enum {
     PH_ERR_OOM = 4,               /* host or device allocation failed */
     PH_ERR_CUDA = 5,              /* a CUDA, cuBLAS or cuSOLVER call failed (no device, launch error ...) */
     PH_ERR_NONFINITE = 6,         /* non-finite theta, or non-finite X when check_finite is set */
-    PH_ERR_TIMEOUT = 7,           /* a bounded device-side wait ran out */
+    PH_ERR_TIMEOUT = 7,           /* a bounded device-side wait ran out (reported by calls that
+                                     synchronise, i.e. ph_matvec with check_finite set) */
     PH_ERR_IO = 8,                /* ph_save / ph_load file error or bad file */
     PH_ERR_UNSUPPORTED = 9        /* option combination not implemented */
 } ph_status;
@@ -109,6 +110,8 @@ typedef struct {
     double offline_seconds;  /* wall time of ph_offline_build */
     double coupling_a_flops_per_rhs;  /* explicit coupling phase 1 (H_k R_k^T xhat), or the whole TT chain */
     double coupling_b_flops_per_rhs;  /* explicit coupling phase 2 (sum L_k z_b); 0 for the TT chain */
+    int tensor_core_phase1;  /* 1 when calls with m > 8 run phase 1 of the explicit coupling on the
+                                tensor cores (see ph_set_tensor_cores), else 0 */
 } ph_info;
 
 /* Build the parametric matrix (offline stage).
@@ -213,6 +216,14 @@ ph_status ph_plan(const double* points, long n, int d, int l_max, double eta,
  * stream, so that per-kernel times measured with ph_profile_read are those of each kernel on
  * its own (used for roofline reports; the result is the same). */
 ph_status ph_set_overlap(ph_handle* h, int enable);
+
+/* enable = 1: on FP32 handles, chunks of 16 right-hand sides and p_s^d a multiple of 32, phase 1
+ * of the explicit coupling runs on the tensor cores (tcgen05.mma kind::tf32 with 3xTF32 split
+ * operands, FP32 accumulation in tensor memory); enable = 0 (the default) keeps the CUDA-core
+ * kernel.  The tensor-core result differs from the CUDA-core one by FP32-level rounding (the
+ * split drops the low x low product and the tensor cores accumulate in their own order).
+ * Errors: PH_ERR_INVALID_ARG for a NULL handle.  Not in the paper: a kernel selection switch. */
+ph_status ph_set_tensor_cores(ph_handle* h, int enable);
 ph_status ph_profile_enable(ph_handle* h, int enable);
 ph_status ph_profile_read(ph_handle* h, double* ms, long* launches);
 

@@ -101,6 +101,12 @@ static void fill_view(ph_handle* h, DevView<T>& v, const std::vector<long>& io, 
     v.citem_key = I + io[27];
     v.citem_first = I + io[28];
     v.citem_count = I + io[29];
+    v.far_tc = (const float*)h->d_tc;
+    v.key_tcoff = L + lo[7];
+    v.n_tcitems = (int)h->tcitem_key.size();
+    v.tcitem_key = I + io[30];
+    v.tcitem_first = I + io[31];
+    v.tcitem_count = I + io[32];
     v.zstride = h->zstride;
     v.zbuf = (T*)h->d_zbuf;
     v.part_stride = h->max_leaf;
@@ -289,6 +295,19 @@ void refresh_views(ph_handle* h) {
     put(h->citem_key);              // 27
     put(h->citem_first);            // 28
     put(h->citem_count);            // 29
+    // tensor-core items: 8 blocks of one class (M = 128 columns at 16 right-hand sides)
+    h->tcitem_key.clear();
+    h->tcitem_first.clear();
+    h->tcitem_count.clear();
+    for (int k = 0; k < nkeys; ++k)
+        for (int i = h->kb_off[k]; i < h->kb_off[k + 1]; i += 8) {
+            h->tcitem_key.push_back(k);
+            h->tcitem_first.push_back(i);
+            h->tcitem_count.push_back(std::min(8, h->kb_off[k + 1] - i));
+        }
+    put(h->tcitem_key);             // 30
+    put(h->tcitem_first);           // 31
+    put(h->tcitem_count);           // 32
     std::vector<long long> lls;
     std::vector<long> lo;
     auto putl = [&](const std::vector<long long>& a) {
@@ -303,6 +322,7 @@ void refresh_views(ph_handle* h) {
     putl(h->fb_soff);
     putl(h->fb_toff);
     putl(h->key_lroff);
+    putl(h->key_tcoff);
     dev_free(h, h->d_int);
     dev_free(h, h->d_ll);
     dev_free(h, h->d_dbl);
@@ -531,6 +551,7 @@ ph_status ph_get_info(const ph_handle* h, ph_info* info) {
         alg += (double)h->far_elems * sc + (double)r.basis_bytes;
     if (h->opts.fmt == PH_FMT_H) alg += (double)h->st_elems * sc;
     r.alg_bytes_per_call = alg;
+    r.tensor_core_phase1 = (h->tc_elems > 0 && h->use_tc && h->rank_max_lr <= 64) ? 1 : 0;
     // flops per right-hand side
     double fl = 2.0 * (double)r.near_entries;  // D_b x
     for (size_t b = 0; b < plan.near_s.size(); ++b)
@@ -578,6 +599,12 @@ ph_status ph_get_info(const ph_handle* h, ph_info* info) {
 ph_status ph_set_overlap(ph_handle* h, int enable) {
     if (!h) return fail(nullptr, PH_ERR_INVALID_ARG, "ph_set_overlap: NULL handle");
     h->overlap = enable != 0;
+    return PH_OK;
+}
+
+ph_status ph_set_tensor_cores(ph_handle* h, int enable) {
+    if (!h) return fail(nullptr, PH_ERR_INVALID_ARG, "ph_set_tensor_cores: NULL handle");
+    h->use_tc = enable != 0;
     return PH_OK;
 }
 

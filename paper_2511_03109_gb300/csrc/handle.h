@@ -66,6 +66,12 @@ struct DevView {
     const int* citem_key;
     const int* citem_first;     // index into kb_list
     const int* citem_count;
+    const float* far_tc;        // R_k^T for tcgen05: per key, per 32-chunk of J, TF32 high then low part
+    const long long* key_tcoff;
+    int n_tcitems;              // key-grouped items of 8 blocks (tensor-core phase 1)
+    const int* tcitem_key;
+    const int* tcitem_first;
+    const int* tcitem_count;
     int zstride;                // rows per far block in zbuf (max r_d)
     T* zbuf;                    // n_far x zstride x mcap: z_b = H_k R_k^T xhat_t
     int n_far;
@@ -116,7 +122,10 @@ struct ph_handle {
     std::vector<int> key_ranks;
     std::vector<long long> key_off, key_hoff;
     std::vector<long long> fb_soff, fb_toff;
-    std::vector<long long> key_lroff;
+    std::vector<long long> key_lroff, key_tcoff;
+    long long tc_elems = 0;
+    void* d_tc = nullptr;
+    std::vector<int> tcitem_key, tcitem_first, tcitem_count;
     long long lr_elems = 0;
     void* d_lr = nullptr;
     std::vector<int> kb_off, kb_list, citem_key, citem_first, citem_count;
@@ -168,6 +177,7 @@ struct ph_handle {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool instantiated = false;
     bool overlap = true;                        // far path on the side stream (ph_set_overlap)
+    bool use_tc = false;                        // tensor-core phase 1 when available (ph_set_tensor_cores)
     // per-kernel timing (ph_profile_enable / ph_profile_read)
     bool prof = false;
     std::vector<cudaEvent_t> prof_pool;

@@ -24,6 +24,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <vector>
 
@@ -692,6 +693,44 @@ ph_status offline_build(ph_handle* h, const double* points, long n) {
     h->lr_elems = (long long)lr.size();
     if (o.prec == PH_FP32) h->d_lr = upload_as<float>(h, lr);
     else h->d_lr = upload_as<double>(h, lr);
+    // Tensor-core copy of R_k^T for phase 1 (FP32, p_s^d a multiple of 32, r' <= 64): rows s padded
+    // to r'_16 = r' rounded up to 16, TF32 high and low parts (3xTF32), each 32-wide chunk of J in
+    // the K-major core-matrix layout of tcgen05 operands (8 rows x 16 bytes per core matrix;
+    // element (s, k) of a chunk at (k/8) r'_16 32 + (s/8) 256 + ((k%8)/4) 128 + (s%8) 16 + (k%4) 4 bytes).
+    h->key_tcoff.assign(nkeys, 0);
+    std::vector<float> tc;
+    if (o.fmt == PH_FMT_H2 && h->opts.coupling == 0 && o.prec == PH_FP32 && h->PD % 32 == 0) {
+        auto tf32_rna = [](float x) {
+            // round to the nearest TF32 value (10 explicit mantissa bits), ties away from zero
+            uint32_t u;
+            std::memcpy(&u, &x, 4);
+            if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x1000u) & 0xFFFFE000u;
+            float y;
+            std::memcpy(&y, &u, 4);
+            return y;
+        };
+        for (int key = 0; key < nkeys; ++key) {
+            const int* rk = &h->key_ranks[(size_t)key * (Delta + 1)];
+            const int rpr = rk[d + dt], rp4 = (rpr + 3) & ~3, r16 = (rpr + 15) & ~15;
+            const double* R = &lr[(size_t)h->key_lroff[key] + (size_t)rk[d] * h->PD];  // [J * rp4 + s]
+            h->key_tcoff[key] = (long long)tc.size();
+            const size_t chunk = (size_t)32 * r16;  // floats per chunk and part
+            tc.resize(tc.size() + 2 * chunk * (h->PD / 32), 0.0f);
+            float* base = &tc[(size_t)h->key_tcoff[key]];
+            for (int c = 0; c < h->PD / 32; ++c)
+                for (int sidx = 0; sidx < rpr; ++sidx)
+                    for (int k = 0; k < 32; ++k) {
+                        const float x = (float)R[(size_t)(32 * c + k) * rp4 + sidx];
+                        const float hi = tf32_rna(x), lo = tf32_rna(x - hi);
+                        const size_t off = ((size_t)(k / 8) * r16 * 32 + (sidx / 8) * 256 + ((k % 8) / 4) * 128 +
+                                            (sidx % 8) * 16 + (k % 4) * 4) / 4;
+                        base[(size_t)c * 2 * chunk + off] = hi;
+                        base[(size_t)c * 2 * chunk + chunk + off] = lo;
+                    }
+        }
+    }
+    h->tc_elems = (long long)tc.size();
+    h->d_tc = upload_vec(h, tc);
     h->far_elems = (long long)far_sp.size();
     h->far_theta_elems = (long long)far_th.size();
     h->H_elems = hoff;

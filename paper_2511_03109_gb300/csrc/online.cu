@@ -14,6 +14,8 @@
 //                    combine_kernel       Y = Y_near + U_s yhat_s (Alg. FastBackward) -> original order
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
+#include <type_traits>
 
 #include "common.cuh"
 #include "handle.h"
@@ -844,6 +846,217 @@ __global__ void __launch_bounds__(kThreads, 2) coupling_a_staged_kernel(DevView<
     }
 }
 
+// ------------------------------------------------------------------ tcgen05 (5th-generation tensor cores)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor of a K-major operand without swizzle: core matrices of 8 rows x
+// 16 bytes, 128 bytes apart along K (leading byte offset) and 256 bytes apart along M / N
+// (stride byte offset); descriptor version 1.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(256 >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+
+// Byte offset of element (r, k) in a chunk of an R-row K-major operand (K = 32 per chunk).
+__device__ __forceinline__ uint32_t kmajor_off(int r, int k, int R) {
+    return (k / 8) * (R * 32) + (r / 8) * 256 + ((k % 8) / 4) * 128 + (r % 8) * 16 + (k % 4) * 4;
+}
+
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t u;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
+    return __uint_as_float(u);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for the phase `parity` of an mbarrier: gives up after about one second (global
+// timer) and returns false then.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t done = 0;
+    const uint64_t t0 = global_ns();
+    for (int it = 0; !done; ++it) {
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done)
+                     : "r"(smem_u32(bar)), "r"(parity));
+        if (!done && (it & 63) == 63 && global_ns() - t0 > 1000000000ull) break;
+    }
+    return done != 0;
+}
+
+__device__ __forceinline__ void umma_tf32(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                 "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar)));
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// Phase 1 of the explicit coupling on the tensor cores (FP32 data, 16 right-hand sides per pass,
+// p_s^d a multiple of 32, r' <= 64).  One CTA of 128 threads per item of up to 8 far blocks of
+// one class k; the item's columns (block, right-hand side) are the 128 rows of
+//     P^T = X^T R_k,   X = [xhat_t(b)]  (p_s^d x 128),  R_k (p_s^d x r'),
+// computed by tcgen05.mma kind::tf32 with split operands (3xTF32: x = x_hi + x_lo, products
+// hi*hi + hi*lo + lo*hi, FP32 accumulation in tensor memory), which keeps FP32 accuracy.
+// K = p_s^d runs in chunks of 32, double-buffered in shared memory: the CTA stages chunk c + 1
+// while the tensor cores work on chunk c.  Epilogue: each thread reads its row of P^T from
+// tensor memory and forms z_b = H_k P for its column, written to zbuf as in coupling_a_kernel.
+// Every wait is bounded; on a timeout the kernel records it in flags[1] and skips its output.
+__global__ void __launch_bounds__(128) coupling_a_tc_kernel(DevView<float> v, int S, int c0) {
+    constexpr int KCH = 32;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // per buffer: A_hi, A_lo (128 x 32 floats each), B_hi, B_lo (64 x 32 floats each)
+    constexpr int A_BYTES = 128 * KCH * 4, B_BYTES = 64 * KCH * 4;
+    constexpr int BUF_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+    unsigned char* buf0 = smem_raw;
+    float* Hs = reinterpret_cast<float*>(smem_raw + 2 * BUF_BYTES);  // r_d x r' (<= 64 x 64)
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_holder;
+    __shared__ long long colbase[8];
+    const int tid = threadIdx.x, warp = tid / 32;
+    const int item = blockIdx.x;
+    const int key = v.tcitem_key[item], first = v.tcitem_first[item], cnt = v.tcitem_count[item];
+    const int* rk = v.key_ranks + (size_t)key * (v.Delta + 1);
+    const int rd = rk[v.d], rp = rk[v.d + 1], r16 = (rp + 15) & ~15;
+    const int PD = v.PD, nchunks = PD / KCH;
+    const float* Rtc = v.far_tc + v.key_tcoff[key];
+    const size_t rchunk = (size_t)KCH * r16;  // floats per chunk and part
+    if (tid < 8) colbase[tid] = (tid < cnt) ? (long long)v.fb_t[v.kb_list[first + tid]] * PD * S + c0 : -1;
+    const float* H = v.H + v.key_hoff[key];
+    for (int e = tid; e < rd * rp; e += blockDim.x) Hs[e] = H[e];
+    if (tid == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+    }
+    __syncwarp();
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
+                     "r"(64));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_holder;
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(r16 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    // my row of X^T: column (block b, right-hand side c)
+    const int b = tid / 16, c = tid % 16;
+    const long long xb = colbase[b];
+    bool ok = true;
+    for (int ch = 0; ch < nchunks; ++ch) {
+        const int bi = ch & 1;
+        unsigned char* bufp = buf0 + bi * BUF_BYTES;
+        if (ch >= 2) ok = ok && mbar_wait(&mbar[bi], ((ch - 2) >> 1) & 1);  // MMAs of chunk ch - 2 done
+        // A (X^T chunk): thread = one row; 4 consecutive J per 16-byte store, hi and lo parts
+        const int k0 = ch * KCH;
+        for (int q = 0; q < KCH / 4; ++q) {
+            float x[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) x[j] = (xb >= 0) ? v.xhat[xb + (long long)(k0 + 4 * q + j) * S + c] : 0.0f;
+            float4 hi, lo;
+            hi.x = tf32_rna(x[0]); hi.y = tf32_rna(x[1]); hi.z = tf32_rna(x[2]); hi.w = tf32_rna(x[3]);
+            lo.x = tf32_rna(x[0] - hi.x); lo.y = tf32_rna(x[1] - hi.y); lo.z = tf32_rna(x[2] - hi.z); lo.w = tf32_rna(x[3] - hi.w);
+            const uint32_t off = kmajor_off(tid, 4 * q, 128);
+            *reinterpret_cast<float4*>(bufp + off) = hi;
+            *reinterpret_cast<float4*>(bufp + A_BYTES + off) = lo;
+        }
+        // B (R_k^T chunk, already in the operand layout): hi then lo, contiguous
+        {
+            const float4* src = reinterpret_cast<const float4*>(Rtc + (size_t)ch * 2 * rchunk);
+            float4* dhi = reinterpret_cast<float4*>(bufp + 2 * A_BYTES);
+            float4* dlo = reinterpret_cast<float4*>(bufp + 2 * A_BYTES + B_BYTES);
+            const int n4 = (int)(rchunk / 4);
+            for (int e = tid; e < n4; e += blockDim.x) {
+                dhi[e] = src[e];
+                dlo[e] = src[n4 + e];
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;");
+        ok = __syncthreads_and(ok);  // uniform across the CTA
+        if (tid == 0 && ok) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t a_hi = smem_u32(bufp), a_lo = a_hi + A_BYTES;
+            const uint32_t b_hi = a_hi + 2 * A_BYTES, b_lo = b_hi + B_BYTES;
+#pragma unroll
+            for (int s = 0; s < KCH / 8; ++s) {
+                const uint32_t ao = s * 128 * 32, bo = s * r16 * 32;
+                const uint32_t acc0 = (ch == 0 && s == 0) ? 0u : 1u;
+                umma_tf32(tmem, umma_desc(a_hi + ao), umma_desc(b_hi + bo), idesc, acc0);
+                umma_tf32(tmem, umma_desc(a_hi + ao), umma_desc(b_lo + bo), idesc, 1u);
+                umma_tf32(tmem, umma_desc(a_lo + ao), umma_desc(b_hi + bo), idesc, 1u);
+            }
+            umma_commit(&mbar[bi]);
+        }
+    }
+    // wait for the last chunk (its commit covers every earlier MMA of this thread)
+    const int last = nchunks - 1;
+    if (ok) ok = mbar_wait(&mbar[last & 1], (last >> 1) & 1);
+    ok = __syncthreads_and(ok);
+    if (!ok) {
+        // record the timeout, give the tensor cores one more bounded wait before tensor memory is freed
+        if (tid == 0) atomicAdd(v.flags + 1, 1);
+        mbar_wait(&mbar[last & 1], (last >> 1) & 1);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (ok) {
+        // epilogue: z_b[r][c] = sum_q H_k[r, q] P^T[(b, c), q].  The tensor-memory loads are
+        // warp-collective: every thread executes them, rows of missing blocks included.
+        float z[64];
+#pragma unroll
+        for (int r = 0; r < 64; ++r) z[r] = 0.0f;
+        __syncwarp();
+        for (int q0 = 0; q0 < r16; q0 += 16) {
+            float pv[16];
+            tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + q0, pv);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int q = q0 + j;
+                if (q < rp) {
+#pragma unroll
+                    for (int r = 0; r < 64; ++r)
+                        if (r < rd) z[r] += Hs[r + rd * q] * pv[j];
+                }
+            }
+        }
+        if (xb >= 0) {
+            const int fb = v.kb_list[first + b];
+            float* dst = v.zbuf + (long long)fb * v.zstride * S + c0 + c;
+#pragma unroll
+            for (int r = 0; r < 64; ++r)
+                if (r < rd) dst[(long long)r * S] = z[r];
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) {
+        __syncwarp();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64));
+    }
+}
+
 // Explicit coupling, phase 2 (grouped by target s): yhat_s += sum over far blocks b of s of
 // L_k z_b, L_k = (I (x) G_1^{2}) ... G_d^{2} formed offline (App. A.4).  Thread tile: 8
 // consecutive rows of yhat_s x CT right-hand sides; z_b staged in shared memory eight blocks at a
@@ -1143,7 +1356,20 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
                     {
                         ProfScope ps(h, 5, far);
                         const bool staged = (MC >= 4) && (PD % 32 == 0) && (h->rank_max_lr <= 64);
-                        if (staged) {
+                        const bool tc = std::is_same<T, float>::value && MC == 16 && h->tc_elems > 0 &&
+                                        (PD % 32 == 0) && (h->rank_max_lr <= 64) && h->use_tc && v.n_tcitems > 0;
+                        bool launched = false;
+                        if constexpr (std::is_same<T, float>::value && MC == 16) {
+                            if (tc) {
+                                const size_t sm_tc = (size_t)2 * (2 * 128 * 32 * 4 + 2 * 64 * 32 * 4) + 64 * 64 * 4;
+                                PH_CUDA(cudaFuncSetAttribute(coupling_a_tc_kernel,
+                                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_tc));
+                                coupling_a_tc_kernel<<<std::max(1, v.n_tcitems), 128, sm_tc, far>>>(v, S, c0);
+                                launched = true;
+                            }
+                        }
+                        if (launched) {
+                        } else if (staged) {
                             size_t sm_a = ((size_t)2 * 32 * 64 + 2 * 32 * 260) * sizeof(T);
                             set_smem<T, MC>((const void*)coupling_a_staged_kernel<T, MC>, sm_a);
                             coupling_a_staged_kernel<T, MC><<<std::max(1, v.n_citems), kThreads, sm_a, far>>>(
@@ -1249,7 +1475,7 @@ ph_status matvec_typed(ph_handle* h, DevView<T>& v, const T* X, long long ldx, i
     const int S = (int)ceil_div(m, MC) * MC;
     const bool h2 = (h->opts.fmt == PH_FMT_H2);
     const int check = h->opts.check_finite ? 1 : 0;
-    if (check) PH_CUDA(cudaMemsetAsync(v.flags, 0, sizeof(int), stream));
+    if (check) PH_CUDA(cudaMemsetAsync(v.flags, 0, 2 * sizeof(int), stream));
     const long long total = (long long)v.n * S;
     int grid = (int)std::min<long long>(ceil_div(total, kThreads), 152 * 16);
     {
@@ -1269,10 +1495,11 @@ ph_status matvec_typed(ph_handle* h, DevView<T>& v, const T* X, long long ldx, i
         default: run_matvec<T, 16>(h, v, X, ldx, m, Y, ldy, stream, S); break;
     }
     if (check) {
-        int bad = 0;
-        PH_CUDA(cudaMemcpyAsync(&bad, v.flags, sizeof(int), cudaMemcpyDeviceToHost, stream));
+        int bad[2] = {0, 0};
+        PH_CUDA(cudaMemcpyAsync(bad, v.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, stream));
         PH_CUDA(cudaStreamSynchronize(stream));
-        if (bad) throw Error(PH_ERR_NONFINITE, "X has non-finite entries");
+        if (bad[0]) throw Error(PH_ERR_NONFINITE, "X has non-finite entries");
+        if (bad[1]) throw Error(PH_ERR_TIMEOUT, "a bounded tensor-core wait ran out");
     }
     return PH_OK;
 }

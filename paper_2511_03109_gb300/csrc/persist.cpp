@@ -94,6 +94,8 @@ void scalars_io(IO& io, H& h) {
     io.vec(h.fb_toff);
     io.vec(h.key_lroff);
     io.val(h.lr_elems);
+    io.vec(h.key_tcoff);
+    io.val(h.tc_elems);
     io.val(h.near_elems);
     io.val(h.near_theta_elems);
     io.val(h.far_elems);
@@ -139,6 +141,7 @@ extern "C" ph_status ph_save(const ph_handle* hc, const char* path) {
         w.dev(h->d_U, (size_t)h->plan.n * h->plan.d * h->opts.p_s * sc);
         w.dev(h->d_E, (size_t)2 * h->opts.p_s * h->opts.p_s * sc);
         w.dev(h->d_lr, h->lr_elems * sc);
+        w.dev(h->d_tc, h->tc_elems * 4);
     } catch (const ph::Error& e) {
         fclose(f);
         h->last_error = e.what();
@@ -190,6 +193,7 @@ extern "C" ph_status ph_load(const char* path, int device, ph_handle** out) {
         h->d_U = r.dev(h);
         h->d_E = r.dev(h);
         h->d_lr = r.dev(h);
+        h->d_tc = r.dev(h);
         h->d_H = ph::dev_alloc(h, (h->H_elems > 0 ? h->H_elems : 1) * h->scalar);
         h->d_w = ph::dev_alloc(h, (h->w_elems > 0 ? h->w_elems : 1) * h->scalar);
         ph::refresh_views(h);

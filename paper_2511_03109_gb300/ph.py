@@ -54,7 +54,8 @@ class Info(C.Structure):
                 ("near_theta_bytes", C.c_long), ("far_bytes", C.c_long),
                 ("basis_bytes", C.c_long), ("alg_bytes_per_call", C.c_double),
                 ("flops_per_rhs", C.c_double), ("offline_seconds", C.c_double),
-                ("coupling_a_flops_per_rhs", C.c_double), ("coupling_b_flops_per_rhs", C.c_double)]
+                ("coupling_a_flops_per_rhs", C.c_double), ("coupling_b_flops_per_rhs", C.c_double),
+                ("tensor_core_phase1", C.c_int)]
 
     def as_dict(self):
         out = {}
@@ -84,6 +85,7 @@ _SIGS = {
     "ph_version": (C.c_char_p, []),
     "ph_profile_enable": (C.c_int, [_H, C.c_int]),
     "ph_set_overlap": (C.c_int, [_H, C.c_int]),
+    "ph_set_tensor_cores": (C.c_int, [_H, C.c_int]),
     "ph_profile_read": (C.c_int, [_H, C.POINTER(C.c_double), C.POINTER(C.c_long)]),
 }
 
@@ -208,6 +210,9 @@ class ParametricMatrix:
 
     def set_overlap(self, enable=True):
         return check(ph_set_overlap(self.h, 1 if enable else 0), self.h)
+
+    def set_tensor_cores(self, enable=True):
+        return check(ph_set_tensor_cores(self.h, 1 if enable else 0), self.h)
 
     def profile(self, enable=True):
         return check(ph_profile_enable(self.h, 1 if enable else 0), self.h)

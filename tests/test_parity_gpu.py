@@ -63,6 +63,29 @@ def test_coupling_modes(coupling, d, prec, m):
     A.close()
 
 
+@pytest.mark.parametrize("ps,theta", [(4, 0.13), (8, 0.47)])
+def test_tensor_core_phase1_against_cuda_core_and_oracle(ps, theta):
+    """FP32, 16 right-hand sides, p_s^d a multiple of 32: phase 1 of the explicit coupling runs on
+    the tensor cores (3xTF32); the CUDA-core kernel and the oracle must agree with it."""
+    n = 2500 if ps == 4 else 6000
+    P = inputs.uniform_points(n, 3, 90 + ps)
+    X = inputs.gaussian_rhs(n, 16, 91 + ps)
+    A, M, targets = build_pair(P, "matern32", [0.05], [0.5], [16], ps, 2, np.sqrt(3.0), 1e-5, 64, "h2", "fp32",
+                               targets_every=11 if ps == 4 else 23)
+    rows = target_rows(targets)
+    ref = M.matvec(M.instantiate([theta], targets), X, targets)
+    assert A.info()["tensor_core_phase1"] == 0  # off by default
+    y_cc = device_apply(A, [theta], X, "fp32")
+    A.set_tensor_cores(True)
+    assert A.info()["tensor_core_phase1"] == 1
+    y_tc = device_apply(A, [theta], X, "fp32")
+    assert np.all(rel_err_rows(ref, y_tc, rows) <= TOL["fp32"])
+    assert np.all(rel_err_rows(ref, y_cc, rows) <= TOL["fp32"])
+    # two FP32 evaluations in different summation orders, each within the FP32 bar of the oracle
+    assert np.all(rel_err_rows(y_cc, y_tc) <= TOL["fp32"])
+    A.close()
+
+
 def test_parity_3d_h2_fp32_sampled_rows():
     """3-D Matern 3/2, eta = sqrt(3), 16 right-hand sides; oracle on a sample of target leaves."""
     n = 3000
