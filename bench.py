@@ -220,6 +220,8 @@ def run_gpu(args, rank, world, local_rank):
         A = ph.ParametricMatrix(P, WL.kernel, opts)
         if args.save:
             A.save(args.save)
+    if args.tensor_cores is not None:
+        A.set_tensor_cores(args.tensor_cores == 1)
     info = A.info()
     log(f"offline done in {info['offline_seconds']:.1f} s")
     total_steps = args.warmup + args.steps
@@ -425,6 +427,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--save", default="", help="profiling only: write the built handle to this file")
     ap.add_argument("--load", default="", help="profiling only: load a handle written by --save")
+    ap.add_argument("--tensor-cores", type=int, default=None, choices=[0, 1],
+                    help="phase 1 of the coupling on the tensor cores (1) or CUDA cores (0); default: the library's")
     ap.add_argument("--n", type=int, default=0,
                     help="profiling only: a smaller point count of the same workload (not a bench line)")
     args = ap.parse_args()

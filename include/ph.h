@@ -110,8 +110,8 @@ typedef struct {
     double offline_seconds;  /* wall time of ph_offline_build */
     double coupling_a_flops_per_rhs;  /* explicit coupling phase 1 (H_k R_k^T xhat), or the whole TT chain */
     double coupling_b_flops_per_rhs;  /* explicit coupling phase 2 (sum L_k z_b); 0 for the TT chain */
-    int tensor_core_phase1;  /* 1 when calls with m > 8 run phase 1 of the explicit coupling on the
-                                tensor cores (see ph_set_tensor_cores), else 0 */
+    int tensor_core_phase1;  /* 1 when calls with 8 < m <= 16 run phase 1 of the explicit coupling
+                                on the tensor cores (see ph_set_tensor_cores), else 0 */
 } ph_info;
 
 /* Build the parametric matrix (offline stage).
@@ -217,7 +217,7 @@ ph_status ph_plan(const double* points, long n, int d, int l_max, double eta,
  * its own (used for roofline reports; the result is the same). */
 ph_status ph_set_overlap(ph_handle* h, int enable);
 
-/* enable = 1: on FP32 handles, chunks of 16 right-hand sides and p_s^d a multiple of 32, phase 1
+/* enable = 1: on FP32 handles, 8 < m <= 16 right-hand sides and p_s^d a multiple of 32, phase 1
  * of the explicit coupling runs on the tensor cores (tcgen05.mma kind::tf32 with 3xTF32 split
  * operands, FP32 accumulation in tensor memory); enable = 0 (the default) keeps the CUDA-core
  * kernel.  The tensor-core result differs from the CUDA-core one by FP32-level rounding (the

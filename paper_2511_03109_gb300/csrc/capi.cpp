@@ -149,6 +149,11 @@ static void fill_view(ph_handle* h, DevView<T>& v, const std::vector<long>& io, 
 // Packs the plan's index arrays into two device allocations and fills the views.
 void refresh_views(ph_handle* h) {
     const Plan& plan = h->plan;
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device) == cudaSuccess && nsm > 0)
+        h->num_sms = nsm;
+    else
+        cudaGetLastError();
     std::vector<int> ints;
     std::vector<long> io;
     auto put = [&](const std::vector<int>& a) {
@@ -551,7 +556,7 @@ ph_status ph_get_info(const ph_handle* h, ph_info* info) {
         alg += (double)h->far_elems * sc + (double)r.basis_bytes;
     if (h->opts.fmt == PH_FMT_H) alg += (double)h->st_elems * sc;
     r.alg_bytes_per_call = alg;
-    r.tensor_core_phase1 = (h->tc_elems > 0 && h->use_tc && h->rank_max_lr <= 64) ? 1 : 0;
+    r.tensor_core_phase1 = (h->tc_elems > 0 && h->use_tc && h->rank_max_lr <= 64) ? 1 : 0;  // for 8 < m <= 16
     // flops per right-hand side
     double fl = 2.0 * (double)r.near_entries;  // D_b x
     for (size_t b = 0; b < plan.near_s.size(); ++b)

@@ -110,6 +110,7 @@ struct ph_handle {
     ph_kernel kernel = PH_KERNEL_GAUSS;
     ph_build_opts opts{};
     int device = 0;
+    int num_sms = 1;  // streaming multiprocessors of the device (persistent grids)
     int PD = 0, Delta = 0, p_theta_total = 1;
     size_t scalar = 8;  // sizeof compute type
     ph::Plan plan;

@@ -915,145 +915,238 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-// Phase 1 of the explicit coupling on the tensor cores (FP32 data, 16 right-hand sides per pass,
-// p_s^d a multiple of 32, r' <= 64).  One CTA of 128 threads per item of up to 8 far blocks of
-// one class k; the item's columns (block, right-hand side) are the 128 rows of
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// 1-D bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16), completing
+// on an mbarrier's transaction count.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Phase 1 of the explicit coupling on the tensor cores (FP32 data, one chunk of 16 right-hand
+// sides, p_s^d a multiple of 32, r', r_d <= 64).  Persistent: CTA i takes items i, i + G, ...
+// (G = grid size) of up to 8 far blocks of one class k.  An item's columns (block, right-hand
+// side) are the 128 rows of
 //     P^T = X^T R_k,   X = [xhat_t(b)]  (p_s^d x 128),  R_k (p_s^d x r'),
 // computed by tcgen05.mma kind::tf32 with split operands (3xTF32: x = x_hi + x_lo, products
-// hi*hi + hi*lo + lo*hi, FP32 accumulation in tensor memory), which keeps FP32 accuracy.
-// K = p_s^d runs in chunks of 32, double-buffered in shared memory: the CTA stages chunk c + 1
-// while the tensor cores work on chunk c.  Epilogue: each thread reads its row of P^T from
-// tensor memory and forms z_b = H_k P for its column, written to zbuf as in coupling_a_kernel.
-// Every wait is bounded; on a timeout the kernel records it in flags[1] and skips its output.
-__global__ void __launch_bounds__(128) coupling_a_tc_kernel(DevView<float> v, int S, int c0) {
-    constexpr int KCH = 32;
+// hi*hi + hi*lo + lo*hi).  K = p_s^d runs in chunks of 32 (a "task" is one chunk of one item):
+//   * thread 0 streams each task's inputs with bulk copies into a ring of NS stages: the eight
+//     2 KB slices of xhat (raw FP32) and the chunk of R_k already split and in operand layout;
+//   * all threads split the raw slices into the hi / lo A operands (double-buffered), then
+//     thread 0 issues the 12 MMAs of the chunk into its own tensor-memory region (two regions);
+//   * while the tensor cores run chunk c, the threads read chunk c - 1's partial product from
+//     tensor memory and add it to P in registers (FP32, round to nearest), so the tensor cores
+//     never accumulate more than one chunk; after an item's last chunk they form
+//     z_b = H_k P for their column, overlapped with the next item's MMAs.
+// Every wait is bounded: on a timeout the kernel counts it in flags[1], stops issuing work,
+// waits (bounded) for the copies and MMAs it started and frees its tensor memory.
+namespace tc1 {
+constexpr int NS = 3;                        // stages of the bulk-copy ring
+constexpr int XSTRIDE = 512 + 16;            // floats per block slice in a stage (bank padding)
+constexpr int XST_BYTES = 8 * XSTRIDE * 4;   // raw xhat slices of one stage
+constexpr int BST_BYTES = 2 * 32 * 64 * 4;   // R_k chunk, hi + lo, r'_16 <= 64
+constexpr int A_BYTES = 128 * 32 * 4;        // one part of the A operand
+constexpr int SMEM = NS * XST_BYTES + NS * BST_BYTES + 2 * 2 * A_BYTES + 64 * 64 * 4;
+}  // namespace tc1
+
+__global__ void __launch_bounds__(128, 1) coupling_a_tc_kernel(DevView<float> v) {
+    using namespace tc1;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    // per buffer: A_hi, A_lo (128 x 32 floats each), B_hi, B_lo (64 x 32 floats each)
-    constexpr int A_BYTES = 128 * KCH * 4, B_BYTES = 64 * KCH * 4;
-    constexpr int BUF_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-    unsigned char* buf0 = smem_raw;
-    float* Hs = reinterpret_cast<float*>(smem_raw + 2 * BUF_BYTES);  // r_d x r' (<= 64 x 64)
-    __shared__ __align__(8) uint64_t mbar[2];
+    unsigned char* xst = smem_raw;                             // NS x XST_BYTES
+    unsigned char* bst = xst + NS * XST_BYTES;                 // NS x BST_BYTES
+    unsigned char* abuf = bst + NS * BST_BYTES;                // 2 x (hi, lo)
+    float* Hs = reinterpret_cast<float*>(abuf + 4 * A_BYTES);  // r_d x r' (<= 64 x 64)
+    __shared__ __align__(8) uint64_t fullbar[NS];
+    __shared__ __align__(8) uint64_t mmabar[2];
     __shared__ uint32_t tmem_holder;
-    __shared__ long long colbase[8];
     const int tid = threadIdx.x, warp = tid / 32;
-    const int item = blockIdx.x;
-    const int key = v.tcitem_key[item], first = v.tcitem_first[item], cnt = v.tcitem_count[item];
-    const int* rk = v.key_ranks + (size_t)key * (v.Delta + 1);
-    const int rd = rk[v.d], rp = rk[v.d + 1], r16 = (rp + 15) & ~15;
-    const int PD = v.PD, nchunks = PD / KCH;
-    const float* Rtc = v.far_tc + v.key_tcoff[key];
-    const size_t rchunk = (size_t)KCH * r16;  // floats per chunk and part
-    if (tid < 8) colbase[tid] = (tid < cnt) ? (long long)v.fb_t[v.kb_list[first + tid]] * PD * S + c0 : -1;
-    const float* H = v.H + v.key_hoff[key];
-    for (int e = tid; e < rd * rp; e += blockDim.x) Hs[e] = H[e];
+    const int PD = v.PD, nchunks = PD / 32;
+    const int G = gridDim.x;
+    const int my_items = (v.n_tcitems - (int)blockIdx.x + G - 1) / G;
+    const int T = my_items * nchunks;
+    const int b = tid / 16, c = tid % 16;  // my row of X^T: column (block b, right-hand side c)
+
     if (tid == 0) {
-        mbar_init(&mbar[0], 1);
-        mbar_init(&mbar[1], 1);
+        for (int i = 0; i < NS; ++i) mbar_init(&fullbar[i], 1);
+        mbar_init(&mmabar[0], 1);
+        mbar_init(&mmabar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncwarp();
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
-                     "r"(64));
+                     "r"(128));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_holder;
-    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(r16 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-    // my row of X^T: column (block b, right-hand side c)
-    const int b = tid / 16, c = tid % 16;
-    const long long xb = colbase[b];
+
+    // thread 0: bulk copies of task t into stage t % NS
+    int issued = 0;  // tasks whose copies were issued (thread 0 only)
+    auto issue = [&](int t) {
+        if (t >= T) return;
+        const int item = (int)blockIdx.x + (t / nchunks) * G, ch = t % nchunks;
+        const int key = v.tcitem_key[item], first = v.tcitem_first[item], cnt = v.tcitem_count[item];
+        const int rp = v.key_ranks[(size_t)key * (v.Delta + 1) + v.d + 1], r16 = (rp + 15) & ~15;
+        const int st = t % NS;
+        const uint32_t bbytes = 2u * 32u * (uint32_t)r16 * 4u;
+        mbar_expect_tx(&fullbar[st], (uint32_t)cnt * 2048u + bbytes);
+        for (int i = 0; i < cnt; ++i) {
+            const float* src = v.xhat + (long long)v.fb_t[v.kb_list[first + i]] * PD * 16 + (long long)ch * 512;
+            bulk_g2s(xst + st * XST_BYTES + i * XSTRIDE * 4, src, 2048u, &fullbar[st]);
+        }
+        bulk_g2s(bst + st * BST_BYTES, v.far_tc + v.key_tcoff[key] + (size_t)ch * 2 * 32 * r16, bbytes, &fullbar[st]);
+        issued = t + 1;
+    };
+    if (tid == 0)
+        for (int t = 0; t < NS - 1; ++t) issue(t);
+
+    float P[64];
+#pragma unroll
+    for (int q = 0; q < 64; ++q) P[q] = 0.0f;
     bool ok = true;
-    for (int ch = 0; ch < nchunks; ++ch) {
-        const int bi = ch & 1;
-        unsigned char* bufp = buf0 + bi * BUF_BYTES;
-        if (ch >= 2) ok = ok && mbar_wait(&mbar[bi], ((ch - 2) >> 1) & 1);  // MMAs of chunk ch - 2 done
-        // A (X^T chunk): thread = one row; 4 consecutive J per 16-byte store, hi and lo parts
-        const int k0 = ch * KCH;
-        for (int q = 0; q < KCH / 4; ++q) {
-            float x[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) x[j] = (xb >= 0) ? v.xhat[xb + (long long)(k0 + 4 * q + j) * S + c] : 0.0f;
-            float4 hi, lo;
-            hi.x = tf32_rna(x[0]); hi.y = tf32_rna(x[1]); hi.z = tf32_rna(x[2]); hi.w = tf32_rna(x[3]);
-            lo.x = tf32_rna(x[0] - hi.x); lo.y = tf32_rna(x[1] - hi.y); lo.z = tf32_rna(x[2] - hi.z); lo.w = tf32_rna(x[3] - hi.w);
-            const uint32_t off = kmajor_off(tid, 4 * q, 128);
-            *reinterpret_cast<float4*>(bufp + off) = hi;
-            *reinterpret_cast<float4*>(bufp + A_BYTES + off) = lo;
-        }
-        // B (R_k^T chunk, already in the operand layout): hi then lo, contiguous
-        {
-            const float4* src = reinterpret_cast<const float4*>(Rtc + (size_t)ch * 2 * rchunk);
-            float4* dhi = reinterpret_cast<float4*>(bufp + 2 * A_BYTES);
-            float4* dlo = reinterpret_cast<float4*>(bufp + 2 * A_BYTES + B_BYTES);
-            const int n4 = (int)(rchunk / 4);
-            for (int e = tid; e < n4; e += blockDim.x) {
-                dhi[e] = src[e];
-                dlo[e] = src[n4 + e];
-            }
-        }
-        asm volatile("fence.proxy.async.shared::cta;");
-        ok = __syncthreads_and(ok);  // uniform across the CTA
-        if (tid == 0 && ok) {
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t a_hi = smem_u32(bufp), a_lo = a_hi + A_BYTES;
-            const uint32_t b_hi = a_hi + 2 * A_BYTES, b_lo = b_hi + B_BYTES;
-#pragma unroll
-            for (int s = 0; s < KCH / 8; ++s) {
-                const uint32_t ao = s * 128 * 32, bo = s * r16 * 32;
-                const uint32_t acc0 = (ch == 0 && s == 0) ? 0u : 1u;
-                umma_tf32(tmem, umma_desc(a_hi + ao), umma_desc(b_hi + bo), idesc, acc0);
-                umma_tf32(tmem, umma_desc(a_hi + ao), umma_desc(b_lo + bo), idesc, 1u);
-                umma_tf32(tmem, umma_desc(a_lo + ao), umma_desc(b_hi + bo), idesc, 1u);
-            }
-            umma_commit(&mbar[bi]);
-        }
-    }
-    // wait for the last chunk (its commit covers every earlier MMA of this thread)
-    const int last = nchunks - 1;
-    if (ok) ok = mbar_wait(&mbar[last & 1], (last >> 1) & 1);
-    ok = __syncthreads_and(ok);
-    if (!ok) {
-        // record the timeout, give the tensor cores one more bounded wait before tensor memory is freed
-        if (tid == 0) atomicAdd(v.flags + 1, 1);
-        mbar_wait(&mbar[last & 1], (last >> 1) & 1);
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (ok) {
-        // epilogue: z_b[r][c] = sum_q H_k[r, q] P^T[(b, c), q].  The tensor-memory loads are
-        // warp-collective: every thread executes them, rows of missing blocks included.
-        float z[64];
-#pragma unroll
-        for (int r = 0; r < 64; ++r) z[r] = 0.0f;
+    int mma_issued = 0;  // tasks whose MMAs were issued (uniform)
+    int landed = 0;      // tasks whose copies this thread saw complete
+
+    // add the partial product of task t (its chunk) to P; after the item's last chunk form z_b
+    auto drain = [&](int t) {
+        const int item = (int)blockIdx.x + (t / nchunks) * G, ch = t % nchunks;
+        const int key = v.tcitem_key[item], first = v.tcitem_first[item], cnt = v.tcitem_count[item];
+        const int* rk = v.key_ranks + (size_t)key * (v.Delta + 1);
+        const int rd = rk[v.d], rp = rk[v.d + 1], r16 = (rp + 15) & ~15;
+        const uint32_t region = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)((t & 1) * 64);
         __syncwarp();
-        for (int q0 = 0; q0 < r16; q0 += 16) {
-            float pv[16];
-            tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + q0, pv);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int q = q0 + j;
+        for (int q0 = 0; q0 < 64; q0 += 16) {
+            if (q0 < r16) {
+                float pv[16];
+                tmem_ld16(region + q0, pv);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) P[q0 + j] += pv[j];
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");  // the region is rewritten after the next barrier
+        if (ch != nchunks - 1) return;
+        // epilogue of the item: z_b[r][c] = sum_q H_k[r, q] P^T[(b, c), q]
+        __syncthreads();  // Hs of the previous item is no longer read
+        const float* H = v.H + v.key_hoff[key];
+        // column q of H_k in row q of Hs, padded to 64 with zeros (16-byte reads below)
+        for (int e = tid; e < rp * 64; e += blockDim.x) {
+            const int q = e / 64, r = e % 64;
+            Hs[e] = (r < rd) ? H[r + rd * q] : 0.0f;
+        }
+        __syncthreads();
+        if (b < cnt) {
+            float z[64];
+#pragma unroll
+            for (int r = 0; r < 64; ++r) z[r] = 0.0f;
+            const float4* H4 = reinterpret_cast<const float4*>(Hs);
+#pragma unroll
+            for (int q = 0; q < 64; ++q) {
                 if (q < rp) {
 #pragma unroll
-                    for (int r = 0; r < 64; ++r)
-                        if (r < rd) z[r] += Hs[r + rd * q] * pv[j];
+                    for (int i = 0; i < 16; ++i)
+                        if (4 * i < rd) {
+                            const float4 hv = H4[q * 16 + i];
+                            z[4 * i] += hv.x * P[q];
+                            z[4 * i + 1] += hv.y * P[q];
+                            z[4 * i + 2] += hv.z * P[q];
+                            z[4 * i + 3] += hv.w * P[q];
+                        }
                 }
             }
-        }
-        if (xb >= 0) {
             const int fb = v.kb_list[first + b];
-            float* dst = v.zbuf + (long long)fb * v.zstride * S + c0 + c;
+            float* dst = v.zbuf + (long long)fb * v.zstride * 16 + c;
 #pragma unroll
             for (int r = 0; r < 64; ++r)
-                if (r < rd) dst[(long long)r * S] = z[r];
+                if (r < rd) dst[(long long)r * 16] = z[r];
         }
+#pragma unroll
+        for (int q = 0; q < 64; ++q) P[q] = 0.0f;
+    };
+
+    for (int t = 0; t < T && ok; ++t) {
+        const int item = (int)blockIdx.x + (t / nchunks) * G;
+        const int key = v.tcitem_key[item], cnt = v.tcitem_count[item];
+        const int rp = v.key_ranks[(size_t)key * (v.Delta + 1) + v.d + 1], r16 = (rp + 15) & ~15;
+        const int st = t % NS;
+        ok = mbar_wait(&fullbar[st], (uint32_t)((t / NS) & 1));
+        if (ok) landed = t + 1;
+        // split the raw slice of my row into the hi / lo A operands of buffer t & 1 (its MMAs of
+        // task t - 2 finished: waited for in the previous iteration)
+        unsigned char* ahi = abuf + (t & 1) * 2 * A_BYTES;
+        const float* raw = reinterpret_cast<const float*>(xst + st * XST_BYTES) + b * XSTRIDE + c;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            float x[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) x[j] = (b < cnt) ? raw[(4 * q + j) * 16] : 0.0f;
+            float4 hi, lo;
+            hi.x = tf32_rna(x[0]); hi.y = tf32_rna(x[1]); hi.z = tf32_rna(x[2]); hi.w = tf32_rna(x[3]);
+            lo.x = tf32_rna(x[0] - hi.x); lo.y = tf32_rna(x[1] - hi.y);
+            lo.z = tf32_rna(x[2] - hi.z); lo.w = tf32_rna(x[3] - hi.w);
+            const uint32_t off = kmajor_off(tid, 4 * q, 128);
+            *reinterpret_cast<float4*>(ahi + off) = hi;
+            *reinterpret_cast<float4*>(ahi + A_BYTES + off) = lo;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        ok = __syncthreads_and(ok);
+        if (!ok) break;
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t a_hi = smem_u32(ahi), a_lo = a_hi + A_BYTES;
+            const uint32_t b_hi = smem_u32(bst + st * BST_BYTES), b_lo = b_hi + 32u * (uint32_t)r16 * 4u;
+            const uint32_t idesc =
+                (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(r16 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+            const uint32_t dt = tmem + (uint32_t)((t & 1) * 64);
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                const uint32_t ao = s * 128 * 32, bo = s * r16 * 32;
+                umma_tf32(dt, umma_desc(a_hi + ao), umma_desc(b_hi + bo), idesc, s == 0 ? 0u : 1u);
+                umma_tf32(dt, umma_desc(a_hi + ao), umma_desc(b_lo + bo), idesc, 1u);
+                umma_tf32(dt, umma_desc(a_lo + ao), umma_desc(b_hi + bo), idesc, 1u);
+            }
+            umma_commit(&mmabar[t & 1]);
+        }
+        mma_issued = t + 1;
+        if (t >= 1) {
+            ok = mbar_wait(&mmabar[(t - 1) & 1], (uint32_t)(((t - 1) >> 1) & 1));
+            ok = __syncthreads_and(ok);
+            if (!ok) break;
+        }
+        // the stage of task t - 1 is free: its slices were split and its MMAs are done
+        if (tid == 0) issue(t + NS - 1);
+        if (t >= 1) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            drain(t - 1);
+        }
+    }
+    if (ok && T > 0) {
+        ok = mbar_wait(&mmabar[(T - 1) & 1], (uint32_t)(((T - 1) >> 1) & 1));
+        ok = __syncthreads_and(ok);
+        if (ok) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            drain(T - 1);
+        }
+    }
+    if (!ok && tid == 0) {
+        atomicAdd(v.flags + 1, 1);
+        // bounded waits for everything this CTA started before its shared and tensor memory go
+        for (int t = landed; t < issued; ++t) mbar_wait(&fullbar[t % NS], (uint32_t)((t / NS) & 1));
+        if (mma_issued > 0) mbar_wait(&mmabar[(mma_issued - 1) & 1], (uint32_t)(((mma_issued - 1) >> 1) & 1));
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 0) {
         __syncwarp();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
     }
 }
 
@@ -1103,7 +1196,29 @@ __global__ void __launch_bounds__(kThreads, 2) coupling_b_kernel(DevView<T> v, i
                 const int cq = it % CQ, rg = it / CQ;
                 const int I0 = rg * RPT;
                 const bool full = vec && (I0 + RPT <= PD);
-                for (int q = 0; q < rd; ++q) {
+                int q = 0;
+                if (NIB == 1 && full) {
+                    // four columns of L_k per step, all loads issued before the products
+                    for (; q + 4 <= rd; q += 4) {
+                        T l[4][RPT];
+#pragma unroll
+                        for (int w = 0; w < 4; ++w) {
+                            const T* lp = Lt + (long long)(q + w) * PD + I0;
+                            load_ct<T, 4>(lp, *reinterpret_cast<T(*)[4]>(&l[w][0]));
+                            load_ct<T, 4>(lp + 4, *reinterpret_cast<T(*)[4]>(&l[w][4]));
+                        }
+#pragma unroll
+                        for (int w = 0; w < 4; ++w) {
+                            T x[CT];
+                            load_ct<T, CT>(zb + (q + w) * MC + cq * CT, x);
+#pragma unroll
+                            for (int i = 0; i < RPT; ++i)
+#pragma unroll
+                                for (int c = 0; c < CT; ++c) acc[u][i][c] += l[w][i] * x[c];
+                        }
+                    }
+                }
+                for (; q < rd; ++q) {
                     T l[RPT];
                     const T* lp = Lt + (long long)q * PD + I0;
                     if (full) {
@@ -1360,11 +1475,11 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
                                         (PD % 32 == 0) && (h->rank_max_lr <= 64) && h->use_tc && v.n_tcitems > 0;
                         bool launched = false;
                         if constexpr (std::is_same<T, float>::value && MC == 16) {
-                            if (tc) {
-                                const size_t sm_tc = (size_t)2 * (2 * 128 * 32 * 4 + 2 * 64 * 32 * 4) + 64 * 64 * 4;
+                            if (tc && S == 16) {
                                 PH_CUDA(cudaFuncSetAttribute(coupling_a_tc_kernel,
-                                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_tc));
-                                coupling_a_tc_kernel<<<std::max(1, v.n_tcitems), 128, sm_tc, far>>>(v, S, c0);
+                                                             cudaFuncAttributeMaxDynamicSharedMemorySize, tc1::SMEM));
+                                const int grid = std::min(v.n_tcitems, h->num_sms);
+                                coupling_a_tc_kernel<<<grid, 128, tc1::SMEM, far>>>(v);
                                 launched = true;
                             }
                         }
