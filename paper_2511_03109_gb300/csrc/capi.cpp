@@ -149,6 +149,8 @@ static void fill_view(ph_handle* h, DevView<T>& v, const std::vector<long>& io, 
 // Packs the plan's index arrays into two device allocations and fills the views.
 void refresh_views(ph_handle* h) {
     const Plan& plan = h->plan;
+    h->near_rank_max = 0;
+    for (int r : h->nb_rank) h->near_rank_max = std::max(h->near_rank_max, r);
     int nsm = 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device) == cudaSuccess && nsm > 0)
         h->num_sms = nsm;

@@ -405,7 +405,8 @@ V* upload_vec(ph_handle* h, const std::vector<V>& v) {
 
 void* dev_alloc(ph_handle* h, size_t bytes) {
     void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, std::max<size_t>(bytes, 16));
+    // 64 bytes of slack: bulk copies round the end of a range up to 16 bytes
+    cudaError_t e = cudaMalloc(&p, bytes + 64);
     if (e != cudaSuccess) {
         cudaGetLastError();
         throw Error(PH_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " +

@@ -1150,6 +1150,163 @@ __global__ void __launch_bounds__(128, 1) coupling_a_tc_kernel(DevView<float> v)
     }
 }
 
+// Near field, bulk-copy pipelined (FP32 / FP64, chunks of MC right-hand sides with S == MC, leaves
+// of at most kThreads points, r ns <= the stage size).  One CTA per near work item, as
+// near_kernel, with a producer warp: the cores G_{b,1} of the item's blocks are streamed in
+// chunks of whole columns j (each chunk contiguous in memory: [(j r + k) ns + i]) by 1-D bulk
+// copies into a ring of NS stages, together with the rows x_t of each block (into one buffer per
+// block).  The eight consumer warps form d_ij = sum_k w_k G[(j r + k) ns + i] from shared memory
+// and accumulate d_ij x_t[j][c] as near_kernel does; a stage is handed back through an mbarrier
+// arrival per consumer warp, so the CTA never stops at a full barrier while the cores stream.
+// Every wait is bounded: after a timeout the CTA counts it in flags[1], stops issuing copies and
+// waits (bounded) for those in flight before it exits.
+namespace nt1 {
+constexpr int NS = 4;                    // stages
+constexpr int STAGE = 16384;             // bytes of cores per stage
+constexpr int STB = STAGE + 16;          // plus the 16-byte rounding of a chunk's start
+constexpr int kConsumers = kThreads / 32;
+}  // namespace nt1
+
+template <typename T>
+__device__ __forceinline__ int near_chunk_cols(int r, int ns) {
+    const long long colf = (long long)r * ns;
+    const int J = (int)((nt1::STAGE - 16) / (colf * (long long)sizeof(T)));
+    return J < 1 ? 1 : J;
+}
+
+template <typename T, int MC>
+__global__ void __launch_bounds__(kThreads + 32, 2) near_tma_kernel(DevView<T> v, int maxleaf) {
+    using namespace nt1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char* stg = smem_raw;                              // NS x STB
+    T* xs = reinterpret_cast<T*>(smem_raw + NS * STB);          // 4 x maxleaf x MC (one per block)
+    T* red = reinterpret_cast<T*>(smem_raw);                    // kThreads x MC, after the stream
+    __shared__ __align__(8) uint64_t full[NS], empty[NS];
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    const int item = blockIdx.x;
+    const int leaf = v.item_leaf[item];
+    const int snode = v.leaf_node[leaf];
+    const int ns = v.node_end[snode] - v.node_begin[snode];
+    const int b0 = v.item_first[item], b1 = b0 + v.item_count[item];
+    if (tid == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kConsumers);
+        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp == kConsumers) {
+        // ---------------- producer warp: lane 0 issues the copies of every chunk of the item
+        if (lane == 0) {
+            int t = 0;
+            bool ok = true;
+            for (int b = b0; b < b1 && ok; ++b) {
+                const int r = v.nb_rank[b];
+                const int tnode = v.nb_t[b];
+                const int tb = v.node_begin[tnode], nt = v.node_end[tnode] - tb;
+                const long long colf = (long long)r * ns;
+                const int J = near_chunk_cols<T>(r, ns);
+                for (int j0 = 0; j0 < nt; j0 += J, ++t) {
+                    const int st = t % NS;
+                    if (t >= NS) ok = mbar_wait(&empty[st], (uint32_t)(((t / NS) - 1) & 1));
+                    if (!ok || *(volatile int*)&abort_flag) {
+                        ok = false;
+                        break;
+                    }
+                    const int jn = min(J, nt - j0);
+                    const uintptr_t a0 = (uintptr_t)(v.near_cores + v.nb_off[b] + j0 * colf);
+                    const uintptr_t a1 = a0 + (uintptr_t)(jn * colf) * sizeof(T);
+                    const uintptr_t s0 = a0 & ~(uintptr_t)15, e0 = (a1 + 15) & ~(uintptr_t)15;
+                    uint32_t bytes = (uint32_t)(e0 - s0);
+                    const uint32_t xbytes = (j0 == 0) ? (uint32_t)(nt * MC * sizeof(T)) : 0u;
+                    mbar_expect_tx(&full[st], bytes + xbytes);
+                    bulk_g2s(stg + st * STB, (const void*)s0, bytes, &full[st]);
+                    if (xbytes)
+                        bulk_g2s(xs + (size_t)(b - b0) * maxleaf * MC, v.Xc + (long long)tb * MC, xbytes, &full[st]);
+                }
+            }
+            if (!ok) {
+                atomicAdd(v.flags + 1, 1);
+                abort_flag = 1;
+            }
+            // before the CTA's shared memory goes: wait (bounded) for the copies still in flight,
+            // i.e. the last NS chunks issued
+            for (int u = max(0, t - NS); u < t; ++u) mbar_wait(&full[u % NS], (uint32_t)((u / NS) & 1));
+        }
+        return;
+    }
+
+    // ---------------- consumer warps
+    const int RP = (ns + 31) & ~31;
+    const int G = kThreads / RP;
+    const int i = tid % RP, g = tid / RP;
+    const bool active = (g < G) && (i < ns);
+    T acc[MC];
+#pragma unroll
+    for (int c = 0; c < MC; ++c) acc[c] = T(0);
+    bool ok = true;
+    int t = 0;
+    for (int b = b0; b < b1 && ok; ++b) {
+        const int r = v.nb_rank[b];
+        const int tnode = v.nb_t[b];
+        const int nt = v.node_end[tnode] - v.node_begin[tnode];
+        const long long colf = (long long)r * ns;
+        const int J = near_chunk_cols<T>(r, ns);
+        constexpr int RK = 8;  // ranks up to RK use the unrolled path
+        T wr[RK];
+        const T* wb = v.w + v.nb_woff[b];
+#pragma unroll
+        for (int k = 0; k < RK; ++k) wr[k] = (k < r) ? wb[k] : T(0);
+        const T* xsb = xs + (size_t)(b - b0) * maxleaf * MC;
+        for (int j0 = 0; j0 < nt; j0 += J, ++t) {
+            const int st = t % NS;
+            ok = mbar_wait(&full[st], (uint32_t)((t / NS) & 1)) && !*(volatile int*)&abort_flag;
+            if (!ok) break;
+            const int jn = min(J, nt - j0);
+            const uintptr_t a0 = (uintptr_t)(v.near_cores + v.nb_off[b] + j0 * colf);
+            const T* Gs = reinterpret_cast<const T*>(stg + st * STB + (a0 & 15)) + i;
+            if (active) {
+                for (int jj = g; jj < jn; jj += G) {
+                    const T* gj = Gs + jj * colf;
+                    T dij = T(0);
+                    if (r <= RK) {
+#pragma unroll
+                        for (int k = 0; k < RK; ++k)
+                            if (k < r) dij += wr[k] * gj[(long long)k * ns];
+                    } else {
+                        for (int k = 0; k < r; ++k) dij += wb[k] * gj[(long long)k * ns];
+                    }
+                    const T* xj = xsb + (j0 + jj) * MC;
+#pragma unroll
+                    for (int c = 0; c < MC; ++c) acc[c] += dij * xj[c];
+                }
+            }
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[st])) : "memory");
+        }
+    }
+    if (!ok && lane == 0) atomicExch(&abort_flag, 1);
+    // reduce the column groups (the stages are no longer written: every chunk was consumed)
+    asm volatile("bar.sync 1, %0;" ::"r"(kThreads) : "memory");
+    if (ok) {
+#pragma unroll
+        for (int c = 0; c < MC; ++c) red[tid * MC + c] = acc[c];
+    }
+    asm volatile("bar.sync 1, %0;" ::"r"(kThreads) : "memory");
+    if (ok && g == 0 && i < ns) {
+        for (int gg = 1; gg < G; ++gg)
+#pragma unroll
+            for (int c = 0; c < MC; ++c) acc[c] += red[(gg * RP + i) * MC + c];
+        T* part = v.partials + (long long)item * v.part_stride * MC;
+#pragma unroll
+        for (int c = 0; c < MC; ++c) part[(long long)i * MC + c] = acc[c];
+    }
+}
+
 // Explicit coupling, phase 2 (grouped by target s): yhat_s += sum over far blocks b of s of
 // L_k z_b, L_k = (I (x) G_1^{2}) ... G_d^{2} formed offline (App. A.4).  Thread tile: 8
 // consecutive rows of yhat_s x CT right-hand sides; z_b staged in shared memory eight blocks at a
@@ -1437,12 +1594,24 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
         PH_CUDA(cudaEventRecord(h->ev_fork, stream));
         PH_CUDA(cudaStreamWaitEvent(far, h->ev_fork, 0));
     }
+    // bulk-copy pipelined near field when one chunk of right-hand sides covers X (rows of x_t
+    // contiguous), rows are 16-byte multiples, leaves fit one CTA and a column of cores fits a stage
+    const size_t sm_ntma = (size_t)nt1::NS * nt1::STB + (size_t)4 * maxleaf * MC * sizeof(T);
+    const bool near_tma = h->use_near_tma && S == MC && (MC * sizeof(T)) % 16 == 0 && maxleaf <= kThreads &&
+                          (size_t)h->near_rank_max * maxleaf * sizeof(T) <= (size_t)nt1::STAGE - 16 &&
+                          sm_ntma <= 110 * 1024 && v.n_items > 0;
     for (int c0 = 0; c0 < S; c0 += MC) {
-        size_t smem = ((size_t)maxleaf * MC + (size_t)kThreads * MC + kMaxNearRank) * sizeof(T);
-        set_smem<T, MC>((const void*)near_kernel<T, MC>, smem);
         ProfScope ps(h, 2, stream);
-        near_kernel<T, MC><<<std::max(1, v.n_items), kThreads, smem, stream>>>(v, S, c0, maxleaf);
-        PH_LAUNCH("near_kernel");
+        if (near_tma) {
+            set_smem<T, MC>((const void*)near_tma_kernel<T, MC>, sm_ntma);
+            near_tma_kernel<T, MC><<<v.n_items, kThreads + 32, sm_ntma, stream>>>(v, maxleaf);
+            PH_LAUNCH("near_tma_kernel");
+        } else {
+            size_t smem = ((size_t)maxleaf * MC + (size_t)kThreads * MC + kMaxNearRank) * sizeof(T);
+            set_smem<T, MC>((const void*)near_kernel<T, MC>, smem);
+            near_kernel<T, MC><<<std::max(1, v.n_items), kThreads, smem, stream>>>(v, S, c0, maxleaf);
+            PH_LAUNCH("near_kernel");
+        }
     }
     if (!plan.far_targets.empty()) {
         for (int c0 = 0; c0 < S; c0 += MC) {
