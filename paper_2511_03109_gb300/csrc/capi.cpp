@@ -288,9 +288,10 @@ void refresh_views(ph_handle* h) {
         h->zstride = std::max(h->zstride, h->key_ranks[(size_t)k * (h->Delta + 1) + plan.d]);
         h->rank_max_lr = std::max(h->rank_max_lr, std::max(h->key_ranks[(size_t)k * (h->Delta + 1) + plan.d],
                                                            h->key_ranks[(size_t)k * (h->Delta + 1) + plan.d + 1]));
-        // blocks per item: about 4096 outputs of P = R_k^T X per CTA at 16 right-hand sides
+        // blocks per item: about 8192 outputs of P = R_k^T X per CTA at 16 right-hand sides
+        // (256 threads with tiles of 4 x 8)
         const int rp4 = (h->key_ranks[(size_t)k * (h->Delta + 1) + plan.d + 1] + 3) & ~3;
-        const int nb = std::max(1, std::min(kCouplingItemBlocks, 256 / std::max(4, rp4)));
+        const int nb = std::max(1, std::min(kCouplingItemBlocks, 512 / std::max(4, rp4)));
         for (int i = h->kb_off[k]; i < h->kb_off[k + 1]; i += nb) {
             h->citem_key.push_back(k);
             h->citem_first.push_back(i);

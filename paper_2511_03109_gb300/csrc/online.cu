@@ -787,15 +787,16 @@ __global__ void __launch_bounds__(kThreads, 2) coupling_a_staged_kernel(DevView<
         }
         cp_async_commit();
     };
+    constexpr int CW = (MC >= 8) ? 8 : 4;  // columns of P per thread (N is a multiple of CW)
     const int TR = rp4 / 4;              // row quads of P
-    const int TC = (N + 3) / 4;          // column quads
+    const int TC = (N + CW - 1) / CW;    // column groups
     const int tr = threadIdx.x % TR, tc = threadIdx.x / TR;
     const bool active = tc < TC;
-    T acc[4][4];
+    T acc[4][CW];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[u][j] = T(0);
+        for (int j = 0; j < CW; ++j) acc[u][j] = T(0);
     const int nchunks = PD / KC;
     issue(0, 0);
     for (int c = 0; c < nchunks; ++c) {
@@ -807,17 +808,18 @@ __global__ void __launch_bounds__(kThreads, 2) coupling_a_staged_kernel(DevView<
         }
         __syncthreads();
         const T* A = As + (c & 1) * KC * 64 + 4 * tr;
-        const T* B = Bs + (c & 1) * KC * BS + 4 * tc;
+        const T* B = Bs + (c & 1) * KC * BS + CW * tc;
         if (active) {
 #pragma unroll 8
             for (int kk = 0; kk < KC; ++kk) {
-                T av[4], bv[4];
+                T av[4], bv[CW];
                 load_ct<T, 4>(A + kk * 64, av);
-                load_ct<T, 4>(B + kk * BS, bv);
+#pragma unroll
+                for (int h = 0; h < CW; h += 4) load_ct<T, 4>(B + kk * BS + h, *reinterpret_cast<T(*)[4]>(&bv[h]));
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[u][j] += av[u] * bv[j];
+                    for (int j = 0; j < CW; ++j) acc[u][j] += av[u] * bv[j];
             }
         }
         __syncthreads();  // the buffer of chunk c is refilled by the issue of chunk c + 2
@@ -825,11 +827,15 @@ __global__ void __launch_bounds__(kThreads, 2) coupling_a_staged_kernel(DevView<
     T* Ps = Bs;  // 64 x BS
     if (active)
 #pragma unroll
-        for (int u = 0; u < 4; ++u) store_ct<T, 4>(Ps + (4 * tr + u) * BS + 4 * tc, acc[u]);
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int h = 0; h < CW; h += 4)
+                store_ct<T, 4>(Ps + (4 * tr + u) * BS + CW * tc + h, *reinterpret_cast<T(*)[4]>(&acc[u][h]));
     __syncthreads();
     const T* H = v.H + v.key_hoff[key];
-    for (int e = threadIdx.x; e < rd * TC; e += blockDim.x) {
-        const int r = e / TC, cq = e % TC;
+    const int TQ = (N + 3) / 4;  // column quads of z
+    for (int e = threadIdx.x; e < rd * TQ; e += blockDim.x) {
+        const int r = e / TQ, cq = e % TQ;
         T z[4] = {T(0), T(0), T(0), T(0)};
         for (int q = 0; q < rp; ++q) {
             const T hv = H[r + rd * q];
