@@ -70,10 +70,14 @@ def kernel_source_hash(name):
 
 
 def kernel_of(kind, info):
-    """The kernel behind a profiling kind; phase 1 of the coupling runs on the tensor cores when
-    the handle reports it."""
-    if kind == "coupling" and info.get("tensor_core_phase1"):
+    """The kernel behind a profiling kind, from the variants the last call reported."""
+    var = info.get("kernel_variants", 0)
+    if kind == "coupling" and var & 4:
         return "coupling_a_tc_kernel"
+    if kind == "near" and var & 1:
+        return "near_tma_kernel"
+    if kind == "coupling_b" and var & 2:
+        return "coupling_b_tma_kernel"
     return KERNEL_OF_KIND.get(kind, kind)
 
 
@@ -305,6 +309,7 @@ def run_gpu(args, rank, world, local_rank):
     alone = {k: v for k, v in A.profile_read().items() if v[1] > 0}
     A.profile(False)
     A.set_overlap(True)
+    info = A.info()  # now with the kernel variants of the last call
     dom = max(alone, key=lambda k: alone[k][0])
     dom_ms, dom_launches = alone[dom]
     avg_ms = dom_ms / dom_launches

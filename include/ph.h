@@ -112,6 +112,9 @@ typedef struct {
     double coupling_b_flops_per_rhs;  /* explicit coupling phase 2 (sum L_k z_b); 0 for the TT chain */
     int tensor_core_phase1;  /* 1 when calls with 8 < m <= 16 run phase 1 of the explicit coupling
                                 on the tensor cores (see ph_set_tensor_cores), else 0 */
+    int kernel_variants;     /* kernels the last ph_matvec on this handle launched: bit 0 the
+                                bulk-copy near field, bit 1 the bulk-copy phase 2 of the
+                                coupling, bit 2 the tensor-core phase 1 (0 before any call) */
 } ph_info;
 
 /* Build the parametric matrix (offline stage).

@@ -560,6 +560,7 @@ ph_status ph_get_info(const ph_handle* h, ph_info* info) {
     if (h->opts.fmt == PH_FMT_H) alg += (double)h->st_elems * sc;
     r.alg_bytes_per_call = alg;
     r.tensor_core_phase1 = (h->tc_elems > 0 && h->use_tc && h->rank_max_lr <= 64) ? 1 : 0;  // for 8 < m <= 16
+    r.kernel_variants = h->last_variants;
     // flops per right-hand side
     double fl = 2.0 * (double)r.near_entries;  // D_b x
     for (size_t b = 0; b < plan.near_s.size(); ++b)

@@ -178,7 +178,8 @@ struct ph_handle {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool instantiated = false;
     bool overlap = true;                        // far path on the side stream (ph_set_overlap)
-    bool use_near_tma = true;                   // bulk-copy pipelined near field when it applies
+    bool use_bulk = true;                       // bulk-copy pipelined near field and phase 2 when they apply
+    int last_variants = 0;                      // kernels the last ph_matvec chose (ph_info.kernel_variants)
     int near_rank_max = 0;                      // max near-block rank
     bool use_tc = false;                        // tensor-core phase 1 when available (ph_set_tensor_cores)
     // per-kernel timing (ph_profile_enable / ph_profile_read)

@@ -1580,6 +1580,148 @@ int pick_mc(int m) {
     return 16;
 }
 
+// Explicit coupling, phase 2, bulk-copy pipelined (one chunk of MC right-hand sides with S == MC,
+// PD rows covered by one pass of 8-row x 4-column thread tiles).  CTA = (target s, part): as
+// coupling_b_kernel, but a producer warp streams, for each far block b of the part, z_b (into one
+// of NS small buffers) and L_k in chunks of whole columns (contiguous: [q PD + I]) by bulk copies
+// into a ring of NS stages; the consumer warps take L_k from shared memory and release stages
+// through per-warp mbarrier arrivals.  Every wait is bounded (timeouts counted in flags[1]).
+namespace cb1 {
+constexpr int NS = 4;
+constexpr int STAGE = 16384;
+constexpr int STB = STAGE + 16;
+}  // namespace cb1
+
+template <typename T>
+__device__ __forceinline__ int coupling_chunk_cols(int PD) {
+    const int Q = (cb1::STAGE - 16) / (PD * (int)sizeof(T));
+    return Q < 1 ? 1 : Q;
+}
+
+template <typename T, int MC>
+__global__ void __launch_bounds__(kThreads + 32, 2) coupling_b_tma_kernel(DevView<T> v, int nsplit) {
+    using namespace cb1;
+    constexpr int CT = 4, CQ = MC / CT, RPT = 8;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char* stg = smem_raw;                                // NS x STB
+    T* zbufs = reinterpret_cast<T*>(smem_raw + NS * STB);         // NS x zstride x MC
+    __shared__ __align__(8) uint64_t full[NS], empty[NS];
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    const int PD = v.PD, zst = v.zstride;
+    const int ti = blockIdx.x / nsplit, part = blockIdx.x % nsplit;
+    const int s = v.far_targets[ti];
+    const int fb0 = v.far_by_target[ti], fb1 = v.far_by_target[ti + 1];
+    const int per = (fb1 - fb0 + nsplit - 1) / nsplit;
+    const int my0 = fb0 + part * per, my1 = min(fb1, my0 + per);
+    if (my0 >= my1) return;
+    const int Q = coupling_chunk_cols<T>(PD);
+    if (tid == 0) {
+        for (int i = 0; i < NS; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], kThreads / 32);
+        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp == kThreads / 32) {
+        if (lane == 0) {
+            int t = 0;
+            bool ok = true;
+            for (int fb = my0; fb < my1 && ok; ++fb) {
+                const int key = v.fb_key[fb];
+                const int rd = v.key_ranks[(size_t)key * (v.Delta + 1) + v.d];
+                const T* Lt = v.far_lr + v.key_lroff[key];
+                for (int q0 = 0; q0 < rd; q0 += Q, ++t) {
+                    const int st = t % NS;
+                    if (t >= NS) ok = mbar_wait(&empty[st], (uint32_t)(((t / NS) - 1) & 1));
+                    if (!ok || *(volatile int*)&abort_flag) {
+                        ok = false;
+                        break;
+                    }
+                    const int qn = min(Q, rd - q0);
+                    const uintptr_t a0 = (uintptr_t)(Lt + (long long)q0 * PD);
+                    const uintptr_t a1 = a0 + (uintptr_t)qn * PD * sizeof(T);
+                    const uintptr_t s0 = a0 & ~(uintptr_t)15, e0 = (a1 + 15) & ~(uintptr_t)15;
+                    const uint32_t bytes = (uint32_t)(e0 - s0);
+                    const uint32_t zbytes = (q0 == 0) ? (uint32_t)(rd * MC * sizeof(T)) : 0u;
+                    mbar_expect_tx(&full[st], bytes + zbytes);
+                    bulk_g2s(stg + st * STB, (const void*)s0, bytes, &full[st]);
+                    if (zbytes)
+                        bulk_g2s(zbufs + (size_t)((fb - my0) % NS) * zst * MC, v.zbuf + (long long)fb * zst * MC, zbytes,
+                                 &full[st]);
+                }
+            }
+            if (!ok) {
+                atomicAdd(v.flags + 1, 1);
+                abort_flag = 1;
+            }
+            for (int u = max(0, t - NS); u < t; ++u) mbar_wait(&full[u % NS], (uint32_t)((u / NS) & 1));
+        }
+        return;
+    }
+
+    // consumer warps: thread = 8 consecutive rows I0.. of yhat_s x 4 right-hand sides
+    const int cq = tid % CQ, rg = tid / CQ;
+    const int I0 = rg * RPT;
+    const bool active = I0 < PD;
+    T acc[RPT][CT];
+#pragma unroll
+    for (int i = 0; i < RPT; ++i)
+#pragma unroll
+        for (int c = 0; c < CT; ++c) acc[i][c] = T(0);
+    bool ok = true;
+    int t = 0;
+    for (int fb = my0; fb < my1 && ok; ++fb) {
+        const int key = v.fb_key[fb];
+        const int rd = v.key_ranks[(size_t)key * (v.Delta + 1) + v.d];
+        const T* Lt = v.far_lr + v.key_lroff[key];
+        const T* zb = zbufs + (size_t)((fb - my0) % NS) * zst * MC;
+        for (int q0 = 0; q0 < rd; q0 += Q, ++t) {
+            const int st = t % NS;
+            ok = mbar_wait(&full[st], (uint32_t)((t / NS) & 1)) && !*(volatile int*)&abort_flag;
+            if (!ok) break;
+            const int qn = min(Q, rd - q0);
+            const uintptr_t a0 = (uintptr_t)(Lt + (long long)q0 * PD);
+            const T* Ls = reinterpret_cast<const T*>(stg + st * STB + (a0 & 15)) + I0;
+            if (active) {
+                for (int q = 0; q < qn; ++q) {
+                    T l[RPT], x[CT];
+                    if ((a0 & 15) == 0) {
+                        load_ct<T, 4>(Ls + q * PD, *reinterpret_cast<T(*)[4]>(&l[0]));
+                        load_ct<T, 4>(Ls + q * PD + 4, *reinterpret_cast<T(*)[4]>(&l[4]));
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < RPT; ++i) l[i] = Ls[q * PD + i];
+                    }
+                    load_ct<T, CT>(zb + (q0 + q) * MC + cq * CT, x);
+#pragma unroll
+                    for (int i = 0; i < RPT; ++i)
+#pragma unroll
+                        for (int c = 0; c < CT; ++c) acc[i][c] += l[i] * x[c];
+                }
+            }
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[st])) : "memory");
+        }
+    }
+    if (!ok) {
+        if (lane == 0) atomicExch(&abort_flag, 1);
+        return;
+    }
+    if (active) {
+        T* dst = v.yhat + (long long)s * PD * MC;
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) {
+            T* o = dst + (long long)(I0 + i) * MC + cq * CT;
+            if (nsplit > 1) atomic_add_ct<T, CT>(o, acc[i]);
+            else store_ct<T, CT>(o, acc[i]);
+        }
+    }
+}
+
 template <typename T, int MC>
 void set_smem(const void* fn, size_t bytes) {
     PH_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
@@ -1594,6 +1736,7 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
     for (int l : plan.leaves) maxleaf = std::max(maxleaf, plan.nodes[l].size());
     const bool h2 = (h->opts.fmt == PH_FMT_H2);
     const int PD = v.PD;
+    h->last_variants = 0;
     // fork: the far path runs on the side stream, concurrently with the near field
     cudaStream_t far = h->overlap ? h->side : stream;
     if (h->overlap) {
@@ -1603,12 +1746,13 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
     // bulk-copy pipelined near field when one chunk of right-hand sides covers X (rows of x_t
     // contiguous), rows are 16-byte multiples, leaves fit one CTA and a column of cores fits a stage
     const size_t sm_ntma = (size_t)nt1::NS * nt1::STB + (size_t)4 * maxleaf * MC * sizeof(T);
-    const bool near_tma = h->use_near_tma && S == MC && (MC * sizeof(T)) % 16 == 0 && maxleaf <= kThreads &&
+    const bool near_tma = h->use_bulk && S == MC && (MC * sizeof(T)) % 16 == 0 && maxleaf <= kThreads &&
                           (size_t)h->near_rank_max * maxleaf * sizeof(T) <= (size_t)nt1::STAGE - 16 &&
                           sm_ntma <= 110 * 1024 && v.n_items > 0;
     for (int c0 = 0; c0 < S; c0 += MC) {
         ProfScope ps(h, 2, stream);
         if (near_tma) {
+            h->last_variants |= 1;
             set_smem<T, MC>((const void*)near_tma_kernel<T, MC>, sm_ntma);
             near_tma_kernel<T, MC><<<v.n_items, kThreads + 32, sm_ntma, stream>>>(v, maxleaf);
             PH_LAUNCH("near_tma_kernel");
@@ -1655,6 +1799,7 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
                                                              cudaFuncAttributeMaxDynamicSharedMemorySize, tc1::SMEM));
                                 const int grid = std::min(v.n_tcitems, h->num_sms);
                                 coupling_a_tc_kernel<<<grid, 128, tc1::SMEM, far>>>(v);
+                                h->last_variants |= 4;
                                 launched = true;
                             }
                         }
@@ -1679,7 +1824,17 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
                         const int nsplit = 4;
                         size_t sm_b = (size_t)8 * v.zstride * MC * sizeof(T);
                         const int nt = (int)plan.far_targets.size() * nsplit;
-                        if (nib <= 1) {
+                        const size_t sm_btma = (size_t)cb1::NS * cb1::STB + (size_t)cb1::NS * v.zstride * MC * sizeof(T);
+                        const bool b_tma = h->use_bulk && S == MC && MC >= 4 && (MC * sizeof(T)) % 16 == 0 &&
+                                           PD % 8 == 0 && itemsb <= kThreads &&
+                                           (size_t)PD * sizeof(T) <= (size_t)cb1::STAGE - 16 && sm_btma <= 110 * 1024;
+                        if (b_tma) {
+                            const int nsp = 2;
+                            set_smem<T, MC>((const void*)coupling_b_tma_kernel<T, MC>, sm_btma);
+                            coupling_b_tma_kernel<T, MC><<<(int)plan.far_targets.size() * nsp, kThreads + 32, sm_btma,
+                                                           far>>>(v, nsp);
+                            h->last_variants |= 2;
+                        } else if (nib <= 1) {
                             set_smem<T, MC>((const void*)coupling_b_kernel<T, MC, 1>, sm_b);
                             coupling_b_kernel<T, MC, 1><<<nt, kThreads, sm_b, far>>>(v, S, c0, nsplit);
                         } else if (nib <= 2) {

@@ -55,7 +55,7 @@ class Info(C.Structure):
                 ("basis_bytes", C.c_long), ("alg_bytes_per_call", C.c_double),
                 ("flops_per_rhs", C.c_double), ("offline_seconds", C.c_double),
                 ("coupling_a_flops_per_rhs", C.c_double), ("coupling_b_flops_per_rhs", C.c_double),
-                ("tensor_core_phase1", C.c_int)]
+                ("tensor_core_phase1", C.c_int), ("kernel_variants", C.c_int)]
 
     def as_dict(self):
         out = {}

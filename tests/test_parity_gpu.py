@@ -86,6 +86,26 @@ def test_tensor_core_phase1_against_cuda_core_and_oracle(ps, theta):
     A.close()
 
 
+def test_bulk_copy_kernels_match_fallback_kernels():
+    """m = 16 takes the bulk-copy near field and phase 2 (one chunk of right-hand sides); m = 17
+    takes the register-staged kernels for the same first 16 columns.  Both meet the oracle."""
+    n = 2500
+    P = inputs.uniform_points(n, 3, 123)
+    X = inputs.gaussian_rhs(n, 17, 124)
+    A, M, targets = build_pair(P, "matern52", [0.1], [0.6], [12], 4, 2, np.sqrt(3.0), 1e-7, 0, "h2", "fp32",
+                               targets_every=9)
+    rows = target_rows(targets)
+    ref = M.matvec(M.instantiate([0.27], targets), X, targets)
+    y16 = device_apply(A, [0.27], X[:, :16], "fp32")
+    assert A.info()["kernel_variants"] & 3 == 3
+    y17 = device_apply(A, [0.27], X, "fp32")
+    assert A.info()["kernel_variants"] & 3 == 0
+    assert np.all(rel_err_rows(ref[:, :16], y16, rows) <= TOL["fp32"])
+    assert np.all(rel_err_rows(ref, y17, rows) <= TOL["fp32"])
+    assert np.all(rel_err_rows(y17[:, :16], y16) <= 2 * TOL["fp32"])
+    A.close()
+
+
 def test_parity_3d_h2_fp32_sampled_rows():
     """3-D Matern 3/2, eta = sqrt(3), 16 right-hand sides; oracle on a sample of target leaves."""
     n = 3000
