@@ -336,6 +336,17 @@ __device__ __forceinline__ void load_ct<double, 4>(const double* p, double (&x)[
     x[0] = v0.x; x[1] = v0.y; x[2] = v1.x; x[3] = v1.y;
 }
 
+// d0 += a0 b0, d1 += a1 b1 as one packed FP32 FMA (same rounding as two fmaf); FP64: two fma.
+__device__ __forceinline__ void fma_pair(float& d0, float& d1, float a0, float a1, float b0, float b1) {
+    const float2 r = __ffma2_rn(make_float2(a0, a1), make_float2(b0, b1), make_float2(d0, d1));
+    d0 = r.x;
+    d1 = r.y;
+}
+__device__ __forceinline__ void fma_pair(double& d0, double& d1, double a0, double a1, double b0, double b1) {
+    d0 = fma(a0, b0, d0);
+    d1 = fma(a1, b1, d1);
+}
+
 // One mode-k product of the tensor z (p^d x MC, little-endian) with a p x p matrix:
 // out[.., a, ..] = sum_b A(a, b) z[.., b, ..] with A(a, b) = E[b p + a] (transposed, up-sweep)
 // or E[a p + b] (down-sweep).  Each thread owns whole fibres along mode k: it loads the p
@@ -819,7 +830,7 @@ __global__ void __launch_bounds__(kThreads, 2) coupling_a_staged_kernel(DevView<
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
 #pragma unroll
-                    for (int j = 0; j < CW; ++j) acc[u][j] += av[u] * bv[j];
+                    for (int j = 0; j < CW; j += 2) fma_pair(acc[u][j], acc[u][j + 1], av[u], av[u], bv[j], bv[j + 1]);
             }
         }
         __syncthreads();  // the buffer of chunk c is refilled by the issue of chunk c + 2
@@ -1169,14 +1180,14 @@ __global__ void __launch_bounds__(128, 1) coupling_a_tc_kernel(DevView<float> v)
 namespace nt1 {
 constexpr int NS = 4;                    // stages
 constexpr int STAGE = 16384;             // bytes of cores per stage
-constexpr int STB = STAGE + 16;          // plus the 16-byte rounding of a chunk's start
+constexpr int STB = STAGE + 32;          // plus the 16-byte rounding of a chunk's start and end
 constexpr int kConsumers = kThreads / 32;
 }  // namespace nt1
 
 template <typename T>
 __device__ __forceinline__ int near_chunk_cols(int r, int ns) {
     const long long colf = (long long)r * ns;
-    const int J = (int)((nt1::STAGE - 16) / (colf * (long long)sizeof(T)));
+    const int J = (int)(nt1::STAGE / (colf * (long long)sizeof(T)));
     return J < 1 ? 1 : J;
 }
 
@@ -1288,7 +1299,7 @@ __global__ void __launch_bounds__(kThreads + 32, 2) near_tma_kernel(DevView<T> v
                     }
                     const T* xj = xsb + (j0 + jj) * MC;
 #pragma unroll
-                    for (int c = 0; c < MC; ++c) acc[c] += dij * xj[c];
+                    for (int c = 0; c < MC; c += 2) fma_pair(acc[c], acc[c + 1], dij, dij, xj[c], xj[c + 1]);
                 }
             }
             __syncwarp();
@@ -1588,13 +1599,13 @@ int pick_mc(int m) {
 // through per-warp mbarrier arrivals.  Every wait is bounded (timeouts counted in flags[1]).
 namespace cb1 {
 constexpr int NS = 4;
-constexpr int STAGE = 16384;
-constexpr int STB = STAGE + 16;
+constexpr int STAGE = 16384;     // bytes of L_k per stage
+constexpr int STB = STAGE + 32;  // plus the 16-byte rounding of a chunk's start and end
 }  // namespace cb1
 
 template <typename T>
 __device__ __forceinline__ int coupling_chunk_cols(int PD) {
-    const int Q = (cb1::STAGE - 16) / (PD * (int)sizeof(T));
+    const int Q = cb1::STAGE / (PD * (int)sizeof(T));
     return Q < 1 ? 1 : Q;
 }
 
@@ -1687,20 +1698,26 @@ __global__ void __launch_bounds__(kThreads + 32, 2) coupling_b_tma_kernel(DevVie
             const uintptr_t a0 = (uintptr_t)(Lt + (long long)q0 * PD);
             const T* Ls = reinterpret_cast<const T*>(stg + st * STB + (a0 & 15)) + I0;
             if (active) {
-                for (int q = 0; q < qn; ++q) {
-                    T l[RPT], x[CT];
-                    if ((a0 & 15) == 0) {
-                        load_ct<T, 4>(Ls + q * PD, *reinterpret_cast<T(*)[4]>(&l[0]));
-                        load_ct<T, 4>(Ls + q * PD + 4, *reinterpret_cast<T(*)[4]>(&l[4]));
-                    } else {
+                for (int qq = 0; qq < qn; qq += 8) {
 #pragma unroll
-                        for (int i = 0; i < RPT; ++i) l[i] = Ls[q * PD + i];
+                    for (int u = 0; u < 8; ++u) {
+                        const int q = qq + u;
+                        if (q < qn) {
+                            T l[RPT], x[CT];
+                            if ((a0 & 15) == 0) {
+                                load_ct<T, 4>(Ls + q * PD, *reinterpret_cast<T(*)[4]>(&l[0]));
+                                load_ct<T, 4>(Ls + q * PD + 4, *reinterpret_cast<T(*)[4]>(&l[4]));
+                            } else {
+#pragma unroll
+                                for (int i = 0; i < RPT; ++i) l[i] = Ls[q * PD + i];
+                            }
+                            load_ct<T, CT>(zb + (q0 + q) * MC + cq * CT, x);
+#pragma unroll
+                            for (int i = 0; i < RPT; i += 2)
+#pragma unroll
+                                for (int c = 0; c < CT; ++c) fma_pair(acc[i][c], acc[i + 1][c], l[i], l[i + 1], x[c], x[c]);
+                        }
                     }
-                    load_ct<T, CT>(zb + (q0 + q) * MC + cq * CT, x);
-#pragma unroll
-                    for (int i = 0; i < RPT; ++i)
-#pragma unroll
-                        for (int c = 0; c < CT; ++c) acc[i][c] += l[i] * x[c];
                 }
             }
             __syncwarp();
@@ -1747,7 +1764,7 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
     // contiguous), rows are 16-byte multiples, leaves fit one CTA and a column of cores fits a stage
     const size_t sm_ntma = (size_t)nt1::NS * nt1::STB + (size_t)4 * maxleaf * MC * sizeof(T);
     const bool near_tma = h->use_bulk && S == MC && (MC * sizeof(T)) % 16 == 0 && maxleaf <= kThreads &&
-                          (size_t)h->near_rank_max * maxleaf * sizeof(T) <= (size_t)nt1::STAGE - 16 &&
+                          (size_t)h->near_rank_max * maxleaf * sizeof(T) <= (size_t)nt1::STAGE &&
                           sm_ntma <= 110 * 1024 && v.n_items > 0;
     for (int c0 = 0; c0 < S; c0 += MC) {
         ProfScope ps(h, 2, stream);
@@ -1827,7 +1844,7 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
                         const size_t sm_btma = (size_t)cb1::NS * cb1::STB + (size_t)cb1::NS * v.zstride * MC * sizeof(T);
                         const bool b_tma = h->use_bulk && S == MC && MC >= 4 && (MC * sizeof(T)) % 16 == 0 &&
                                            PD % 8 == 0 && itemsb <= kThreads &&
-                                           (size_t)PD * sizeof(T) <= (size_t)cb1::STAGE - 16 && sm_btma <= 110 * 1024;
+                                           (size_t)PD * sizeof(T) <= (size_t)cb1::STAGE && sm_btma <= 110 * 1024;
                         if (b_tma) {
                             const int nsp = 2;
                             set_smem<T, MC>((const void*)coupling_b_tma_kernel<T, MC>, sm_btma);
