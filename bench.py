@@ -159,19 +159,37 @@ class ClockSampler:
         self.proc = None
         self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
 
+    def _lines(self):
+        try:
+            with open(self.path) as f:
+                return f.read().splitlines()
+        except OSError:
+            return []
+
     def start(self):
+        """Starts sampling every 50 ms and returns once the first sample is in, so that the
+        samples counted (from `mark()` to `stop()`) fall inside the timed region."""
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        self.first = 0
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                 "-lms", "50"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        t0 = time.time()
+        while time.time() - t0 < 5 and not self._lines() and self.proc.poll() is None:
+            time.sleep(0.01)
+
+    def mark(self):
+        self.first = len(self._lines())
 
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        lines = self._lines()[self.first:]
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -180,8 +198,8 @@ class ClockSampler:
         self.f.close()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        with open(self.path) as f:
-            for line in f:
+        if True:
+            for line in lines:
                 parts = [p.strip() for p in line.split(",")]
                 if len(parts) < 9:
                     continue
@@ -252,15 +270,16 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    sampler.mark()
     ev0.record(stream)
     for k in range(args.steps):
         step(thetas[args.warmup + k])
     ev1.record(stream)
     torch.cuda.synchronize()
+    clocks = sampler.stop()
     if dist:
         dist.barrier()
     ms = ev0.elapsed_time(ev1)
-    clocks = sampler.stop()
     prof = A.profile_read()
     kinds = {k: v for k, v in prof.items() if v[1] > 0}
     A.profile(False)
@@ -338,6 +357,22 @@ def run_gpu(args, rank, world, local_rank):
     roof["peak_source"] = peak_kind
     roof["traffic"] = measured_traffic(dom, info)
     roof["timing"] = "CUDA events around each launch, far and near paths serialised (roofline pass)"
+    # the three large kernels against their own bounds, same pass
+    others = {}
+    alu_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) / 1e6
+    if "near" in alone:
+        t = alone["near"][0] / alone["near"][1] / 1e3
+        b = info["near_bytes"] + 2.0 * n * m * sc + info["near_rank_sum"] * sc
+        others["near"] = {"kernel": kernel_of("near", info), "bound": "hbm", "ms": t * 1e3,
+                          "achieved": b / t / 1e9, "unit": "GB/s", "frac": b / t / 1e9 / peaks["hbm_gbs"],
+                          "traffic": measured_traffic("near", info)}
+    for kind, key in (("coupling", "coupling_a_flops_per_rhs"), ("coupling_b", "coupling_b_flops_per_rhs")):
+        if kind in alone and info[key] > 0:
+            t = alone[kind][0] / alone[kind][1] / 1e3
+            f = info[key] * m
+            others[kind] = {"kernel": kernel_of(kind, info), "bound": "alu", "ms": t * 1e3,
+                            "achieved": f / t / 1e12, "unit": "TFLOP/s", "frac": f / t / 1e12 / alu_peak,
+                            "traffic": measured_traffic(kind, info)}
     gpu_launches = int(sum(v[1] for v in prof.values()))
     # whole-step bytes over the step time, for context
     step_bytes = info["alg_bytes_per_call"] + 2.0 * n * m * sc
@@ -345,7 +380,7 @@ def run_gpu(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": workload_config(), "roofline": roof,
+        "config": workload_config(), "roofline": roof, "rooflines_by_kernel": others,
         "step_hbm_fraction": step_bytes / (ms / args.steps / 1e3) / 1e9 / peaks["hbm_gbs"],
         "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kinds.items()},
         "kernels_ms_alone": {k: v[0] / v[1] for k, v in alone.items()},
@@ -383,6 +418,9 @@ def run_gpu(args, rank, world, local_rank):
 
 
 # -------------------------------------------------------------------- reference (oracle) arm
+REF_TIME_LIMIT = 120.0
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -404,16 +442,22 @@ def run_reference(args, rank, world):
     def step(th):
         M.matvec(M.instantiate(th, targets), Xh, targets)
 
-    for k in range(args.warmup):
+    for k in range(min(args.warmup, 3)):
         step(thetas[k])
+    # each step is about a second of host work: stop after REF_TIME_LIMIT s so that any
+    # --steps finishes within a few minutes, and report the steps actually timed
     t0 = time.perf_counter()
+    done = 0
     for k in range(args.steps):
-        step(thetas[args.warmup + k])
+        step(thetas[(args.warmup + k) % len(thetas)])
+        done += 1
+        if time.perf_counter() - t0 > REF_TIME_LIMIT:
+            break
     dt = (time.perf_counter() - t0) / frac
-    value = args.steps * m / dt
+    value = done * m / dt
     cores = os.cpu_count() or 1
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+           "steps": args.steps, "steps_timed": done, "warmup": args.warmup, "ms_per_step": dt / done * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "config": workload_config(),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -426,7 +470,7 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
