@@ -233,6 +233,16 @@ ph_status ph_profile_read(ph_handle* h, double* ms, long* launches);
 /* Library version string. */
 const char* ph_version(void);
 
+/* Self-test of the device-side wait bound (the paper has no counterpart).  Runs one CTA on
+ * `device` that waits on an mbarrier nothing arrives on, with the same bounded wait the
+ * bulk-copy and tensor-core kernels use (about one second of the global timer).  The kernel
+ * gives up, records it and returns, so the context stays usable.  Returns PH_ERR_TIMEOUT
+ * (what a wait that ran out produces) and stores the seconds waited in *waited (may be
+ * NULL); PH_ERR_INVALID_ARG for a device that does not exist; PH_ERR_CUDA if the launch or
+ * copy failed (message in ph_last_error(NULL)).  Allocates and frees 16 bytes of device
+ * memory; synchronous. */
+ph_status ph_selftest_wait_bound(int device, double* waited);
+
 #ifdef __cplusplus
 }
 #endif

@@ -383,6 +383,19 @@ extern "C" {
 
 const char* ph_version(void) { return "libph 0.1 (sm_103a)"; }
 
+ph_status ph_selftest_wait_bound(int device, double* waited) {
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return fail(nullptr, PH_ERR_INVALID_ARG, "ph_selftest_wait_bound: no CUDA device " + std::to_string(device));
+    }
+    try {
+        return ph::wait_bound_selftest(device, waited);
+    } catch (const ph::Error& e) {
+        return fail(nullptr, e.status, e.what());
+    }
+}
+
 const char* ph_last_error(const ph_handle* h) {
     if (h) return h->last_error.c_str();
     return g_last_error.c_str();

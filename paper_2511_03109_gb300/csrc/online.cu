@@ -897,7 +897,7 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 
 // Bounded wait for the phase `parity` of an mbarrier: gives up after about one second (global
-// timer) and returns false then.
+// timer), or after 2^28 polls should the timer not advance, and returns false then.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     uint32_t done = 0;
     const uint64_t t0 = global_ns();
@@ -906,9 +906,25 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
                      " selp.u32 %0, 1, 0, p;\n}\n"
                      : "=r"(done)
                      : "r"(smem_u32(bar)), "r"(parity));
-        if (!done && (it & 63) == 63 && global_ns() - t0 > 1000000000ull) break;
+        if (!done && (it & 63) == 63 && (global_ns() - t0 > 1000000000ull || it >= (1 << 28) - 1)) break;
     }
     return done != 0;
+}
+
+// One CTA waits on an mbarrier that nothing arrives on, with the bounded wait of the bulk-copy and
+// tensor-core kernels: out[0] = 1 if the wait ended by the phase completing (it cannot), out[1] =
+// nanoseconds waited.
+__global__ void wait_bound_kernel(unsigned long long* out) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    const uint64_t t0 = global_ns();
+    const bool done = mbar_wait(&bar, 0);
+    const uint64_t t1 = global_ns();
+    if (threadIdx.x == 0) {
+        out[0] = done ? 1ull : 0ull;
+        out[1] = t1 - t0;
+    }
 }
 
 __device__ __forceinline__ void umma_tf32(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
@@ -2001,6 +2017,25 @@ ProfScope::~ProfScope() {
     cudaEvent_t e = prof_event(h);
     cudaEventRecord(e, s);
     h->prof_recs.push_back({kind, b, e});
+}
+
+ph_status wait_bound_selftest(int device, double* waited) {
+    int prev = 0;
+    PH_CUDA(cudaGetDevice(&prev));
+    PH_CUDA(cudaSetDevice(device));
+    unsigned long long* d = nullptr;
+    unsigned long long hres[2] = {1, 0};
+    cudaError_t e = cudaMalloc(&d, sizeof(hres));
+    if (e == cudaSuccess) {
+        wait_bound_kernel<<<1, 32>>>(d);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpy(hres, d, sizeof(hres), cudaMemcpyDeviceToHost);
+        cudaFree(d);
+    }
+    cudaSetDevice(prev);
+    if (e != cudaSuccess) throw Error(PH_ERR_CUDA, std::string("wait_bound_kernel: ") + cudaGetErrorString(e));
+    if (waited) *waited = (double)hres[1] * 1e-9;
+    return hres[0] ? PH_OK : PH_ERR_TIMEOUT;
 }
 
 ph_status online_instantiate(ph_handle* h, const double* theta, cudaStream_t stream) {

@@ -87,6 +87,7 @@ _SIGS = {
     "ph_set_overlap": (C.c_int, [_H, C.c_int]),
     "ph_set_tensor_cores": (C.c_int, [_H, C.c_int]),
     "ph_profile_read": (C.c_int, [_H, C.POINTER(C.c_double), C.POINTER(C.c_long)]),
+    "ph_selftest_wait_bound": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -133,6 +134,13 @@ def make_opts(d, theta_lo, theta_hi, degree, p_s, l_max, eta, tol, rank_cap=0, f
     o.device = int(device)
     o.coupling = {"explicit": 0, "chain": 1}[coupling]
     return o
+
+
+def selftest_wait_bound(device=0):
+    """ph_selftest_wait_bound: returns (status, seconds the device-side wait took)."""
+    waited = C.c_double(0.0)
+    st = ph_selftest_wait_bound(int(device), C.byref(waited))
+    return st, waited.value
 
 
 def plan(points, l_max, eta):

@@ -198,6 +198,23 @@ def test_errors_are_status_codes():
     A.close()
 
 
+def test_bounded_device_wait_returns_timeout_and_context_survives():
+    """The device-side wait bound: a wait on an mbarrier nothing arrives on gives up after about
+    a second and reports PH_ERR_TIMEOUT; the context keeps working afterwards."""
+    from paper_2511_03109_gb300 import ph
+
+    st, waited = ph.selftest_wait_bound(0)
+    assert st == ph.PH_ERR_TIMEOUT
+    assert 0.9 <= waited <= 5.0, waited
+    n = 500
+    P = inputs.uniform_points(n, 2, 131)
+    X = inputs.gaussian_rhs(n, 2, 132)
+    A, M, _ = build_pair(P, "gauss", [0.1], [1.0], [10], 5, 3, 1.0, 1e-9, 0, "h2", "fp64")
+    ref = M.matvec(M.instantiate([0.4]), X)
+    assert np.all(rel_err_rows(ref, device_apply(A, [0.4], X, "fp64")) <= TOL["fp64"])
+    A.close()
+
+
 def test_host_entry_point_and_save_load(tmp_path):
     from paper_2511_03109_gb300 import ph
 
