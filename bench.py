@@ -109,7 +109,8 @@ def oracle_sample(P, X, theta, n_leaves=ORACLE_SAMPLE_LEAVES, seed=7):
 
     Offline work for the sample (its near blocks and the far blocks of its ancestors) is done
     first with a spawn-started process pool and is not timed; the timed part is the oracle's
-    instantiate + matvec for the sample rows.  Returns (seconds, rows, Y_rows, cores).
+    instantiate + matvec for the sample rows.  Returns (seconds, rows, Y_rows, cores, leaves,
+    dY_rows) with dY = dK_hat/dtheta X (untimed).
     """
     from oracle import pmatrix
 
@@ -125,7 +126,8 @@ def oracle_sample(P, X, theta, n_leaves=ORACLE_SAMPLE_LEAVES, seed=7):
     Y = M.matvec(inst, X, targets)
     dt = time.perf_counter() - t0
     rows = np.sort(np.concatenate([c.idx for c in targets]))
-    return dt, rows, Y[rows], os.cpu_count() or 1, len(M.leaves)
+    Yd = M.matvec(M.instantiate(theta, targets, deriv=0), X, targets)  # untimed: the derivative check
+    return dt, rows, Y[rows], os.cpu_count() or 1, len(M.leaves), Yd[rows]
 
 
 def _oracle_pool():
@@ -305,6 +307,25 @@ def run_gpu(args, rank, world, local_rank):
     e2e_s = time.perf_counter() - t0
     e2e_s = sharding.max_over_ranks(e2e_s, dist)
 
+    # theta-derivative products dK_hat/dtheta X (ph_instantiate_derivative + ph_matvec), device
+    # inputs as in the timed region
+    def step_d(th):
+        A.instantiate_derivative(th, 0, sp)
+        A.matvec_ptr(X.data_ptr(), n, m, Y.data_ptr(), n, sp)
+
+    nd = min(args.steps, 50)
+    for k in range(min(args.warmup, 3)):
+        step_d(thetas[k])
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for k in range(nd):
+        step_d(thetas[args.warmup + k])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    d_ms = sharding.max_over_ranks(ev0.elapsed_time(ev1), dist)
+
     if rank != 0:
         if dist:
             dist.barrier()
@@ -387,6 +408,9 @@ def run_gpu(args, rank, world, local_rank):
         "gpu_launches": gpu_launches, "clocks": clocks,
         "e2e": {"value": world * args.steps * m / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": n * m * sc + 8 * WL.d, "d2h_bytes_per_step": n * m * sc},
+        "derivative": {"what": "dK_hat/dtheta X: ph_instantiate_derivative + ph_matvec, one theta per step",
+                       "value": world * nd * m / (d_ms / 1e3), "unit": UNIT, "steps": nd,
+                       "ms_per_step": d_ms / nd},
         "offline_seconds": info["offline_seconds"],
         "structure": {k: info[k] for k in ("n_near", "n_far", "n_far_keys", "near_entries", "near_rank_max",
                                            "far_rank_max", "far_rank_mean", "near_bytes", "far_bytes")},
@@ -398,7 +422,11 @@ def run_gpu(args, rank, world, local_rank):
         torch.cuda.synchronize()
         Ygpu = Y.double().cpu().numpy().T
         log("oracle sample")
-        dt, rows, Yo, cores, nleaves = oracle_sample(P, Xh, th0)
+        A.instantiate_derivative(th0, 0, sp)
+        A.matvec_ptr(X.data_ptr(), n, m, Y.data_ptr(), n, sp)
+        torch.cuda.synchronize()
+        Ygpu_d = Y.double().cpu().numpy().T
+        dt, rows, Yo, cores, nleaves, Yod = oracle_sample(P, Xh, th0)
         log(f"oracle sample timed part {dt:.2f} s")
         frac = len(rows) / n
         out["cpu_baseline"] = {"value": m / (dt / frac), "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -406,6 +434,8 @@ def run_gpu(args, rank, world, local_rank):
                                          f"({len(rows)} rows, 16 RHS, one theta); time scaled by n / rows"}
         err = np.linalg.norm(Ygpu[rows] - Yo, axis=0) / np.linalg.norm(Yo, axis=0)
         out["rel_err_vs_oracle"] = float(err.max())
+        out["derivative"]["rel_err_vs_oracle"] = float((np.linalg.norm(Ygpu_d[rows] - Yod, axis=0)
+                                                        / np.linalg.norm(Yod, axis=0)).max())
         from oracle import kernels
         exact = kernels.dense_apply(WL.kernel, P, th0, Xh, rows=rows)
         out["rel_err_vs_exact"] = float((np.linalg.norm(Ygpu[rows] - exact, axis=0)

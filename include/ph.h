@@ -134,6 +134,17 @@ ph_status ph_offline_build(const double* points, long n, ph_kernel kernel,
  * Stream-ordered; theta is copied before the call returns. */
 ph_status ph_instantiate(ph_handle* h, const double* theta, void* stream);
 
+/* The theta-derivative of the instantiated matrix: as ph_instantiate, with the parametric
+ * vector of dimension `dim` replaced by the derivatives of its Lagrange polynomials,
+ * [v_dim']_k = d ell_k / d theta_dim (the other dimensions keep v_i).  Every stored
+ * quantity enters linearly in each v_i (§4.3 near weights, App. A.4 H_b), so the handle
+ * then holds dK_hat(theta) / dtheta_dim and ph_matvec applies it.  The derivative weights
+ * are FP64, by the barycentric derivative (Berrut & Trefethen 2004, §9; the
+ * differentiation-matrix form when theta is a node).  Not in the paper: it serves gradients
+ * of GP hyperparameter objectives.  Errors: as ph_instantiate, plus PH_ERR_INVALID_ARG when
+ * dim is not in [0, d_theta).  Stream-ordered; theta is copied before the call returns. */
+ph_status ph_instantiate_derivative(ph_handle* h, const double* theta, int dim, void* stream);
+
 /* Y = K_hat(theta) X for the last instantiated theta (§4.5: the H-matrix MVM with
  * S_b H_b T_b^T far blocks, or Alg. "Modified H^2-Matrix MVM").
  *   X : device, n x m column-major, leading dimension ldx >= n, original point order.

@@ -275,8 +275,8 @@ class ParametricMatrix:
         return self._E[c.id]
 
     # ------------------------------------------------------------------- online
-    def parametric_vectors(self, theta):
-        return cheb.parametric_vectors(theta, self.theta_lo, self.theta_hi, self.degree)
+    def parametric_vectors(self, theta, deriv=None):
+        return cheb.parametric_vectors(theta, self.theta_lo, self.theta_hi, self.degree, deriv)
 
     def check_theta(self, theta):
         th = np.atleast_1d(np.asarray(theta, float))
@@ -295,10 +295,16 @@ class ParametricMatrix:
         a = G1 @ w[:, 0]
         return tensor.freshape(a, (b.s.n, b.t.n))
 
-    def instantiate(self, theta, targets=None):
-        """Online stage (Alg. "Online Stage", §4.4): D_b(theta) for near blocks, H_b(theta) for far blocks."""
+    def instantiate(self, theta, targets=None, deriv=None):
+        """Online stage (Alg. "Online Stage", §4.4): D_b(theta) for near blocks, H_b(theta) for far blocks.
+
+        ``deriv = i``: instantiate dK_hat/dtheta_i instead (v_i replaced by its derivative; every
+        stored quantity enters linearly in v_i).
+        """
         th = self.check_theta(theta)
-        vs = self.parametric_vectors(th)
+        if deriv is not None and not 0 <= int(deriv) < self.dt:
+            raise ValueError("deriv is not a parameter dimension")
+        vs = self.parametric_vectors(th, deriv)
         near, far = self.blocks_for(targets)
         inst = {"theta": th, "vs": vs, "D": {}, "H": {}}
         for b in near:

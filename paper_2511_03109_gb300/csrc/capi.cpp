@@ -472,9 +472,11 @@ ph_status ph_offline_build(const double* points, long n, ph_kernel kernel, const
     return PH_OK;
 }
 
-ph_status ph_instantiate(ph_handle* h, const double* theta, void* stream) {
+static ph_status instantiate_common(ph_handle* h, const double* theta, int deriv, void* stream) {
     if (!h) return fail(nullptr, PH_ERR_INVALID_ARG, "ph_instantiate: NULL handle");
     if (!theta) return fail(h, PH_ERR_INVALID_ARG, "ph_instantiate: NULL theta");
+    if (deriv < -1 || deriv >= h->opts.dtheta)
+        return fail(h, PH_ERR_INVALID_ARG, "ph_instantiate_derivative: dim outside [0, d_theta)");
     for (int k = 0; k < h->opts.dtheta; ++k) {
         if (!std::isfinite(theta[k])) return fail(h, PH_ERR_NONFINITE, "theta is not finite");
         if (theta[k] < h->opts.theta_lo[k] || theta[k] > h->opts.theta_hi[k])
@@ -482,10 +484,19 @@ ph_status ph_instantiate(ph_handle* h, const double* theta, void* stream) {
     }
     return guarded(h, [&]() -> ph_status {
         PH_CUDA(cudaSetDevice(h->device));
-        ph::online_instantiate(h, theta, as_stream(stream));
+        ph::online_instantiate(h, theta, as_stream(stream), deriv);
         h->instantiated = true;
         return PH_OK;
     });
+}
+
+ph_status ph_instantiate(ph_handle* h, const double* theta, void* stream) {
+    return instantiate_common(h, theta, -1, stream);
+}
+
+ph_status ph_instantiate_derivative(ph_handle* h, const double* theta, int dim, void* stream) {
+    if (dim < 0) return fail(h, PH_ERR_INVALID_ARG, "ph_instantiate_derivative: dim outside [0, d_theta)");
+    return instantiate_common(h, theta, dim, stream);
 }
 
 static ph_status check_mv(ph_handle* h, const void* X, long ldx, int m, void* Y, long ldy) {

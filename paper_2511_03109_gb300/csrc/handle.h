@@ -197,7 +197,7 @@ namespace ph {
 // offline.cu
 ph_status offline_build(ph_handle* h, const double* points, long n);
 // online.cu
-ph_status online_instantiate(ph_handle* h, const double* theta, cudaStream_t stream);
+ph_status online_instantiate(ph_handle* h, const double* theta, cudaStream_t stream, int deriv = -1);
 ph_status wait_bound_selftest(int device, double* waited);  // bounded mbarrier wait on a barrier nothing completes
 ph_status online_matvec(ph_handle* h, const void* X, long ldx, int m, void* Y, long ldy,
                         cudaStream_t stream);

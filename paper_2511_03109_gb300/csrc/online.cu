@@ -30,32 +30,65 @@ constexpr int kThreads = 256;
 
 // v_k(theta) = (w_k / (theta - eta_k)) / sum_j w_j / (theta - eta_j) with the
 // barycentric weights w (Berrut & Trefethen, SIAM Review 2004, eq. 4.2); an
-// exact node gives the exact unit vector.  One warp per parameter dimension.
+// exact node gives the exact unit vector.  For dimension `deriv` the derivatives
+// v_k'(theta) instead (the instantiated matrix is linear in each v_i, so this gives
+// dK_hat/dtheta_deriv).  One warp per parameter dimension.
 __device__ void parametric_vectors(const double* nodes, const double* bw, const int* pt, int dt,
-                                   const double* theta, double (*out)[kMaxPTheta]) {
+                                   const double* theta, int deriv, double (*out)[kMaxPTheta]) {
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     if (warp < dt) {
         const int p = pt[warp];
         const double th = theta[warp];
-        double num = 0.0;
-        bool hit = false;
-        if (lane < p) {
-            double diff = th - nodes[warp * kMaxPTheta + lane];
-            hit = (diff == 0.0);
-            num = hit ? 0.0 : bw[warp * kMaxPTheta + lane] / diff;
+        const double x = (lane < p) ? nodes[warp * kMaxPTheta + lane] : 0.0;
+        const double w = (lane < p) ? bw[warp * kMaxPTheta + lane] : 0.0;
+        const double diff = th - x;
+        const bool hit = (lane < p) && (diff == 0.0);
+        const unsigned any = __ballot_sync(0xffffffffu, hit);
+        auto warp_sum = [](double s) {
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            return s;
+        };
+        if (warp != deriv) {
+            const double num = (lane < p && !hit) ? w / diff : 0.0;
+            const double den = warp_sum(num);
+            if (lane < p) out[warp][lane] = any ? (hit ? 1.0 : 0.0) : num / den;
+        } else if (any) {
+            // theta at node k: ell_j'(x_k) = (w_j / w_k) / (x_k - x_j) for j != k, and the
+            // derivatives sum to zero (the differentiation matrix of Berrut & Trefethen, §9)
+            const int k = __ffs(any) - 1;
+            const double xk = __shfl_sync(0xffffffffu, x, k), wk = __shfl_sync(0xffffffffu, w, k);
+            const double dj = (lane < p && lane != k) ? (w / wk) / (xk - x) : 0.0;
+            const double sum = warp_sum(dj);
+            if (lane < p) out[warp][lane] = (lane == k) ? -sum : dj;
+        } else {
+            // a_j = w_j / (theta - x_j), S = sum a_j, T = sum a_j / (theta - x_j):
+            // ell_j' = (ell_j T - a_j / (theta - x_j)) / S; the nearest node's entry is taken as
+            // minus the sum of the others, which avoids its cancellation
+            const double a = (lane < p) ? w / diff : 0.0;
+            const double S = warp_sum(a);
+            const double T = warp_sum((lane < p) ? a / diff : 0.0);
+            const double dj = (lane < p) ? ((a / S) * T - a / diff) / S : 0.0;
+            double best = (lane < p) ? fabs(a) : -1.0;
+            int kmax = lane;
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int ok = __shfl_xor_sync(0xffffffffu, kmax, o);
+                if (ob > best || (ob == best && ok < kmax)) {
+                    best = ob;
+                    kmax = ok;
+                }
+            }
+            const double others = warp_sum(lane == kmax ? 0.0 : dj);
+            if (lane < p) out[warp][lane] = (lane == kmax) ? -others : dj;
         }
-        unsigned any = __ballot_sync(0xffffffffu, hit);
-        double den = num;
-        for (int o = 16; o > 0; o >>= 1) den += __shfl_xor_sync(0xffffffffu, den, o);
-        if (lane < p) out[warp][lane] = any ? (hit ? 1.0 : 0.0) : num / den;
     }
 }
 
 template <typename T>
-__global__ void instantiate_kernel(DevView<T> v, double th0, double th1, double th2, int near_ctas) {
+__global__ void instantiate_kernel(DevView<T> v, double th0, double th1, double th2, int near_ctas, int deriv) {
     __shared__ double sv[kMaxDim][kMaxPTheta];
     const double th[3] = {th0, th1, th2};
-    parametric_vectors(v.theta_nodes, v.theta_bw, v.p_theta, v.dtheta, th, sv);
+    parametric_vectors(v.theta_nodes, v.theta_bw, v.p_theta, v.dtheta, th, deriv, sv);
     __syncthreads();
     const int P = v.p_theta[0];
     if (blockIdx.x == 0 && threadIdx.x < P) v.v64[threadIdx.x] = sv[0][threadIdx.x];
@@ -1983,13 +2016,13 @@ ph_status matvec_typed(ph_handle* h, DevView<T>& v, const T* X, long long ldx, i
 }
 
 template <typename T>
-void instantiate_typed(ph_handle* h, DevView<T>& v, const double* theta, cudaStream_t stream) {
+void instantiate_typed(ph_handle* h, DevView<T>& v, const double* theta, int deriv, cudaStream_t stream) {
     const int near_ctas = (int)ceil_div(std::max(v.n_near, 1), kThreads);
     const int grid = near_ctas + v.n_keys;
     double th[3] = {0, 0, 0};
     for (int k = 0; k < h->opts.dtheta; ++k) th[k] = theta[k];
     ProfScope ps(h, 0, stream);
-    instantiate_kernel<T><<<grid, kThreads, 0, stream>>>(v, th[0], th[1], th[2], near_ctas);
+    instantiate_kernel<T><<<grid, kThreads, 0, stream>>>(v, th[0], th[1], th[2], near_ctas, deriv);
     PH_LAUNCH("instantiate_kernel");
 }
 
@@ -2038,9 +2071,9 @@ ph_status wait_bound_selftest(int device, double* waited) {
     return hres[0] ? PH_OK : PH_ERR_TIMEOUT;
 }
 
-ph_status online_instantiate(ph_handle* h, const double* theta, cudaStream_t stream) {
-    if (h->opts.prec == PH_FP32) instantiate_typed<float>(h, h->vf, theta, stream);
-    else instantiate_typed<double>(h, h->vd, theta, stream);
+ph_status online_instantiate(ph_handle* h, const double* theta, cudaStream_t stream, int deriv) {
+    if (h->opts.prec == PH_FP32) instantiate_typed<float>(h, h->vf, theta, deriv, stream);
+    else instantiate_typed<double>(h, h->vd, theta, deriv, stream);
     return PH_OK;
 }
 

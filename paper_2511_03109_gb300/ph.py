@@ -72,6 +72,7 @@ _SIGS = {
     "ph_offline_build": (C.c_int, [C.POINTER(C.c_double), C.c_long, C.c_int, C.POINTER(BuildOpts),
                                    C.POINTER(_H)]),
     "ph_instantiate": (C.c_int, [_H, C.POINTER(C.c_double), _P]),
+    "ph_instantiate_derivative": (C.c_int, [_H, C.POINTER(C.c_double), C.c_int, _P]),
     "ph_matvec": (C.c_int, [_H, _P, C.c_long, C.c_int, _P, C.c_long, _P]),
     "ph_matvec_host": (C.c_int, [_H, _P, C.c_long, C.c_int, _P, C.c_long, _P]),
     "ph_matvec_noalloc": (C.c_int, [_H, _P, C.c_long, C.c_int, _P, C.c_long, _P]),
@@ -189,6 +190,11 @@ class ParametricMatrix:
     def instantiate(self, theta, stream=0):
         th = (C.c_double * 3)(*[float(t) for t in list(theta)[:3]])
         return check(ph_instantiate(self.h, th, C.c_void_p(stream)), self.h)
+
+    def instantiate_derivative(self, theta, dim, stream=0):
+        """ph_instantiate_derivative: the handle then applies dK_hat(theta)/dtheta_dim."""
+        th = (C.c_double * 3)(*[float(t) for t in list(theta)[:3]])
+        return check(ph_instantiate_derivative(self.h, th, int(dim), C.c_void_p(stream)), self.h)
 
     def matvec_ptr(self, x_ptr, ldx, m, y_ptr, ldy, stream=0):
         return check(ph_matvec(self.h, C.c_void_p(x_ptr), ldx, m, C.c_void_p(y_ptr), ldy,

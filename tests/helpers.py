@@ -27,8 +27,9 @@ def build_pair(P, kernel, lo, hi, degree, p_s, l_max, eta, tol, cap, fmt, prec, 
     return A, M, targets
 
 
-def device_apply(A, theta, X, prec, ldx_pad=0):
-    """Instantiate and apply on cuda:0 through the C ABI (raw device pointers)."""
+def device_apply(A, theta, X, prec, ldx_pad=0, deriv=None):
+    """Instantiate (or, with deriv = i, instantiate dK_hat/dtheta_i) and apply on cuda:0
+    through the C ABI (raw device pointers)."""
     import torch
 
     dt = torch.float64 if prec == "fp64" else torch.float32
@@ -37,7 +38,10 @@ def device_apply(A, theta, X, prec, ldx_pad=0):
     Xd = torch.zeros((m, ld), dtype=dt, device="cuda:0")
     Xd[:, :n] = torch.tensor(X.T, dtype=dt)
     Yd = torch.full((m, ld), float("nan"), dtype=dt, device="cuda:0")
-    A.instantiate(theta)
+    if deriv is None:
+        A.instantiate(theta)
+    else:
+        A.instantiate_derivative(theta, deriv)
     A.matvec_ptr(Xd.data_ptr(), ld, m, Yd.data_ptr(), ld)
     torch.cuda.synchronize()
     return Yd[:, :n].double().cpu().numpy().T

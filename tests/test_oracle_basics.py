@@ -153,3 +153,33 @@ def test_truncation_rank_keeps_ties_whole():
     assert tensor.truncation_rank(s, delta=1.0001e-3) == 4
     assert tensor.truncation_rank(s, delta=1.0, rank_cap=3) == 1
     assert tensor.truncation_rank(s, delta=0.0) == 5
+
+
+@pytest.mark.parametrize("p", [2, 5, 11, 21])
+def test_lagrange_derivative_against_polyder_and_differences(p):
+    """ell_k' from the product rule: sums to zero, differentiates polynomials of degree < p
+    exactly (NumPy's polyder), and matches central differences of the Lagrange values."""
+    rng = np.random.default_rng(9)
+    a, b = 0.05, 0.5
+    nodes = cheb.cheb_nodes(a, b, p)
+    x = np.concatenate([rng.uniform(a, b, 40), nodes])  # includes the nodes themselves
+    Ld = cheb.lagrange_derivative(nodes, x)
+    scale = np.abs(Ld).max()
+    np.testing.assert_allclose(Ld.sum(axis=1), 0.0, atol=1e-12 * scale)
+    coef = rng.standard_normal(p)
+    ref = nppoly.polyval(x, nppoly.polyder(coef))
+    np.testing.assert_allclose(Ld @ nppoly.polyval(nodes, coef), ref, rtol=1e-9,
+                               atol=1e-10 * scale * np.abs(coef).sum())
+    h = 1e-6
+    fd = (cheb.lagrange(nodes, x + h) - cheb.lagrange(nodes, x - h)) / (2 * h)
+    np.testing.assert_allclose(Ld, fd, rtol=0, atol=1e-6 * scale)
+
+
+def test_parametric_vectors_derivative_dimension_only():
+    lo, hi, deg = [0.1, 1.0], [1.0, 3.0], [6, 9]
+    th = [0.43, 2.2]
+    v = cheb.parametric_vectors(th, lo, hi, deg)
+    dv = cheb.parametric_vectors(th, lo, hi, deg, deriv=1)
+    assert np.array_equal(dv[0], v[0])  # other dimensions keep their values
+    nodes = cheb.cheb_nodes(1.0, 3.0, 10)
+    np.testing.assert_allclose(dv[1], cheb.lagrange_derivative(nodes, 2.2)[0], rtol=0, atol=0)

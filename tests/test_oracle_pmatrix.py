@@ -181,3 +181,23 @@ def test_target_rows_match_full():
     part = M.matvec(M.instantiate([0.33], targets), X, targets)
     keep = ~np.isnan(part[:, 0])
     np.testing.assert_allclose(part[keep], full[keep], rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("fmt", ["h2", "h"])
+def test_theta_derivative_against_differences_and_exact_derivative(fmt):
+    """dK_hat/dtheta X (v replaced by its derivative) equals the central difference of the
+    method in theta (K_hat is a polynomial of degree q in theta), and approximates the exact
+    derivative of the Gaussian, d/dl exp(-r^2 / (2 l^2)) = r^2 / l^3 exp(-r^2 / (2 l^2))."""
+    X = np.random.default_rng(21).standard_normal((400, 2))
+    M = _model(400, 2, "gauss", [0.2], [0.6], [24], 8, 2, 1.0, 1e-10, fmt, cap=48)
+    M.offline()
+    th, h = 0.37, 1e-5
+    dY = M.matvec(M.instantiate([th], deriv=0), X)
+    fd = (M.matvec(M.instantiate([th + h]), X) - M.matvec(M.instantiate([th - h]), X)) / (2 * h)
+    assert np.all(pmatrix.relative_error(fd, dY) < 1e-8)
+    P = M.P
+    r2 = ((P[:, None, :] - P[None, :, :]) ** 2).sum(-1)
+    dK = r2 / th ** 3 * np.exp(-r2 / (2 * th * th))
+    assert np.all(pmatrix.relative_error(dK @ X, dY) < 1e-6)
+    with pytest.raises(ValueError):
+        M.instantiate([th], deriv=1)

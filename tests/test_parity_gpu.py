@@ -198,6 +198,37 @@ def test_errors_are_status_codes():
     A.close()
 
 
+DERIV_CASES = [
+    # name, n, d, kernel, lo, hi, degree, p_s, l_max, eta, tol, fmt, prec, m, targets_every
+    ("h2_fp64_d2", 1200, 2, "matern52", [0.1], [0.6], [12], 6, 3, 1.0, 1e-9, "h2", "fp64", 2, None),
+    ("h_fp64_d2", 1000, 2, "gauss", [0.2], [0.9], [14], 6, 3, 1.0, 1e-9, "h", "fp64", 3, None),
+    ("h2_fp32_d3_m16", 2500, 3, "matern32", [0.05], [0.5], [20], 4, 2, np.sqrt(3.0), 1e-6, "h2", "fp32", 16, 9),
+]
+
+
+@pytest.mark.parametrize("case", DERIV_CASES, ids=[c[0] for c in DERIV_CASES])
+def test_theta_derivative_parity(case):
+    """dK_hat/dtheta X (ph_instantiate_derivative + ph_matvec) against the oracle's derivative
+    instantiation, inside the box, at both ends and at a Chebyshev node (the node branch of the
+    barycentric derivative)."""
+    name, n, d, kern, lo, hi, deg, ps, lmax, eta, tol, fmt, prec, m, every = case
+    P = inputs.uniform_points(n, d, 300 + n)
+    X = inputs.gaussian_rhs(n, m, 301 + n)
+    A, M, targets = build_pair(P, kern, lo, hi, deg, ps, lmax, eta, tol, 0, fmt, prec, targets_every=every)
+    rows = None if targets is None else target_rows(targets)
+    node = float(cheb.cheb_nodes(lo[0], hi[0], deg[0] + 1)[3])
+    for theta in ([lo[0] + 0.43 * (hi[0] - lo[0])], [lo[0]], [hi[0]], [node]):
+        ref = M.matvec(M.instantiate(theta, targets, deriv=0), X, targets)
+        got = device_apply(A, theta, X, prec, deriv=0)
+        err = rel_err_rows(ref, got, rows)
+        assert np.all(err <= TOL[prec]), (name, theta, err)
+    from paper_2511_03109_gb300 import ph
+    with pytest.raises(ph.PHError) as e:
+        A.instantiate_derivative([lo[0]], 1)
+    assert e.value.status == ph.PH_ERR_INVALID_ARG
+    A.close()
+
+
 def test_bounded_device_wait_returns_timeout_and_context_survives():
     """The device-side wait bound: a wait on an mbarrier nothing arrives on gives up after about
     a second and reports PH_ERR_TIMEOUT; the context keeps working afterwards."""
