@@ -14,7 +14,7 @@
 
 namespace {
 
-const char kMagic[8] = {'P', 'H', 'L', 'I', 'B', '0', '0', '2'};
+const char kMagic[8] = {'P', 'H', 'L', 'I', 'B', '0', '0', '3'};  // 003: tensor-core R_k layout
 
 struct Writer {
     FILE* f;

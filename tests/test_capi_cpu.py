@@ -78,3 +78,13 @@ def test_null_handle_calls_fail_cleanly():
     assert ph.ph_matvec(None, None, 1, 1, None, 1, None) == ph.PH_ERR_INVALID_ARG
     assert ph.ph_last_error(None)
     ph.ph_destroy(None)
+    assert ph.ph_instantiate_derivative(None, th, 0, None) == ph.PH_ERR_INVALID_ARG
+    assert ph.ph_set_tensor_cores(None, 1) == ph.PH_ERR_INVALID_ARG
+    assert ph.ph_set_overlap(None, 1) == ph.PH_ERR_INVALID_ARG
+    assert ph.ph_profile_enable(None, 1) == ph.PH_ERR_INVALID_ARG
+
+
+def test_wait_bound_selftest_rejects_missing_device():
+    waited = C.c_double(-1.0)
+    assert ph.ph_selftest_wait_bound(-1, C.byref(waited)) == ph.PH_ERR_INVALID_ARG
+    assert waited.value == -1.0  # untouched on error
