@@ -326,6 +326,30 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.synchronize()
     d_ms = sharding.max_over_ranks(ev0.elapsed_time(ev1), dist)
 
+    # many theta, one X (ph_matvec_batched): BATCH_THETAS values per call, the first being the
+    # oracle's theta below; a failure here is reported in the line instead of ending the bench
+    batched = {}
+    try:
+        tb = [thetas[args.warmup]] + list(inputs.uniform_thetas(WL.theta_lo, WL.theta_hi, BATCH_THETAS - 1,
+                                                                 WL.theta_seed + 17))
+        Yb = torch.empty((len(tb), m, n), dtype=torch.float32, device=f"cuda:{local_rank}")
+        A.matvec_batched_ptr(tb, X.data_ptr(), n, m, Yb.data_ptr(), n, m * n, -1, sp)  # warm-up
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(BATCH_CALLS):
+            A.matvec_batched_ptr(tb, X.data_ptr(), n, m, Yb.data_ptr(), n, m * n, -1, sp)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        b_ms = sharding.max_over_ranks(ev0.elapsed_time(ev1), dist) / BATCH_CALLS
+        batched = {"what": f"ph_matvec_batched: {len(tb)} theta x {m} RHS per call, one X",
+                   "value": world * len(tb) * m / (b_ms / 1e3), "unit": UNIT, "ms_per_call": b_ms,
+                   "calls": BATCH_CALLS}
+        Yb0 = Yb[0].double().cpu().numpy().T
+        del Yb
+    except Exception as exc:  # noqa: BLE001 - reported, not hidden
+        batched = {"error": f"{type(exc).__name__}: {exc}"}
+        Yb0 = None
+
     if rank != 0:
         if dist:
             dist.barrier()
@@ -411,6 +435,7 @@ def run_gpu(args, rank, world, local_rank):
         "derivative": {"what": "dK_hat/dtheta X: ph_instantiate_derivative + ph_matvec, one theta per step",
                        "value": world * nd * m / (d_ms / 1e3), "unit": UNIT, "steps": nd,
                        "ms_per_step": d_ms / nd},
+        "batched": batched,
         "offline_seconds": info["offline_seconds"],
         "structure": {k: info[k] for k in ("n_near", "n_far", "n_far_keys", "near_entries", "near_rank_max",
                                            "far_rank_max", "far_rank_mean", "near_bytes", "far_bytes")},
@@ -436,6 +461,9 @@ def run_gpu(args, rank, world, local_rank):
         out["rel_err_vs_oracle"] = float(err.max())
         out["derivative"]["rel_err_vs_oracle"] = float((np.linalg.norm(Ygpu_d[rows] - Yod, axis=0)
                                                         / np.linalg.norm(Yod, axis=0)).max())
+        if Yb0 is not None:
+            out["batched"]["rel_err_vs_oracle"] = float((np.linalg.norm(Yb0[rows] - Yo, axis=0)
+                                                         / np.linalg.norm(Yo, axis=0)).max())
         from oracle import kernels
         exact = kernels.dense_apply(WL.kernel, P, th0, Xh, rows=rows)
         out["rel_err_vs_exact"] = float((np.linalg.norm(Ygpu[rows] - exact, axis=0)
@@ -449,6 +477,8 @@ def run_gpu(args, rank, world, local_rank):
 
 # -------------------------------------------------------------------- reference (oracle) arm
 REF_TIME_LIMIT = 120.0
+BATCH_THETAS = 256
+BATCH_CALLS = 3
 
 
 def run_reference(args, rank, world):

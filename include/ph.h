@@ -154,6 +154,27 @@ ph_status ph_instantiate_derivative(ph_handle* h, const double* theta, int dim, 
 ph_status ph_matvec(ph_handle* h, const void* X, long ldx, int m, void* Y, long ldy,
                     void* stream);
 
+/* Many theta, one block of right-hand sides (d_theta = 1): Y_t = K_hat(theta_t) X for
+ * t < n_theta, or dK_hat/dtheta(theta_t) X with deriv = 0 (deriv = -1: the matrix itself).
+ * K_hat(theta) is linear in the parametric vector (§4.3 weights, App. A.4 H_b), so
+ * K_hat(theta) X = sum_q ell_q(theta) K_hat(eta_q) X exactly over the p_theta Chebyshev nodes
+ * eta_q.  With n_theta >= p_theta the call forms the p_theta products K_hat(eta_q) X once and
+ * combines them per theta in one kernel (the weights in FP64, by the barycentric formula);
+ * with fewer theta, and always for the derivative of an FP32 handle (whose node combination
+ * would amplify FP32 rounding by the size of the derivative weights), it instantiates and
+ * applies once per theta.  Not in the paper.
+ *   thetas   : host, n_theta doubles, each in B_theta (1 <= n_theta <= 2,097,120).
+ *   X        : device, n x m, column-major, leading dimension ldx >= n, original order.
+ *   Y        : device, n_theta blocks n x m, block t at Y + t * stride_y (elements), leading
+ *              dimension ldy >= n, stride_y >= ldy * m; overwritten.
+ * Leaves the handle instantiated at an unspecified theta: call ph_instantiate before the
+ * next ph_matvec.  Allocates p_theta * n * m scalars of workspace on first use (kept by the
+ * handle).  Errors: PH_ERR_INVALID_ARG (sizes, deriv), PH_ERR_THETA_OUT_OF_BOX,
+ * PH_ERR_NONFINITE (theta), PH_ERR_UNSUPPORTED (d_theta != 1), PH_ERR_OOM, PH_ERR_CUDA.
+ * Stream-ordered; thetas are copied before the call returns. */
+ph_status ph_matvec_batched(ph_handle* h, const double* thetas, int n_theta, const void* X, long ldx, int m,
+                            void* Y, long ldy, long stride_y, int deriv, void* stream);
+
 /* ph_matvec on HOST buffers: copies X to the device, applies K_hat(theta),
  * copies Y back and synchronises the stream before returning.  X and Y are
  * host pointers with the same layout as in ph_matvec (pinned memory makes the

@@ -516,6 +516,27 @@ ph_status ph_matvec(ph_handle* h, const void* X, long ldx, int m, void* Y, long 
     });
 }
 
+ph_status ph_matvec_batched(ph_handle* h, const double* thetas, int n_theta, const void* X, long ldx, int m, void* Y,
+                            long ldy, long stride_y, int deriv, void* stream) {
+    if (!h) return fail(nullptr, PH_ERR_INVALID_ARG, "ph_matvec_batched: NULL handle");
+    if (!thetas || n_theta < 1 || n_theta > 65535 * 32 || !X || !Y || m < 1 || m > 1024 || ldx < h->plan.n ||
+        ldy < h->plan.n || stride_y < ldy * (long)m || deriv < -1 || deriv >= h->opts.dtheta)
+        return fail(h, PH_ERR_INVALID_ARG, "ph_matvec_batched: invalid argument");
+    if (h->opts.dtheta != 1) return fail(h, PH_ERR_UNSUPPORTED, "ph_matvec_batched: d_theta must be 1");
+    for (int t = 0; t < n_theta; ++t) {
+        if (!std::isfinite(thetas[t])) return fail(h, PH_ERR_NONFINITE, "theta is not finite");
+        if (thetas[t] < h->opts.theta_lo[0] || thetas[t] > h->opts.theta_hi[0])
+            return fail(h, PH_ERR_THETA_OUT_OF_BOX, "theta outside the parameter box");
+    }
+    return guarded(h, [&]() -> ph_status {
+        PH_CUDA(cudaSetDevice(h->device));
+        ph_status st = ph::online_matvec_batched(h, thetas, n_theta, X, ldx, m, Y, ldy, stride_y, deriv,
+                                                 as_stream(stream));
+        h->instantiated = true;
+        return st;
+    });
+}
+
 ph_status ph_matvec_host(ph_handle* h, const void* X, long ldx, int m, void* Y, long ldy, void* stream) {
     ph_status s = check_mv(h, X, ldx, m, Y, ldy);
     if (s != PH_OK) return s;

@@ -156,6 +156,11 @@ struct ph_handle {
     // workspace, sized for mcap right-hand sides
     int mcap = 0;
     void* d_Xc = nullptr;
+    void* d_ynodes = nullptr;                   // K_hat(eta_q) X at the theta nodes (ph_matvec_batched)
+    size_t ynodes_bytes = 0;
+    double* d_thetas = nullptr;                 // the theta values of a batched call
+    size_t thetas_cap = 0;
+    std::vector<double> host_thetas;            // source of their copy (kept until the next call)
     void* d_Ynear = nullptr;
     void* d_yfar = nullptr;
     void* d_xhat = nullptr;
@@ -198,6 +203,8 @@ namespace ph {
 ph_status offline_build(ph_handle* h, const double* points, long n);
 // online.cu
 ph_status online_instantiate(ph_handle* h, const double* theta, cudaStream_t stream, int deriv = -1);
+ph_status online_matvec_batched(ph_handle* h, const double* thetas, int n_theta, const void* X, long ldx, int m,
+                                void* Y, long ldy, long stride_y, int deriv, cudaStream_t stream);
 ph_status wait_bound_selftest(int device, double* waited);  // bounded mbarrier wait on a barrier nothing completes
 ph_status online_matvec(ph_handle* h, const void* X, long ldx, int m, void* Y, long ldy,
                         cudaStream_t stream);

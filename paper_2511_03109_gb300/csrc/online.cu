@@ -33,55 +33,61 @@ constexpr int kThreads = 256;
 // exact node gives the exact unit vector.  For dimension `deriv` the derivatives
 // v_k'(theta) instead (the instantiated matrix is linear in each v_i, so this gives
 // dK_hat/dtheta_deriv).  One warp per parameter dimension.
+// One warp: out[k] = ell_k(theta) (or ell_k'(theta) with deriv) for the p nodes / barycentric
+// weights given; lanes >= p write nothing.  Every lane of the warp must call it.
+__device__ void lagrange_weights_warp(const double* nodes, const double* bw, int p, double th, bool deriv,
+                                      double* out) {
+    const int lane = threadIdx.x % 32;
+    const double x = (lane < p) ? nodes[lane] : 0.0;
+    const double w = (lane < p) ? bw[lane] : 0.0;
+    const double diff = th - x;
+    const bool hit = (lane < p) && (diff == 0.0);
+    const unsigned any = __ballot_sync(0xffffffffu, hit);
+    auto warp_sum = [](double s) {
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        return s;
+    };
+    if (!deriv) {
+        const double num = (lane < p && !hit) ? w / diff : 0.0;
+        const double den = warp_sum(num);
+        if (lane < p) out[lane] = any ? (hit ? 1.0 : 0.0) : num / den;
+    } else if (any) {
+        // theta at node k: ell_j'(x_k) = (w_j / w_k) / (x_k - x_j) for j != k, and the
+        // derivatives sum to zero (the differentiation matrix of Berrut & Trefethen, §9)
+        const int k = __ffs(any) - 1;
+        const double xk = __shfl_sync(0xffffffffu, x, k), wk = __shfl_sync(0xffffffffu, w, k);
+        const double dj = (lane < p && lane != k) ? (w / wk) / (xk - x) : 0.0;
+        const double sum = warp_sum(dj);
+        if (lane < p) out[lane] = (lane == k) ? -sum : dj;
+    } else {
+        // a_j = w_j / (theta - x_j), S = sum a_j, T = sum a_j / (theta - x_j):
+        // ell_j' = (ell_j T - a_j / (theta - x_j)) / S; the nearest node's entry is taken as
+        // minus the sum of the others, which avoids its cancellation
+        const double a = (lane < p) ? w / diff : 0.0;
+        const double S = warp_sum(a);
+        const double T = warp_sum((lane < p) ? a / diff : 0.0);
+        const double dj = (lane < p) ? ((a / S) * T - a / diff) / S : 0.0;
+        double best = (lane < p) ? fabs(a) : -1.0;
+        int kmax = lane;
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int ok = __shfl_xor_sync(0xffffffffu, kmax, o);
+            if (ob > best || (ob == best && ok < kmax)) {
+                best = ob;
+                kmax = ok;
+            }
+        }
+        const double others = warp_sum(lane == kmax ? 0.0 : dj);
+        if (lane < p) out[lane] = (lane == kmax) ? -others : dj;
+    }
+}
+
 __device__ void parametric_vectors(const double* nodes, const double* bw, const int* pt, int dt,
                                    const double* theta, int deriv, double (*out)[kMaxPTheta]) {
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    if (warp < dt) {
-        const int p = pt[warp];
-        const double th = theta[warp];
-        const double x = (lane < p) ? nodes[warp * kMaxPTheta + lane] : 0.0;
-        const double w = (lane < p) ? bw[warp * kMaxPTheta + lane] : 0.0;
-        const double diff = th - x;
-        const bool hit = (lane < p) && (diff == 0.0);
-        const unsigned any = __ballot_sync(0xffffffffu, hit);
-        auto warp_sum = [](double s) {
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            return s;
-        };
-        if (warp != deriv) {
-            const double num = (lane < p && !hit) ? w / diff : 0.0;
-            const double den = warp_sum(num);
-            if (lane < p) out[warp][lane] = any ? (hit ? 1.0 : 0.0) : num / den;
-        } else if (any) {
-            // theta at node k: ell_j'(x_k) = (w_j / w_k) / (x_k - x_j) for j != k, and the
-            // derivatives sum to zero (the differentiation matrix of Berrut & Trefethen, §9)
-            const int k = __ffs(any) - 1;
-            const double xk = __shfl_sync(0xffffffffu, x, k), wk = __shfl_sync(0xffffffffu, w, k);
-            const double dj = (lane < p && lane != k) ? (w / wk) / (xk - x) : 0.0;
-            const double sum = warp_sum(dj);
-            if (lane < p) out[warp][lane] = (lane == k) ? -sum : dj;
-        } else {
-            // a_j = w_j / (theta - x_j), S = sum a_j, T = sum a_j / (theta - x_j):
-            // ell_j' = (ell_j T - a_j / (theta - x_j)) / S; the nearest node's entry is taken as
-            // minus the sum of the others, which avoids its cancellation
-            const double a = (lane < p) ? w / diff : 0.0;
-            const double S = warp_sum(a);
-            const double T = warp_sum((lane < p) ? a / diff : 0.0);
-            const double dj = (lane < p) ? ((a / S) * T - a / diff) / S : 0.0;
-            double best = (lane < p) ? fabs(a) : -1.0;
-            int kmax = lane;
-            for (int o = 16; o > 0; o >>= 1) {
-                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-                const int ok = __shfl_xor_sync(0xffffffffu, kmax, o);
-                if (ob > best || (ob == best && ok < kmax)) {
-                    best = ob;
-                    kmax = ok;
-                }
-            }
-            const double others = warp_sum(lane == kmax ? 0.0 : dj);
-            if (lane < p) out[warp][lane] = (lane == kmax) ? -others : dj;
-        }
-    }
+    const int warp = threadIdx.x / 32;
+    if (warp < dt)
+        lagrange_weights_warp(nodes + warp * kMaxPTheta, bw + warp * kMaxPTheta, pt[warp], theta[warp],
+                              warp == deriv, out[warp]);
 }
 
 template <typename T>
@@ -117,6 +123,47 @@ __global__ void instantiate_kernel(DevView<T> v, double th0, double th1, double 
             double s = 0.0;
             for (int t = 0; t < P; ++t) s += G[a + ra * (t + P * b)] * sv[0][t];
             H[e] = (T)s;
+        }
+    }
+}
+
+// Many theta, one X: the instantiated matrix is linear in the parametric vector (§4.3 weights,
+// App. A.4 H_b), so K_hat(theta) X = sum_q ell_q(theta) K_hat(eta_q) X exactly, with eta_q the
+// theta nodes; likewise its derivative with ell_q'.  Yq holds the p products K_hat(eta_q) X
+// (n x m each, leading dimension n).  CTA (x, y): a range of the n m entries for up to 32
+// values of theta, whose weights one warp each forms in FP64 (cast to T for the sums).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) node_combine_kernel(DevView<T> v, const T* __restrict__ Yq, int n, int m,
+                                                               const double* __restrict__ thetas, int n_theta,
+                                                               int deriv, T* __restrict__ Y, long long ldy,
+                                                               long long stride_y) {
+    constexpr int TB = 32;
+    __shared__ double Wd[TB][kMaxPTheta];
+    __shared__ T W[TB][kMaxPTheta];
+    const int p = v.p_theta[0];
+    const int t0 = blockIdx.y * TB;
+    const int tc = min(TB, n_theta - t0);
+    const int warp = threadIdx.x / 32;
+    for (int tt = warp; tt < tc; tt += kThreads / 32)
+        lagrange_weights_warp(v.theta_nodes, v.theta_bw, p, thetas[t0 + tt], deriv >= 0, Wd[tt]);
+    __syncthreads();
+    for (int e = threadIdx.x; e < TB * kMaxPTheta; e += blockDim.x) {
+        const int tt = e / kMaxPTheta, q = e % kMaxPTheta;
+        W[tt][q] = (tt < tc && q < p) ? (T)Wd[tt][q] : T(0);
+    }
+    __syncthreads();
+    const long long nel = (long long)n * m;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nel;
+         e += (long long)gridDim.x * blockDim.x) {
+        T yq[kMaxPTheta];
+#pragma unroll
+        for (int q = 0; q < kMaxPTheta; ++q) yq[q] = (q < p) ? Yq[(long long)q * nel + e] : T(0);
+        const long long i = e % n, c = e / n;
+        for (int tt = 0; tt < tc; ++tt) {
+            T acc = T(0);
+#pragma unroll
+            for (int q = 0; q < kMaxPTheta; ++q) acc += W[tt][q] * yq[q];
+            Y[(long long)(t0 + tt) * stride_y + i + c * ldy] = acc;
         }
     }
 }
@@ -2082,6 +2129,56 @@ ph_status online_matvec_view(ph_handle* h, DevView<float>& vf, DevView<double>& 
     if (h->opts.prec == PH_FP32)
         return matvec_typed<float>(h, vf, (const float*)X, ldx, m, (float*)Y, ldy, stream);
     return matvec_typed<double>(h, vd, (const double*)X, ldx, m, (double*)Y, ldy, stream);
+}
+
+ph_status online_matvec_batched(ph_handle* h, const double* thetas, int n_theta, const void* X, long ldx, int m,
+                                void* Y, long ldy, long stride_y, int deriv, cudaStream_t stream) {
+    const int p = h->opts.degree[0] + 1;
+    const size_t sc = h->scalar;
+    // FP32 derivatives always take the direct route: the derivative weights alternate in sign and
+    // grow like p^2 / (theta_hi - theta_lo), so combining FP32 node products would amplify their
+    // rounding; the direct route cancels in FP64 inside the instantiation
+    if (h->opts.dtheta != 1 || n_theta < p || (deriv >= 0 && h->opts.prec == PH_FP32)) {
+        // one instantiation and product per theta
+        for (int t = 0; t < n_theta; ++t) {
+            online_instantiate(h, thetas + t, stream, deriv);
+            online_matvec(h, X, ldx, m, (char*)Y + (size_t)t * stride_y * sc, ldy, stream);
+        }
+        return PH_OK;
+    }
+    const long n = h->plan.n;
+    const size_t ybytes = (size_t)p * n * m * sc;
+    if (ybytes > h->ynodes_bytes) {
+        dev_free(h, h->d_ynodes);
+        h->d_ynodes = dev_alloc(h, ybytes);
+        h->ynodes_bytes = ybytes;
+    }
+    if ((size_t)n_theta > h->thetas_cap) {
+        dev_free(h, h->d_thetas);
+        h->d_thetas = (double*)dev_alloc(h, (size_t)n_theta * sizeof(double));
+        h->thetas_cap = (size_t)n_theta;
+    }
+    for (int q = 0; q < p; ++q) {
+        const double eta = h->theta_nodes[q];
+        online_instantiate(h, &eta, stream, -1);
+        online_matvec(h, X, ldx, m, (char*)h->d_ynodes + (size_t)q * n * m * sc, n, stream);
+    }
+    h->host_thetas.assign(thetas, thetas + n_theta);
+    PH_CUDA(cudaMemcpyAsync(h->d_thetas, h->host_thetas.data(), (size_t)n_theta * sizeof(double),
+                            cudaMemcpyHostToDevice, stream));
+    const long long nel = (long long)n * m;
+    dim3 grid((unsigned)std::max<long long>(1, std::min<long long>(ceil_div(nel, kThreads), (long long)h->num_sms * 4)),
+              (unsigned)ceil_div(n_theta, 32));
+    if (h->opts.prec == PH_FP32)
+        node_combine_kernel<float><<<grid, kThreads, 0, stream>>>(h->vf, (const float*)h->d_ynodes, (int)n, m,
+                                                                  h->d_thetas, n_theta, deriv, (float*)Y, ldy,
+                                                                  stride_y);
+    else
+        node_combine_kernel<double><<<grid, kThreads, 0, stream>>>(h->vd, (const double*)h->d_ynodes, (int)n, m,
+                                                                   h->d_thetas, n_theta, deriv, (double*)Y, ldy,
+                                                                   stride_y);
+    PH_LAUNCH("node_combine_kernel");
+    return PH_OK;
 }
 
 ph_status online_matvec(ph_handle* h, const void* X, long ldx, int m, void* Y, long ldy, cudaStream_t stream) {

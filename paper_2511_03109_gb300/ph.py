@@ -75,6 +75,8 @@ _SIGS = {
     "ph_instantiate_derivative": (C.c_int, [_H, C.POINTER(C.c_double), C.c_int, _P]),
     "ph_matvec": (C.c_int, [_H, _P, C.c_long, C.c_int, _P, C.c_long, _P]),
     "ph_matvec_host": (C.c_int, [_H, _P, C.c_long, C.c_int, _P, C.c_long, _P]),
+    "ph_matvec_batched": (C.c_int, [_H, C.POINTER(C.c_double), C.c_int, _P, C.c_long, C.c_int, _P, C.c_long,
+                                    C.c_long, C.c_int, _P]),
     "ph_matvec_noalloc": (C.c_int, [_H, _P, C.c_long, C.c_int, _P, C.c_long, _P]),
     "ph_get_info": (C.c_int, [_H, C.POINTER(Info)]),
     "ph_save": (C.c_int, [_H, C.c_char_p]),
@@ -199,6 +201,14 @@ class ParametricMatrix:
     def matvec_ptr(self, x_ptr, ldx, m, y_ptr, ldy, stream=0):
         return check(ph_matvec(self.h, C.c_void_p(x_ptr), ldx, m, C.c_void_p(y_ptr), ldy,
                                C.c_void_p(stream)), self.h)
+
+    def matvec_batched_ptr(self, thetas, x_ptr, ldx, m, y_ptr, ldy, stride_y, deriv=-1, stream=0):
+        """ph_matvec_batched: Y_t = K_hat(theta_t) X (or its theta-derivative with deriv = 0)."""
+        import numpy as np
+        vals = np.ascontiguousarray(np.asarray(thetas, dtype=np.float64).ravel())  # d_theta = 1
+        th = (C.c_double * vals.size)(*vals.tolist())
+        return check(ph_matvec_batched(self.h, th, vals.size, C.c_void_p(x_ptr), ldx, m, C.c_void_p(y_ptr), ldy,
+                                       stride_y, int(deriv), C.c_void_p(stream)), self.h)
 
     def matvec_noalloc_ptr(self, x_ptr, ldx, m, y_ptr, ldy, stream=0):
         """ph_matvec_noalloc: same result as matvec_ptr, workspace in the library's static array."""

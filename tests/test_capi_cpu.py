@@ -79,6 +79,7 @@ def test_null_handle_calls_fail_cleanly():
     assert ph.ph_last_error(None)
     ph.ph_destroy(None)
     assert ph.ph_instantiate_derivative(None, th, 0, None) == ph.PH_ERR_INVALID_ARG
+    assert ph.ph_matvec_batched(None, th, 1, None, 1, 1, None, 1, 1, -1, None) == ph.PH_ERR_INVALID_ARG
     assert ph.ph_set_tensor_cores(None, 1) == ph.PH_ERR_INVALID_ARG
     assert ph.ph_set_overlap(None, 1) == ph.PH_ERR_INVALID_ARG
     assert ph.ph_profile_enable(None, 1) == ph.PH_ERR_INVALID_ARG

@@ -201,3 +201,21 @@ def test_theta_derivative_against_differences_and_exact_derivative(fmt):
     assert np.all(pmatrix.relative_error(dK @ X, dY) < 1e-6)
     with pytest.raises(ValueError):
         M.instantiate([th], deriv=1)
+
+
+@pytest.mark.parametrize("fmt", ["h2", "h"])
+def test_instance_is_lagrange_combination_of_node_instances(fmt):
+    """K_hat(theta) X = sum_q ell_q(theta) K_hat(eta_q) X (and the same with ell_q' for the
+    theta-derivative): the identity the batched product relies on, checked on the oracle."""
+    X = np.random.default_rng(33).standard_normal((350, 2))
+    M = _model(350, 2, "matern52", [0.1], [0.6], [9], 6, 2, 1.0, 1e-9, fmt)
+    M.offline()
+    nodes = cheb.cheb_nodes(0.1, 0.6, 10)
+    Yq = np.stack([M.matvec(M.instantiate([eta]), X) for eta in nodes])
+    for th in (0.1, 0.2345, float(nodes[4]), 0.6):
+        direct = M.matvec(M.instantiate([th]), X)
+        comb = np.tensordot(cheb.lagrange(nodes, th)[0], Yq, axes=1)
+        assert np.all(pmatrix.relative_error(direct, comb) < 1e-12)
+        d_direct = M.matvec(M.instantiate([th], deriv=0), X)
+        d_comb = np.tensordot(cheb.lagrange_derivative(nodes, th)[0], Yq, axes=1)
+        assert np.all(pmatrix.relative_error(d_direct, d_comb) < 1e-11)

@@ -229,6 +229,59 @@ def test_theta_derivative_parity(case):
     A.close()
 
 
+def _batched(A, thetas, X, prec, deriv=-1, ldy_pad=3):
+    """ph_matvec_batched on cuda:0: returns (len(thetas), n, m)."""
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    n, m = X.shape
+    ldy = n + ldy_pad
+    Xd = torch.tensor(X.T, dtype=dt, device="cuda:0").contiguous()
+    Yd = torch.full((len(thetas), m, ldy), float("nan"), dtype=dt, device="cuda:0")
+    A.matvec_batched_ptr(list(thetas), Xd.data_ptr(), n, m, Yd.data_ptr(), ldy, m * ldy, deriv)
+    torch.cuda.synchronize()
+    return Yd[:, :, :n].double().cpu().numpy().transpose(0, 2, 1)
+
+
+@pytest.mark.parametrize("prec,d,m", [("fp64", 2, 3), ("fp32", 3, 16)])
+def test_batched_theta_products(prec, d, m):
+    """ph_matvec_batched: with at least p_theta values of theta it combines the products at the
+    theta nodes, with fewer it applies each theta; both against the oracle per theta, for the
+    matrix and its theta-derivative, and the two routes against each other."""
+    from paper_2511_03109_gb300 import ph
+
+    n = 1200 if d == 2 else 2500
+    P = inputs.uniform_points(n, d, 410 + d)
+    X = inputs.gaussian_rhs(n, m, 411 + d)
+    lmax, eta, ps = (3, 1.0, 6) if d == 2 else (2, np.sqrt(3.0), 4)
+    lo, hi, deg = [0.1], [0.6], [12]
+    A, M, targets = build_pair(P, "matern52", lo, hi, deg, ps, lmax, eta, 1e-7, 0, "h2", prec,
+                               targets_every=None if d == 2 else 9)
+    rows = None if targets is None else target_rows(targets)
+    node = float(cheb.cheb_nodes(lo[0], hi[0], deg[0] + 1)[2])
+    many = [0.1, 0.6, node] + list(np.linspace(0.13, 0.57, 14))  # 17 >= p_theta = 13
+    few = many[:5]
+    for deriv in (-1, 0):
+        Ym = _batched(A, many, X, prec, deriv)
+        Yf = _batched(A, few, X, prec, deriv)
+        for t in (0, 1, 2, 3, 4):
+            ref = M.matvec(M.instantiate([many[t]], targets, deriv=None if deriv < 0 else 0), X, targets)
+            assert np.all(rel_err_rows(ref, Ym[t], rows) <= TOL[prec]), (deriv, t, "nodes")
+            assert np.all(rel_err_rows(ref, Yf[t], rows) <= TOL[prec]), (deriv, t, "direct")
+            assert np.all(rel_err_rows(Yf[t], Ym[t], rows) <= 2 * TOL[prec])
+        t = 11
+        ref = M.matvec(M.instantiate([many[t]], targets, deriv=None if deriv < 0 else 0), X, targets)
+        assert np.all(rel_err_rows(ref, Ym[t], rows) <= TOL[prec])
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    Xd = torch.zeros((m, n), dtype=dt, device="cuda:0")
+    Yd = torch.zeros((2, m, n), dtype=dt, device="cuda:0")
+    with pytest.raises(ph.PHError) as e:  # blocks would overlap
+        A.matvec_batched_ptr([0.2, 0.3], Xd.data_ptr(), n, m, Yd.data_ptr(), n, n * m - 1)
+    assert e.value.status == ph.PH_ERR_INVALID_ARG
+    with pytest.raises(ph.PHError) as e:
+        A.matvec_batched_ptr([0.2, 0.7], Xd.data_ptr(), n, m, Yd.data_ptr(), n, n * m)
+    assert e.value.status == ph.PH_ERR_THETA_OUT_OF_BOX
+    A.close()
+
+
 def test_bounded_device_wait_returns_timeout_and_context_survives():
     """The device-side wait bound: a wait on an mbarrier nothing arrives on gives up after about
     a second and reports PH_ERR_TIMEOUT; the context keeps working afterwards."""
