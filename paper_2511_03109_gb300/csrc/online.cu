@@ -840,9 +840,9 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-// Phase 1 of the explicit coupling, staged path (p_s^d a multiple of 32, MC >= 4): for an item of
-// nb far blocks of class k (nb chosen so that r'_4 x nb MC ~ 4096 outputs, r'_4 = r_{d+1}
-// rounded up to 4), P = R_k^T X with X the items' xhat_t columns, then z_b = H_k P.  Chunks of
+// Phase 1 of the explicit coupling (§4.5, App. A.4), staged path (p_s^d a multiple of 32, MC >= 4):
+// for an item of nb far blocks of class k (nb chosen so that r'_4 x nb MC ~ 8192 outputs,
+// r'_4 = r_{d+1} rounded up to 4), P = R_k^T X with X the items' xhat_t columns, then z_b = H_k P.  Chunks of
 // R_k (32 x r'_4, row-major) and of X (32 x N) are copied into shared memory with 16-byte
 // asynchronous copies, two chunks in flight, so the copy of chunk c + 1 overlaps the products of
 // chunk c.  Thread tile: 4 rows of P x 4 columns.
@@ -1041,7 +1041,8 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                  : "memory");
 }
 
-// Phase 1 of the explicit coupling on the tensor cores (FP32 data, one chunk of 16 right-hand
+// Phase 1 of the explicit coupling, z_b = H_k R_k^T xhat_t (§4.5; R_k from the right cores,
+// App. A.4), on the tensor cores (FP32 data, one chunk of 16 right-hand
 // sides, p_s^d a multiple of 32, r', r_d <= 64).  Persistent: CTA i takes items i, i + G, ...
 // (G = grid size) of up to 8 far blocks of one class k.  An item's columns (block, right-hand
 // side) are the 128 rows of
@@ -1263,7 +1264,8 @@ __global__ void __launch_bounds__(128, 1) coupling_a_tc_kernel(DevView<float> v)
     }
 }
 
-// Near field, bulk-copy pipelined (FP32 / FP64, chunks of MC right-hand sides with S == MC, leaves
+// Near field Y_s += reshape(G_{b,1} w_b) X_t (§4.3, applied as in §4.5), bulk-copy pipelined
+// (FP32 / FP64, chunks of MC right-hand sides with S == MC, leaves
 // of at most kThreads points, r ns <= the stage size).  One CTA per near work item, as
 // near_kernel, with a producer warp: the cores G_{b,1} of the item's blocks are streamed in
 // chunks of whole columns j (each chunk contiguous in memory: [(j r + k) ns + i]) by 1-D bulk
@@ -1687,7 +1689,8 @@ int pick_mc(int m) {
     return 16;
 }
 
-// Explicit coupling, phase 2, bulk-copy pipelined (one chunk of MC right-hand sides with S == MC,
+// Explicit coupling, phase 2: yhat_s += sum_b L_k z_b (§4.5; L_k from the left cores, App. A.4),
+// bulk-copy pipelined (one chunk of MC right-hand sides with S == MC,
 // PD rows covered by one pass of 8-row x 4-column thread tiles).  CTA = (target s, part): as
 // coupling_b_kernel, but a producer warp streams, for each far block b of the part, z_b (into one
 // of NS small buffers) and L_k in chunks of whole columns (contiguous: [q PD + I]) by bulk copies
