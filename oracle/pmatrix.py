@@ -376,6 +376,58 @@ class ParametricMatrix:
         backward(self.root)
         return self._mask(Y, targets)
 
+    # ------------------------------------------------------------------ adjoint
+    def matvec_transpose(self, inst, Ybar):
+        """Xbar = K_hat(theta)^T Ybar, the adjoint of ``matvec`` (not in the paper; the gradient of
+        a scalar function of Y with respect to X).  Every block contributes its transpose:
+        D_b^T Ybar_s into the rows of t; for H, T_b H_b^T S_b^T Ybar_s; for H^2, Alg. FastForward
+        on Ybar with the same nested bases, x_t += C_b^T yhat_s, then Alg. FastBackward into
+        Xbar.  Needs every block compressed (``offline()`` without targets) and instantiated
+        (``instantiate(theta)`` without targets); an instance of the derivative gives
+        (dK_hat/dtheta)^T Ybar.
+        """
+        Ybar = np.asarray(Ybar, float)
+        if Ybar.ndim == 1:
+            return self.matvec_transpose(inst, Ybar[:, None])[:, 0]
+        for b in self.near:
+            if id(b) not in inst["D"]:
+                raise ValueError("matvec_transpose needs an instance of every block")
+        Xb = np.zeros_like(Ybar)
+        for b in self.near:
+            Xb[b.t.idx] += inst["D"][id(b)].T @ Ybar[b.s.idx]
+        if self.fmt == "h":
+            for b in self.far:
+                Xb[b.t.idx] += b.T @ (inst["H"][id(b)].T @ (b.S.T @ Ybar[b.s.idx]))
+            return Xb
+        m = Ybar.shape[1]
+        yhat = {}
+
+        def forward(c):  # Alg. FastForward on Ybar
+            if c.is_leaf():
+                yhat[c.id] = self.basis(c).T @ Ybar[c.idx]
+            else:
+                acc = np.zeros((self.p_s ** self.d, m))
+                for ch in c.children:
+                    forward(ch)
+                    acc += self.transfer(ch).T @ yhat[ch.id]
+                yhat[c.id] = acc
+
+        forward(self.root)
+        xhat = {c.id: np.zeros((self.p_s ** self.d, m)) for c in self.nodes}
+        for b in self.far:
+            xhat[b.t.id] += self.coupling(b, inst).T @ yhat[b.s.id]
+
+        def backward(c):  # Alg. FastBackward into Xbar
+            if c.is_leaf():
+                Xb[c.idx] += self.basis(c) @ xhat[c.id]
+            else:
+                for ch in c.children:
+                    xhat[ch.id] += self.transfer(ch) @ xhat[c.id]
+                    backward(ch)
+
+        backward(self.root)
+        return Xb
+
     def _mask(self, Y, targets):
         if targets is None:
             return Y

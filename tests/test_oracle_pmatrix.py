@@ -219,3 +219,39 @@ def test_instance_is_lagrange_combination_of_node_instances(fmt):
         d_direct = M.matvec(M.instantiate([th], deriv=0), X)
         d_comb = np.tensordot(cheb.lagrange_derivative(nodes, th)[0], Yq, axes=1)
         assert np.all(pmatrix.relative_error(d_direct, d_comb) < 1e-11)
+
+
+@pytest.mark.parametrize("fmt", ["h2", "h"])
+def test_adjoint_inner_products_and_dense_transpose(fmt):
+    """matvec_transpose is the adjoint of matvec: <K_hat x, y> = <x, K_hat^T y> for random x, y
+    (matrix and theta-derivative), and on a tiny problem it applies the transpose of the dense
+    matrix that matvec applies (both formed column by column)."""
+    rng = np.random.default_rng(44)
+    M = _model(400, 2, "matern52", [0.1], [0.6], [8], 6, 3, 1.0, 1e-9, fmt)
+    M.offline()
+    x = rng.standard_normal((400, 3))
+    y = rng.standard_normal((400, 3))
+    for deriv in (None, 0):
+        inst = M.instantiate([0.29], deriv=deriv)
+        lhs = np.sum(M.matvec(inst, x) * y, axis=0)
+        rhs = np.sum(x * M.matvec_transpose(inst, y), axis=0)
+        scale = np.linalg.norm(M.matvec(inst, x), axis=0) * np.linalg.norm(y, axis=0)
+        assert np.all(np.abs(lhs - rhs) <= 1e-13 * scale)
+    T = _model(90, 2, "gauss", [0.2], [0.9], [6], 4, 2, 1.0, 1e-10, fmt)
+    T.offline()
+    assert len(T.far) > 0
+    inst = T.instantiate([0.55])
+    eye = np.eye(90)
+    K = T.matvec(inst, eye)
+    Kt = T.matvec_transpose(inst, eye)
+    np.testing.assert_allclose(Kt, K.T, rtol=0, atol=1e-13 * np.abs(K).max())
+
+
+def test_adjoint_close_to_matrix_for_symmetric_kernel():
+    """For a symmetric kernel K_hat^T differs from K_hat only by the truncations of the blocks
+    (each block and its mirror are compressed on their own)."""
+    M = _model(500, 2, "gauss", [0.1], [1.0], [16], 8, 2, 1.0, 1e-9, "h2", cap=32)
+    M.offline()
+    y = np.random.default_rng(45).standard_normal((500, 2))
+    inst = M.instantiate([0.37])
+    assert np.all(pmatrix.relative_error(M.matvec(inst, y), M.matvec_transpose(inst, y)) < 1e-8)
