@@ -329,10 +329,10 @@ def run_gpu(args, rank, world, local_rank):
 
     # many theta, one X (ph_matvec_batched): BATCH_THETAS values per call, the first being the
     # oracle's theta below; a failure here is reported in the line instead of ending the bench
-    batched = {}
+    b_local, b_err, Yb0 = -1.0, None, None
+    tb = [thetas[args.warmup]] + list(inputs.uniform_thetas(WL.theta_lo, WL.theta_hi, BATCH_THETAS - 1,
+                                                             WL.theta_seed + 17))
     try:
-        tb = [thetas[args.warmup]] + list(inputs.uniform_thetas(WL.theta_lo, WL.theta_hi, BATCH_THETAS - 1,
-                                                                 WL.theta_seed + 17))
         Yb = torch.empty((len(tb), m, n), dtype=torch.float32, device=f"cuda:{local_rank}")
         A.matvec_batched_ptr(tb, X.data_ptr(), n, m, Yb.data_ptr(), n, m * n, -1, sp)  # warm-up
         torch.cuda.synchronize()
@@ -341,15 +341,21 @@ def run_gpu(args, rank, world, local_rank):
             A.matvec_batched_ptr(tb, X.data_ptr(), n, m, Yb.data_ptr(), n, m * n, -1, sp)
         ev1.record(stream)
         torch.cuda.synchronize()
-        b_ms = sharding.max_over_ranks(ev0.elapsed_time(ev1), dist) / BATCH_CALLS
+        b_local = ev0.elapsed_time(ev1) / BATCH_CALLS
+        Yb0 = Yb[0].double().cpu().numpy().T
+        del Yb
+    except Exception as exc:  # noqa: BLE001 - reported in the line, not hidden
+        b_err = f"{type(exc).__name__}: {exc}"
+    # every rank takes part in both reductions, whatever happened above
+    b_ms = sharding.max_over_ranks(b_local, dist)
+    b_fail = sharding.max_over_ranks(1.0 if b_err else 0.0, dist)
+    if b_fail > 0 or b_ms <= 0:
+        batched = {"error": b_err or "failed on another rank"}
+        Yb0 = None
+    else:
         batched = {"what": f"ph_matvec_batched: {len(tb)} theta x {m} RHS per call, one X",
                    "value": world * len(tb) * m / (b_ms / 1e3), "unit": UNIT, "ms_per_call": b_ms,
                    "calls": BATCH_CALLS}
-        Yb0 = Yb[0].double().cpu().numpy().T
-        del Yb
-    except Exception as exc:  # noqa: BLE001 - reported, not hidden
-        batched = {"error": f"{type(exc).__name__}: {exc}"}
-        Yb0 = None
 
     if rank != 0:
         if dist:
