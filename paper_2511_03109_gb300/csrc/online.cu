@@ -1921,10 +1921,12 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
                         }
                         if (launched) {
                         } else if (staged) {
-                            size_t sm_a = ((size_t)2 * 32 * 64 + 2 * 32 * 260) * sizeof(T);
-                            set_smem<T, MC>((const void*)coupling_a_staged_kernel<T, MC>, sm_a);
-                            coupling_a_staged_kernel<T, MC><<<std::max(1, v.n_citems), kThreads, sm_a, far>>>(
-                                v, S, c0);
+                            if constexpr (MC >= 4) {  // staged needs MC >= 4; no instances below that
+                                size_t sm_a = ((size_t)2 * 32 * 64 + 2 * 32 * 260) * sizeof(T);
+                                set_smem<T, MC>((const void*)coupling_a_staged_kernel<T, MC>, sm_a);
+                                coupling_a_staged_kernel<T, MC><<<std::max(1, v.n_citems), kThreads, sm_a, far>>>(
+                                    v, S, c0);
+                            }
                         } else {
                             size_t sm_a = ((size_t)64 * 33 + 32 * 68 + 64 * 68) * sizeof(T);
                             set_smem<T, MC>((const void*)coupling_a_kernel<T, MC>, sm_a);
@@ -1944,12 +1946,18 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
                         const bool b_tma = h->use_bulk && S == MC && MC >= 4 && (MC * sizeof(T)) % 16 == 0 &&
                                            PD % 8 == 0 && itemsb <= kThreads &&
                                            (size_t)PD * sizeof(T) <= (size_t)cb1::STAGE && sm_btma <= 110 * 1024;
-                        if (b_tma) {
-                            const int nsp = 2;
-                            set_smem<T, MC>((const void*)coupling_b_tma_kernel<T, MC>, sm_btma);
-                            coupling_b_tma_kernel<T, MC><<<(int)plan.far_targets.size() * nsp, kThreads + 32, sm_btma,
-                                                           far>>>(v, nsp);
-                            h->last_variants |= 2;
+                        bool b_done = false;
+                        if constexpr (MC >= 4) {  // b_tma needs MC >= 4; no instances below that
+                            if (b_tma) {
+                                const int nsp = 2;
+                                set_smem<T, MC>((const void*)coupling_b_tma_kernel<T, MC>, sm_btma);
+                                coupling_b_tma_kernel<T, MC><<<(int)plan.far_targets.size() * nsp, kThreads + 32,
+                                                               sm_btma, far>>>(v, nsp);
+                                h->last_variants |= 2;
+                                b_done = true;
+                            }
+                        }
+                        if (b_done) {
                         } else if (nib <= 1) {
                             set_smem<T, MC>((const void*)coupling_b_kernel<T, MC, 1>, sm_b);
                             coupling_b_kernel<T, MC, 1><<<nt, kThreads, sm_b, far>>>(v, S, c0, nsplit);
