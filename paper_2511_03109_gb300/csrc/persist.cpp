@@ -36,14 +36,24 @@ struct Writer {
 
 struct Reader {
     FILE* f;
+    unsigned long long left = 0;  // bytes not yet read
+    explicit Reader(FILE* file) : f(file) {
+        if (fseek(f, 0, SEEK_END) == 0) {
+            const long end = ftell(f);
+            left = end > 0 ? (unsigned long long)end : 0ull;
+        }
+        fseek(f, 0, SEEK_SET);
+    }
     void raw(void* p, size_t n) {
-        if (n && fread(p, 1, n, f) != n) throw ph::Error(PH_ERR_IO, "truncated file");
+        if (n > left || (n && fread(p, 1, n, f) != n)) throw ph::Error(PH_ERR_IO, "truncated file");
+        left -= n;
     }
     template <typename T> void val(T& v) { raw(&v, sizeof(T)); }
     template <typename T> void vec(std::vector<T>& v) {
         unsigned long long n = 0;
         val(n);
-        if (n > (1ull << 40)) throw ph::Error(PH_ERR_IO, "corrupt file");
+        // a length the rest of the file cannot hold is corrupt: refuse it before allocating
+        if (n > left / sizeof(T)) throw ph::Error(PH_ERR_IO, "corrupt file");
         v.resize(n);
         raw(v.data(), n * sizeof(T));
     }
@@ -159,7 +169,7 @@ extern "C" ph_status ph_load(const char* path, int device, ph_handle** out) {
     ph_handle* h = new ph_handle();
     ph_status st = PH_OK;
     try {
-        Reader r{f};
+        Reader r(f);
         char magic[8];
         r.raw(magic, 8);
         if (std::memcmp(magic, kMagic, 8) != 0) throw ph::Error(PH_ERR_IO, "not a libph file");

@@ -89,3 +89,26 @@ def test_wait_bound_selftest_rejects_missing_device():
     waited = C.c_double(-1.0)
     assert ph.ph_selftest_wait_bound(-1, C.byref(waited)) == ph.PH_ERR_INVALID_ARG
     assert waited.value == -1.0  # untouched on error
+
+
+def test_load_rejects_missing_foreign_old_and_corrupt_files(tmp_path):
+    """ph_load refuses files it cannot trust before it touches a device: a missing path, a
+    foreign file, the previous format's magic, a truncated file, and a vector length the file
+    cannot hold (refused without allocating it)."""
+    import struct
+
+    def load(path):
+        h = C.c_void_p()
+        return ph.ph_load(str(path).encode(), 0, C.byref(h))
+
+    assert load(tmp_path / "missing.ph") == ph.PH_ERR_IO
+    (tmp_path / "foreign.ph").write_bytes(b"not a handle at all" * 10)
+    assert load(tmp_path / "foreign.ph") == ph.PH_ERR_IO
+    (tmp_path / "old.ph").write_bytes(b"PHLIB002" + bytes(4096))
+    assert load(tmp_path / "old.ph") == ph.PH_ERR_IO
+    (tmp_path / "short.ph").write_bytes(b"PHLIB003" + bytes(3))
+    assert load(tmp_path / "short.ph") == ph.PH_ERR_IO
+    # the right magic followed by 8-byte words of 2^40: whichever field reads a length first
+    # gets an impossible one
+    (tmp_path / "huge.ph").write_bytes(b"PHLIB003" + struct.pack("<Q", 1 << 40) * 4096)
+    assert load(tmp_path / "huge.ph") == ph.PH_ERR_IO
