@@ -67,7 +67,7 @@ typedef enum { PH_FP64 = 0, PH_FP32 = 1 } ph_precision;       /* stored cores an
  * "... H^2-matrix", §4.4).  Fixed-size arrays keep the struct plain. */
 typedef struct {
     int d;                 /* spatial dimension, 1..3 */
-    int dtheta;            /* parameter dimension, 1..3 */
+    int dtheta;            /* parameter dimension; the offline build implements 1 (PH_ERR_UNSUPPORTED else) */
     double theta_lo[3];    /* parameter box B_theta = prod [theta_lo_i, theta_hi_i] */
     double theta_hi[3];
     int degree[3];         /* Chebyshev degree in theta_i; p_theta_i = degree_i + 1 nodes (§2.2) */
