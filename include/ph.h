@@ -233,7 +233,10 @@ const char* ph_last_error(const ph_handle* h);
 ph_status ph_plan(const double* points, long n, int d, int l_max, double eta,
                   long* counts, int* perm);
 
-/* Per-kernel device time, measured with CUDA events recorded on the stream each
+/* Every launch of the library also sits in an NVTX range named for its kind (and each
+ * ph_instantiate / ph_matvec / ph_matvec_batched in one named for the call); without an
+ * attached tool these are no-ops.
+ * Per-kernel device time, measured with CUDA events recorded on the stream each
  * kernel is launched on (for roofline reports).  While enabled, every launch of
  * the library is bracketed by an event pair; ph_profile_read synchronises the
  * handle's streams and returns, for each of the PH_PROF_KINDS kernel kinds in
@@ -254,7 +257,8 @@ ph_status ph_set_overlap(ph_handle* h, int enable);
 
 /* enable = 1: on FP32 handles, 8 < m <= 16 right-hand sides and p_s^d a multiple of 32, phase 1
  * of the explicit coupling runs on the tensor cores (tcgen05.mma kind::tf32 with 3xTF32 split
- * operands, FP32 accumulation in tensor memory); enable = 0 (the default) keeps the CUDA-core
+ * operands; each 32-wide K chunk accumulates in tensor memory and the chunks are summed in
+ * FP32 registers); enable = 0 (the default) keeps the CUDA-core
  * kernel.  The tensor-core result differs from the CUDA-core one by FP32-level rounding (the
  * split drops the low x low product and the tensor cores accumulate in their own order).
  * Errors: PH_ERR_INVALID_ARG for a NULL handle.  Not in the paper: a kernel selection switch. */

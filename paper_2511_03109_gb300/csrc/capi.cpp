@@ -483,6 +483,7 @@ static ph_status instantiate_common(ph_handle* h, const double* theta, int deriv
             return fail(h, PH_ERR_THETA_OUT_OF_BOX, "theta outside the parameter box");
     }
     return guarded(h, [&]() -> ph_status {
+        ph::NvtxRange range(deriv < 0 ? "ph_instantiate" : "ph_instantiate_derivative");
         PH_CUDA(cudaSetDevice(h->device));
         ph::online_instantiate(h, theta, as_stream(stream), deriv);
         h->instantiated = true;
@@ -511,6 +512,7 @@ ph_status ph_matvec(ph_handle* h, const void* X, long ldx, int m, void* Y, long 
     ph_status s = check_mv(h, X, ldx, m, Y, ldy);
     if (s != PH_OK) return s;
     return guarded(h, [&]() -> ph_status {
+        ph::NvtxRange range("ph_matvec");
         PH_CUDA(cudaSetDevice(h->device));
         return ph::online_matvec(h, X, ldx, m, Y, ldy, as_stream(stream));
     });
@@ -529,6 +531,7 @@ ph_status ph_matvec_batched(ph_handle* h, const double* thetas, int n_theta, con
             return fail(h, PH_ERR_THETA_OUT_OF_BOX, "theta outside the parameter box");
     }
     return guarded(h, [&]() -> ph_status {
+        ph::NvtxRange range("ph_matvec_batched");
         PH_CUDA(cudaSetDevice(h->device));
         ph_status st = ph::online_matvec_batched(h, thetas, n_theta, X, ldx, m, Y, ldy, stride_y, deriv,
                                                  as_stream(stream));

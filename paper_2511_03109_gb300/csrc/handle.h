@@ -216,7 +216,15 @@ void refresh_views(ph_handle* h);
 void free_device(ph_handle* h);
 void* dev_alloc(ph_handle* h, size_t bytes);  // throws ph::Error(PH_ERR_OOM) on failure
 void dev_free(ph_handle* h, void* p);
-// Event pair around one launch when profiling is on (no-op otherwise).
+// NVTX range for tools (nsys, ncu --nvtx); a no-op unless a tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char* name);
+    ~NvtxRange();
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+// NVTX range named for the launch's kind, and an event pair around the launch when profiling
+// is on.
 struct ProfScope {
     ph_handle* h;
     int kind;

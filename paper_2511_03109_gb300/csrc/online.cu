@@ -17,6 +17,8 @@
 #include <cstdint>
 #include <type_traits>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 #include "handle.h"
 
@@ -2097,17 +2099,27 @@ static cudaEvent_t prof_event(ph_handle* h) {
     return e;
 }
 
+NvtxRange::NvtxRange(const char* name) { nvtxRangePushA(name); }
+NvtxRange::~NvtxRange() { nvtxRangePop(); }
+
+static const char* const kKindNames[PH_PROF_KINDS] = {"instantiate", "gather",        "near",  "upsweep_leaf",
+                                                      "transfer_up", "coupling",      "transfer_down",
+                                                      "far_h",       "combine",       "coupling_b"};
+
 ProfScope::ProfScope(ph_handle* h_, int kind_, cudaStream_t s_) : h(h_), kind(kind_), s(s_) {
+    nvtxRangePushA((kind >= 0 && kind < PH_PROF_KINDS) ? kKindNames[kind] : "libph");
     if (!h->prof) return;
     b = prof_event(h);
     PH_CUDA(cudaEventRecord(b, s));
 }
 
 ProfScope::~ProfScope() {
-    if (!b) return;
-    cudaEvent_t e = prof_event(h);
-    cudaEventRecord(e, s);
-    h->prof_recs.push_back({kind, b, e});
+    if (b) {
+        cudaEvent_t e = prof_event(h);
+        cudaEventRecord(e, s);
+        h->prof_recs.push_back({kind, b, e});
+    }
+    nvtxRangePop();
 }
 
 ph_status wait_bound_selftest(int device, double* waited) {
