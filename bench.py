@@ -95,6 +95,17 @@ def measured_traffic(kind, info):
     return rec["bytes_per_launch"]
 
 
+def step_binding(step_bytes, step_flops, step_ms, peaks):
+    """max(B_alg / BW, F / P_simt) / T for one step, with the term that binds: the step's
+    algorithmic bytes against the measured copy bandwidth, its flops against the FP32 FMA
+    peak (152 SMs x 128 lanes x 2 flops x max SM clock)."""
+    t = step_ms / 1e3
+    hbm = step_bytes / peaks["hbm_gbs"] / 1e9
+    alu = step_flops / (152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6)
+    return {"term": "hbm" if hbm >= alu else "alu", "fraction": max(hbm, alu) / t,
+            "hbm_seconds": hbm, "alu_seconds": alu}
+
+
 def load_peaks():
     try:
         with open(PEAKS_FILE) as f:
@@ -434,6 +445,7 @@ def run_gpu(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config(), "roofline": roof, "rooflines_by_kernel": others,
         "step_hbm_fraction": step_bytes / (ms / args.steps / 1e3) / 1e9 / peaks["hbm_gbs"],
+        "step_binding": step_binding(step_bytes, info["flops_per_rhs"] * m, ms / args.steps, peaks),
         "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kinds.items()},
         "kernels_ms_alone": {k: v[0] / v[1] for k, v in alone.items()},
         "gpu_launches": gpu_launches, "clocks": clocks,
@@ -472,7 +484,12 @@ def run_gpu(args, rank, world, local_rank):
             out["batched"]["rel_err_vs_oracle"] = float((np.linalg.norm(Yb0[rows] - Yo, axis=0)
                                                          / np.linalg.norm(Yo, axis=0)).max())
         from oracle import kernels
+        t_dense = time.perf_counter()
         exact = kernels.dense_apply(WL.kernel, P, th0, Xh, rows=rows)
+        t_dense = time.perf_counter() - t_dense
+        out["cpu_dense"] = {"value": m / (t_dense / frac), "unit": UNIT, "cores": cores,
+                            "kind": "brute-force K(theta) X (NumPy FP64), the product the method avoids",
+                            "sample": f"the same {len(rows)} rows; time scaled by n / rows"}
         out["rel_err_vs_exact"] = float((np.linalg.norm(Ygpu[rows] - exact, axis=0)
                                          / np.linalg.norm(exact, axis=0)).max())
     print(json.dumps(out), flush=True)
