@@ -255,3 +255,18 @@ def test_adjoint_close_to_matrix_for_symmetric_kernel():
     y = np.random.default_rng(45).standard_normal((500, 2))
     inst = M.instantiate([0.37])
     assert np.all(pmatrix.relative_error(M.matvec(inst, y), M.matvec_transpose(inst, y)) < 1e-8)
+
+
+def test_error_follows_the_truncation_tolerance():
+    """With a fine spatial and theta grid the error against the exact product is set by the
+    TT-SVD tolerance (§2.1): it stays within 2 eps and falls with eps (1e-2 ... 1e-8)."""
+    X = np.random.default_rng(61).standard_normal((500, 1))
+    errs = []
+    for tol in (1e-2, 1e-4, 1e-6, 1e-8):
+        M = _model(500, 2, "gauss", [0.2], [0.9], [24], 10, 2, 1.0, tol, "h2")
+        M.offline()
+        e = max(pmatrix.relative_error(kernels.dense_apply("gauss", M.P, [th], X),
+                                       M.matvec(M.instantiate([th]), X))[0] for th in (0.27, 0.81))
+        assert e <= 2 * tol, (tol, e)
+        errs.append(e)
+    assert all(errs[i + 1] < errs[i] / 30 for i in range(3)), errs
