@@ -36,7 +36,7 @@ WL = inputs.LARGE_3D_MATERN_H2
 METRIC = "online instantiate+H-MVM (theta*RHS)/s and % HBM roofline at rel.err vs FP64 oracle"
 UNIT = "(theta*RHS)/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-ORACLE_SAMPLE_LEAVES = 1
+ORACLE_SAMPLE_LEAVES = 2
 
 
 def workload_config():
@@ -74,7 +74,7 @@ def kernel_of(kind, info):
     """The kernel behind a profiling kind, from the variants the last call reported."""
     var = info.get("kernel_variants", 0)
     if kind == "coupling" and var & 4:
-        return "coupling_a_tc_kernel"
+        return "coupling_a_umma_kernel"
     if kind == "near" and var & 1:
         return "near_tma_kernel"
     if kind == "coupling_b" and var & 2:
@@ -95,15 +95,31 @@ def measured_traffic(kind, info):
     return rec["bytes_per_launch"]
 
 
-def step_binding(step_bytes, step_flops, step_ms, peaks):
+def alu_peak_tflops(peaks, sms):
+    """FP32 FMA peak derived from unit counts: SMs x 128 FP32 lanes x 2 flops x max SM clock."""
+    return sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) / 1e6
+
+
+def step_binding(step_bytes, step_flops, step_ms, peaks, sms):
     """max(B_alg / BW, F / P_simt) / T for one step, with the term that binds: the step's
     algorithmic bytes against the measured copy bandwidth, its flops against the FP32 FMA
-    peak (152 SMs x 128 lanes x 2 flops x max SM clock)."""
+    peak derived from the device's SM count (alu_peak_tflops)."""
     t = step_ms / 1e3
     hbm = step_bytes / peaks["hbm_gbs"] / 1e9
-    alu = step_flops / (152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6)
+    alu = step_flops / (alu_peak_tflops(peaks, sms) * 1e12)
     return {"term": "hbm" if hbm >= alu else "alu", "fraction": max(hbm, alu) / t,
             "hbm_seconds": hbm, "alu_seconds": alu}
+
+
+def tensor_roofline(flops, ms, peaks):
+    """Roofline of a 3xTF32 tensor-core contraction.  `achieved` counts the algorithmic FP32
+    flops; the peak is the dense TF32 rate (measured bf16 x the nominal TF32 / bf16 ratio
+    1.1 / 2.25) divided by 3, since every FP32 product is issued as three TF32 MMAs."""
+    tf32 = peaks["bf16_tflops"] * 1.1 / 2.25
+    ach = flops / (ms / 1e3) / 1e12
+    return {"bound": "tensor", "achieved": ach, "peak": tf32 / 3.0, "unit": "TFLOP/s", "per_launch_flops": flops,
+            "peak_source": "derived", "tf32_issue_frac": 3.0 * ach / tf32,
+            "peak_note": "3xTF32 ceiling: dense TF32 (measured bf16 x nominal 1.1/2.25) / 3 MMAs per FP32 product"}
 
 
 def load_peaks():
@@ -116,30 +132,137 @@ def load_peaks():
 
 
 # --------------------------------------------------------------------- oracle (CPU) baseline
-def oracle_sample(P, X, theta, n_leaves=ORACLE_SAMPLE_LEAVES, seed=7):
-    """Oracle online stage on a bounded sample: the rows of n_leaves target leaves.
+ORACLE_RUNS = 5
 
-    Offline work for the sample (its near blocks and the far blocks of its ancestors) is done
-    first with a spawn-started process pool and is not timed; the timed part is the oracle's
-    instantiate + matvec for the sample rows.  Returns (seconds, rows, Y_rows, cores, leaves,
-    dY_rows) with dY = dK_hat/dtheta X (untimed).
-    """
+
+def oracle_model(P, n_leaves=ORACLE_SAMPLE_LEAVES, seed=7):
+    """The oracle's model of the workload with the offline work of a bounded sample done: the
+    near blocks of `n_leaves` target leaves (a corner leaf and random others) and the far
+    blocks of their ancestors, compressed in a spawn-started pool (offline, not timed)."""
     from oracle import pmatrix
 
     M = pmatrix.ParametricMatrix(P, WL.kernel, WL.theta_lo, WL.theta_hi, WL.degree, WL.p_s,
                                  WL.l_max, WL.eta, WL.tol, rank_cap=WL.rank_cap, fmt=WL.fmt)
     rng = np.random.default_rng(seed)
-    pick = sorted(rng.choice(len(M.leaves), size=n_leaves, replace=False))
-    targets = [M.leaves[i] for i in pick]
+    rest = [int(i) for i in rng.choice(np.arange(1, len(M.leaves)), size=max(0, n_leaves - 1), replace=False)]
+    targets = [M.leaves[i] for i in sorted([0] + rest)]
     with _oracle_pool() as pool:
         M.offline(targets, pool=pool)
-    t0 = time.perf_counter()
-    inst = M.instantiate(theta, targets)
-    Y = M.matvec(inst, X, targets)
-    dt = time.perf_counter() - t0
+    return M, targets
+
+
+def oracle_step_seconds(M, targets, X, theta):
+    """Seconds of one online step (instantiate + H^2 matvec) of the FP64 oracle for the WHOLE
+    matrix, composed from timed samples: every part of the oracle's step (near-block
+    instantiation and product, far-block core instantiation and coupling, leaf sweeps, transfers)
+    is timed on the sample's units and scaled by that part's own count of units in the full
+    matrix (near blocks by stored entries, far blocks, leaves and transfer nodes by number), so
+    no unit is counted more often than the full step holds it.  Returns (seconds, parts)."""
+    from oracle import pmatrix
+
+    near, far = M.blocks_for(targets)
+    anc = {}
+    for c in targets:
+        a = c
+        while a.parent is not None:
+            anc[a.id] = a
+            a = a.parent
+    tnodes = list(anc.values())
+    m = X.shape[1]
+    pd = M.p_s ** M.d
+    rng = np.random.default_rng(5)
+    xh = {c.id: rng.standard_normal((pd, m)) for c in M.nodes}
+    parts = {}
+    t = time.perf_counter
+    vs = M.parametric_vectors(np.atleast_1d(theta))
+    t0 = t()
+    D = {id(b): M.near_instance(b, vs) for b in near}
+    parts["near_instantiate"] = t() - t0
+    t0 = t()
+    H = {id(b): pmatrix.H_matrix(b.cores, M.d, vs) for b in far}
+    parts["far_instantiate"] = t() - t0
+    inst = {"H": H}
+    t0 = t()
+    for c in targets:
+        M.basis(c).T @ X[c.idx]
+    parts["leaf_up"] = t() - t0
+    t0 = t()
+    for c in tnodes:
+        M.transfer(c).T @ xh[c.id]
+    parts["transfer_up"] = t() - t0
+    t0 = t()
+    for b in far:
+        M.coupling(b, inst) @ xh[b.t.id]
+    parts["coupling"] = t() - t0
+    t0 = t()
+    for b in near:
+        D[id(b)] @ X[b.t.idx]
+    parts["near_product"] = t() - t0
+    t0 = t()
+    for c in tnodes:
+        M.transfer(c) @ xh[c.parent.id]
+    parts["transfer_down"] = t() - t0
+    t0 = t()
+    for c in targets:
+        M.basis(c) @ xh[c.id]
+    parts["leaf_down"] = t() - t0
+    ent = lambda bs: sum(b.s.n * b.t.n for b in bs)
+    scale = {"near_instantiate": ent(M.near) / ent(near), "near_product": ent(M.near) / ent(near),
+             "far_instantiate": len(M.far) / max(1, len(far)), "coupling": len(M.far) / max(1, len(far)),
+             "leaf_up": len(M.leaves) / len(targets), "leaf_down": len(M.leaves) / len(targets),
+             "transfer_up": (len(M.nodes) - 1) / max(1, len(tnodes)),
+             "transfer_down": (len(M.nodes) - 1) / max(1, len(tnodes))}
+    total = sum(parts[k] * scale[k] for k in parts)
+    return total, {k: parts[k] * scale[k] for k in parts}
+
+
+def oracle_baseline_runs(M, targets, X, thetas, runs=ORACLE_RUNS):
+    """Warm-up (builds the oracle's cached bases, offline work), then `runs` timed steps:
+    (median seconds, all per-step seconds, median parts, sample wall seconds per step)."""
+    oracle_step_seconds(M, targets, X, thetas[0])
+    totals, parts, walls = [], [], []
+    for k in range(runs):
+        w0 = time.perf_counter()
+        tot, pr = oracle_step_seconds(M, targets, X, thetas[(k + 1) % len(thetas)])
+        walls.append(time.perf_counter() - w0)
+        totals.append(tot)
+        parts.append(pr)
+    med = float(statistics.median(totals))
+    i = totals.index(sorted(totals)[len(totals) // 2])
+    return med, totals, parts[i], float(statistics.median(walls))
+
+
+def _single_thread_child(args):
+    M, targets, X, thetas = args
+    return oracle_baseline_runs(M, targets, X, thetas)
+
+
+def oracle_baseline(M, targets, X, thetas):
+    """The oracle's step time on this host with BLAS on one thread (a spawned process started
+    with OMP/OPENBLAS/MKL_NUM_THREADS=1) and with NumPy's default threads (all cores)."""
+    import multiprocessing as mp
+    nproc = os.cpu_count() or 1
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(1) as pool:
+            single = pool.apply(_single_thread_child, ((M, targets, X, list(thetas)),))
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    multi = oracle_baseline_runs(M, targets, X, thetas)
+    return {"single": single, "all": multi, "nproc": nproc}
+
+
+def oracle_rows(M, targets, X, theta, deriv=None):
+    """The oracle's Y (or dK_hat/dtheta X) on the rows of the sampled target leaves (untimed)."""
     rows = np.sort(np.concatenate([c.idx for c in targets]))
-    Yd = M.matvec(M.instantiate(theta, targets, deriv=0), X, targets)  # untimed: the derivative check
-    return dt, rows, Y[rows], os.cpu_count() or 1, len(M.leaves), Yd[rows]
+    Y = M.matvec(M.instantiate(theta, targets, deriv=deriv), X, targets)
+    return rows, Y[rows]
 
 
 def _oracle_pool():
@@ -340,7 +463,7 @@ def run_gpu(args, rank, world, local_rank):
 
     # many theta, one X (ph_matvec_batched): BATCH_THETAS values per call, the first being the
     # oracle's theta below; a failure here is reported in the line instead of ending the bench
-    b_local, b_err, Yb0 = -1.0, None, None
+    b_local, b_err, Ybs = -1.0, None, None
     tb = [thetas[args.warmup]] + list(inputs.uniform_thetas(WL.theta_lo, WL.theta_hi, BATCH_THETAS - 1,
                                                              WL.theta_seed + 17))
     try:
@@ -353,7 +476,7 @@ def run_gpu(args, rank, world, local_rank):
         ev1.record(stream)
         torch.cuda.synchronize()
         b_local = ev0.elapsed_time(ev1) / BATCH_CALLS
-        Yb0 = Yb[0].double().cpu().numpy().T
+        Ybs = [(t, Yb[t].double().cpu().numpy().T) for t in (0, len(tb) // 2, len(tb) - 1)]
         del Yb
     except Exception as exc:  # noqa: BLE001 - reported in the line, not hidden
         b_err = f"{type(exc).__name__}: {exc}"
@@ -362,7 +485,7 @@ def run_gpu(args, rank, world, local_rank):
     b_fail = sharding.max_over_ranks(1.0 if b_err else 0.0, dist)
     if b_fail > 0 or b_ms <= 0:
         batched = {"error": b_err or "failed on another rank"}
-        Yb0 = None
+        Ybs = None
     else:
         batched = {"what": f"ph_matvec_batched: {len(tb)} theta x {m} RHS per call, one X",
                    "value": world * len(tb) * m / (b_ms / 1e3), "unit": UNIT, "ms_per_call": b_ms,
@@ -377,6 +500,7 @@ def run_gpu(args, rank, world, local_rank):
 
     value = world * args.steps * m / (ms / 1e3)
     peaks, peak_kind = load_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     # roofline pass: the same steps with the far and near paths serialised on one stream, so that
     # each kernel's CUDA-event time is its own (in the timed region they overlap)
     A.set_overlap(False)
@@ -404,25 +528,21 @@ def run_gpu(args, rank, world, local_rank):
         # FP32 CUDA-core flops of the kernel (flop counts of the built structure, per launch)
         per_rhs = {"coupling": info["coupling_a_flops_per_rhs"], "coupling_b": info["coupling_b_flops_per_rhs"]}
         fl = per_rhs.get(dom, info["flops_per_rhs"] - 2.0 * info["near_entries"]) * m
-        if kernel_of(dom, info) == "coupling_a_tc_kernel":
-            tf32_peak = peaks["bf16_tflops"] * 1.1 / 2.25  # burst: the kernel runs for about a millisecond
-            roof = {"bound": "tensor", "achieved": fl / (avg_ms / 1e3) / 1e12, "peak": tf32_peak,
-                    "unit": "TFLOP/s", "per_launch_flops": fl,
-                    "peak_note": "dense TF32 = measured bf16 x nominal TF32/bf16 ratio 1.1/2.25; the 3xTF32 "
-                                 "split issues three MMAs per product, so algorithmic flops top out at peak/3"}
+        if kernel_of(dom, info) == "coupling_a_umma_kernel":
+            roof = tensor_roofline(fl, avg_ms, peaks)
         else:
-            alu_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) / 1e6
+            alu_peak = alu_peak_tflops(peaks, sms)
             roof = {"bound": "alu", "achieved": fl / (avg_ms / 1e3) / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
-                    "per_launch_flops": fl,
-                    "peak_note": "FP32 FMA lanes: 152 SMs x 128 x 2 flops x max SM clock"}
+                    "per_launch_flops": fl, "peak_source": "derived",
+                    "peak_note": f"FP32 FMA lanes: {sms} SMs (device count) x 128 x 2 flops x max SM clock"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["kernel"] = kernel_of(dom, info)
-    roof["peak_source"] = peak_kind
+    roof.setdefault("peak_source", peak_kind)
     roof["traffic"] = measured_traffic(dom, info)
     roof["timing"] = "CUDA events around each launch, far and near paths serialised (roofline pass)"
     # the three large kernels against their own bounds, same pass
     others = {}
-    alu_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) / 1e6
+    alu_peak = alu_peak_tflops(peaks, sms)
     if "near" in alone:
         t = alone["near"][0] / alone["near"][1] / 1e3
         b = info["near_bytes"] + 2.0 * n * m * sc + info["near_rank_sum"] * sc
@@ -433,9 +553,15 @@ def run_gpu(args, rank, world, local_rank):
         if kind in alone and info[key] > 0:
             t = alone[kind][0] / alone[kind][1] / 1e3
             f = info[key] * m
-            others[kind] = {"kernel": kernel_of(kind, info), "bound": "alu", "ms": t * 1e3,
-                            "achieved": f / t / 1e12, "unit": "TFLOP/s", "frac": f / t / 1e12 / alu_peak,
-                            "traffic": measured_traffic(kind, info)}
+            if kernel_of(kind, info) == "coupling_a_umma_kernel":
+                rt = tensor_roofline(f, t * 1e3, peaks)
+                others[kind] = {"kernel": kernel_of(kind, info), "bound": "tensor", "ms": t * 1e3,
+                                "achieved": rt["achieved"], "unit": "TFLOP/s", "frac": rt["achieved"] / rt["peak"],
+                                "tf32_issue_frac": rt["tf32_issue_frac"], "traffic": measured_traffic(kind, info)}
+            else:
+                others[kind] = {"kernel": kernel_of(kind, info), "bound": "alu", "ms": t * 1e3,
+                                "achieved": f / t / 1e12, "unit": "TFLOP/s", "frac": f / t / 1e12 / alu_peak,
+                                "traffic": measured_traffic(kind, info)}
     gpu_launches = int(sum(v[1] for v in prof.values()))
     # whole-step bytes over the step time, for context
     step_bytes = info["alg_bytes_per_call"] + 2.0 * n * m * sc
@@ -445,7 +571,7 @@ def run_gpu(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config(), "roofline": roof, "rooflines_by_kernel": others,
         "step_hbm_fraction": step_bytes / (ms / args.steps / 1e3) / 1e9 / peaks["hbm_gbs"],
-        "step_binding": step_binding(step_bytes, info["flops_per_rhs"] * m, ms / args.steps, peaks),
+        "step_binding": step_binding(step_bytes, info["flops_per_rhs"] * m, ms / args.steps, peaks, sms),
         "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kinds.items()},
         "kernels_ms_alone": {k: v[0] / v[1] for k, v in alone.items()},
         "gpu_launches": gpu_launches, "clocks": clocks,
@@ -465,33 +591,45 @@ def run_gpu(args, rank, world, local_rank):
         A.matvec_ptr(X.data_ptr(), n, m, Y.data_ptr(), n, sp)
         torch.cuda.synchronize()
         Ygpu = Y.double().cpu().numpy().T
-        log("oracle sample")
         A.instantiate_derivative(th0, 0, sp)
         A.matvec_ptr(X.data_ptr(), n, m, Y.data_ptr(), n, sp)
         torch.cuda.synchronize()
         Ygpu_d = Y.double().cpu().numpy().T
-        dt, rows, Yo, cores, nleaves, Yod = oracle_sample(P, Xh, th0)
-        log(f"oracle sample timed part {dt:.2f} s")
-        frac = len(rows) / n
-        out["cpu_baseline"] = {"value": m / (dt / frac), "unit": UNIT, "cores": cores, "kind": "oracle",
-                               "sample": f"rows of {ORACLE_SAMPLE_LEAVES} of {nleaves} target leaves "
-                                         f"({len(rows)} rows, 16 RHS, one theta); time scaled by n / rows"}
-        err = np.linalg.norm(Ygpu[rows] - Yo, axis=0) / np.linalg.norm(Yo, axis=0)
-        out["rel_err_vs_oracle"] = float(err.max())
-        out["derivative"]["rel_err_vs_oracle"] = float((np.linalg.norm(Ygpu_d[rows] - Yod, axis=0)
-                                                        / np.linalg.norm(Yod, axis=0)).max())
-        if Yb0 is not None:
-            out["batched"]["rel_err_vs_oracle"] = float((np.linalg.norm(Yb0[rows] - Yo, axis=0)
-                                                         / np.linalg.norm(Yo, axis=0)).max())
+        log("oracle sample: offline work of the sample")
+        M, targets = oracle_model(P)
+        rows, Yo = oracle_rows(M, targets, Xh, th0)
+        _, Yod = oracle_rows(M, targets, Xh, th0, deriv=0)
+        rel = lambda ref, got: float((np.linalg.norm(got - ref, axis=0) / np.linalg.norm(ref, axis=0)).max())
+        out["rel_err_vs_oracle"] = rel(Yo, Ygpu[rows])
+        out["derivative"]["rel_err_vs_oracle"] = rel(Yod, Ygpu_d[rows])
+        out["oracle_rows"] = {"leaves": [int(c.id) for c in targets], "rows": int(len(rows))}
+        if Ybs is not None:
+            errs = []
+            for t, Yt in Ybs:
+                _, Yot = oracle_rows(M, targets, Xh, tb[t])
+                errs.append(rel(Yot, Yt[rows]))
+            out["batched"]["rel_err_vs_oracle"] = max(errs)
+            out["batched"]["thetas_checked"] = [int(t) for t, _ in Ybs]
+        log("oracle step timing (single thread and all cores)")
+        base = oracle_baseline(M, targets, Xh, thetas[args.warmup:args.warmup + ORACLE_RUNS + 1])
+        s1, s_all, parts, wall = base["single"][0], base["all"][0], base["all"][2], base["all"][3]
+        sample = (f"one full online step (instantiate + H^2 matvec, {m} RHS, every block) composed from timed "
+                  f"parts of {len(targets)} of {len(M.leaves)} target leaves (their near blocks, the far blocks "
+                  f"of their ancestors, their sweeps), each part scaled by its own unit count in the full matrix; "
+                  f"median of {ORACLE_RUNS} warm runs")
+        out["cpu_baseline"] = {"value": m / s_all, "unit": UNIT, "cores": base["nproc"], "kind": "oracle",
+                               "sample": sample, "seconds_per_step": s_all,
+                               "single_thread": {"value": m / s1, "cores": 1, "seconds_per_step": s1},
+                               "parts_seconds": parts, "sample_wall_seconds_per_step": wall}
         from oracle import kernels
         t_dense = time.perf_counter()
         exact = kernels.dense_apply(WL.kernel, P, th0, Xh, rows=rows)
         t_dense = time.perf_counter() - t_dense
-        out["cpu_dense"] = {"value": m / (t_dense / frac), "unit": UNIT, "cores": cores,
+        frac = len(rows) / n
+        out["cpu_dense"] = {"value": m / (t_dense / frac), "unit": UNIT, "cores": base["nproc"],
                             "kind": "brute-force K(theta) X (NumPy FP64), the product the method avoids",
-                            "sample": f"the same {len(rows)} rows; time scaled by n / rows"}
-        out["rel_err_vs_exact"] = float((np.linalg.norm(Ygpu[rows] - exact, axis=0)
-                                         / np.linalg.norm(exact, axis=0)).max())
+                            "sample": f"the same {len(rows)} rows; time scaled by n / rows (every row costs the same)"}
+        out["rel_err_vs_exact"] = rel(exact, Ygpu[rows])
     print(json.dumps(out), flush=True)
     if dist:
         dist.barrier()
@@ -506,47 +644,38 @@ BATCH_CALLS = 3
 
 
 def run_reference(args, rank, world):
+    """The FP64 oracle on this host's cores: each step is one full online step composed from
+    timed parts of a bounded sample (oracle_step_seconds), all cores (NumPy's default threads)."""
     if rank != 0:
         return
     P = WL.points()
     Xh = WL.rhs()
-    m, n = WL.m, WL.n
+    m = WL.m
     thetas = inputs.uniform_thetas(WL.theta_lo, WL.theta_hi, max(30, args.warmup + args.steps), WL.theta_seed)
-    from oracle import pmatrix
-
-    M = pmatrix.ParametricMatrix(P, WL.kernel, WL.theta_lo, WL.theta_hi, WL.degree, WL.p_s, WL.l_max,
-                                 WL.eta, WL.tol, rank_cap=WL.rank_cap, fmt=WL.fmt)
-    rng = np.random.default_rng(7)
-    targets = [M.leaves[i] for i in sorted(rng.choice(len(M.leaves), size=ORACLE_SAMPLE_LEAVES, replace=False))]
-    with _oracle_pool() as pool:
-        M.offline(targets, pool=pool)
-    rows = np.concatenate([c.idx for c in targets])
-    frac = len(rows) / n
-
-    def step(th):
-        M.matvec(M.instantiate(th, targets), Xh, targets)
-
-    for k in range(min(args.warmup, 3)):
-        step(thetas[k])
-    # each step is about a second of host work: stop after REF_TIME_LIMIT s so that any
-    # --steps finishes within a few minutes, and report the steps actually timed
+    M, targets = oracle_model(P)
+    for k in range(min(max(args.warmup, 1), 3)):
+        oracle_step_seconds(M, targets, Xh, thetas[k])
+    # every composed step takes about a second of host work: stop after REF_TIME_LIMIT s so that
+    # any --steps finishes within a few minutes, and report the steps actually timed
     t0 = time.perf_counter()
-    done = 0
+    secs = []
     for k in range(args.steps):
-        step(thetas[(args.warmup + k) % len(thetas)])
-        done += 1
+        secs.append(oracle_step_seconds(M, targets, Xh, thetas[(args.warmup + k) % len(thetas)])[0])
         if time.perf_counter() - t0 > REF_TIME_LIMIT:
             break
-    dt = (time.perf_counter() - t0) / frac
-    value = done * m / dt
+    wall = (time.perf_counter() - t0) / len(secs)
+    step_s = float(statistics.median(secs))
+    value = m / step_s
     cores = os.cpu_count() or 1
+    sample = (f"one full online step (instantiate + H^2 matvec, {m} RHS, every block) composed from timed parts "
+              f"of {len(targets)} of {len(M.leaves)} target leaves, each part scaled by its own unit count in the "
+              f"full matrix; median over the steps timed")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-           "steps": args.steps, "steps_timed": done, "warmup": args.warmup, "ms_per_step": dt / done * 1e3,
+           "steps": args.steps, "steps_timed": len(secs), "warmup": args.warmup, "ms_per_step": step_s * 1e3,
+           "sample_wall_ms_per_step": wall * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "config": workload_config(),
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                            "sample": f"rows of {ORACLE_SAMPLE_LEAVES} of {len(M.leaves)} target leaves per step "
-                                      f"({len(rows)} rows, 16 RHS); time scaled by n / rows"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 

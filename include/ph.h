@@ -39,8 +39,12 @@ typedef enum {
     PH_ERR_OOM = 4,               /* host or device allocation failed */
     PH_ERR_CUDA = 5,              /* a CUDA, cuBLAS or cuSOLVER call failed (no device, launch error ...) */
     PH_ERR_NONFINITE = 6,         /* non-finite theta, or non-finite X when check_finite is set */
-    PH_ERR_TIMEOUT = 7,           /* a bounded device-side wait ran out (reported by calls that
-                                     synchronise, i.e. ph_matvec with check_finite set) */
+    PH_ERR_TIMEOUT = 7,           /* a bounded device-side wait ran out: the result of the call it
+                                     ran out in is invalid.  Reported by that call when it
+                                     synchronises (check_finite set), else by ph_check, or by the
+                                     first ph_instantiate / ph_matvec* call on the handle made
+                                     after the stream passed that call, which then does no work
+                                     (call it again to proceed) */
     PH_ERR_IO = 8,                /* ph_save / ph_load file error or bad file */
     PH_ERR_UNSUPPORTED = 9        /* option combination not implemented */
 } ph_status;
@@ -183,15 +187,18 @@ ph_status ph_matvec_host(ph_handle* h, const void* X, long ldx, int m, void* Y, 
                          void* stream);
 
 /* ph_matvec for callers that cannot allocate device memory.  The paper has no
- * counterpart; this is a service of the library.  Some callers may not call
- * cudaMalloc at the time they apply the matrix: code that runs while a CUDA graph
- * is being captured, processes held to a fixed device-memory budget, or host
- * applications that own every device allocation themselves.  ph_matvec
- * allocates its per-call workspace on first use; this variant allocates nothing
- * and calls no allocating library routine.  Its workspace lives in one
- * file-scope device array of 16 MiB that every GPU loading the library holds
- * until the process exits.
- *   Arguments, layout and result are those of ph_matvec.
+ * counterpart; this is a service of the library.  ph_matvec allocates its per-call
+ * workspace with cudaMalloc the first time it meets a problem size, and cudaMalloc
+ * may synchronise the device and can fail when memory is tight.  Some callers cannot
+ * allow that when they apply the matrix: processes held to a fixed device-memory
+ * budget that is fully committed after set-up, host applications that own every
+ * device allocation through their own allocator, and latency-bound loops that must
+ * not stall on an allocation.  This variant allocates nothing and calls no allocating
+ * library routine (no cudaMalloc, no cudaFree, nothing from PyTorch).  Its workspace
+ * lives in one file-scope device array of 16 MiB that every GPU loading the library
+ * holds until the process exits.
+ *   Arguments, layout, result and errors are those of ph_matvec; with check_finite set
+ *     the call reads a flag back and synchronises the stream, as ph_matvec does.
  *   Sizes: the workspace needed is about 4 (float) or 8 (double) bytes times
  *     m_pad * (n + near work items * largest leaf + 2 * tree nodes * p_s^d
  *     + far blocks * largest r_d) (H^2) or m_pad * (n + items * largest leaf +
@@ -208,11 +215,36 @@ ph_status ph_matvec_host(ph_handle* h, const void* X, long ldx, int m, void* Y, 
 ph_status ph_matvec_noalloc(ph_handle* h, const void* X, long ldx, int m, void* Y, long ldy,
                             void* stream);
 
+/* Waits for the handle's work on `stream` (and on its internal far-field stream) and reports
+ * PH_ERR_TIMEOUT if a bounded device-side wait of an earlier call ran out since the last
+ * report (that call's result is invalid), else PH_OK; PH_ERR_CUDA if the stream reports an
+ * error.  Synchronous.  Not in the paper: a status query of the library. */
+ph_status ph_check(ph_handle* h, void* stream);
+
+/* Test hook (the paper has no counterpart): runs, on `stream`, one CTA that waits on an mbarrier
+ * nothing arrives on, with the bounded wait of the production kernels (about one second), and
+ * counts the expiry in the handle's device flag exactly as a production kernel whose wait ran
+ * out does.  The call itself returns PH_OK (asynchronous).  ph_check on the handle then reports
+ * PH_ERR_TIMEOUT once; so does the first ph_instantiate / ph_matvec* call made after the stream
+ * has passed the wait (after a synchronisation).  No kernel is faulted or hung. */
+ph_status ph_selftest_timeout(ph_handle* h, void* stream);
+
+/* Test hook (the paper has no counterpart): after `after` more successful device allocations
+ * of the library in this process, every further one fails as if cudaMalloc had failed, so
+ * that the caller sees PH_ERR_OOM; after < 0 switches the injection off.  A handle whose
+ * allocation failed in ph_matvec stays valid (destroy it, or switch the injection off and
+ * call again).  Affects every handle of the process; always returns PH_OK. */
+ph_status ph_inject_alloc_failure(long after);
+
 /* Fill *info with sizes and counts of a built handle. */
 ph_status ph_get_info(const ph_handle* h, ph_info* info);
 
 /* Serialise a handle (tree, block lists, all stored cores) to a file / rebuild a
- * handle from such a file on the device recorded in it (or opts-less default 0). */
+ * handle from such a file on `device`.  ph_load reads and checks the whole file on the host
+ * before it touches the device: every length against the bytes left in the file, and every
+ * stored offset, index and size against the table or arena it points into; a file that
+ * fails any check is refused with PH_ERR_IO (message in ph_last_error(NULL)), a missing
+ * device gives PH_ERR_CUDA. */
 ph_status ph_save(const ph_handle* h, const char* path);
 ph_status ph_load(const char* path, int device, ph_handle** out);
 
@@ -257,9 +289,10 @@ ph_status ph_set_overlap(ph_handle* h, int enable);
 
 /* enable = 1: on FP32 handles, 8 < m <= 16 right-hand sides and p_s^d a multiple of 32, phase 1
  * of the explicit coupling runs on the tensor cores (tcgen05.mma kind::tf32 with 3xTF32 split
- * operands; each 32-wide K chunk accumulates in tensor memory and the chunks are summed in
- * FP32 registers); enable = 0 (the default) keeps the CUDA-core
- * kernel.  The tensor-core result differs from the CUDA-core one by FP32-level rounding (the
+ * operands; every two 32-wide K chunks accumulate in tensor memory and are summed in FP32
+ * registers); enable = 0 (the default) selects the CUDA-core kernel, which is faster at the
+ * ranks of the 3-D Matern workloads (r' ~ 27..64: each 3xTF32 chunk takes 12 small MMAs whose
+ * issue cost exceeds their arithmetic).  The tensor-core result differs from the CUDA-core one by FP32-level rounding (the
  * split drops the low x low product and the tensor cores accumulate in their own order).
  * Errors: PH_ERR_INVALID_ARG for a NULL handle.  Not in the paper: a kernel selection switch. */
 ph_status ph_set_tensor_cores(ph_handle* h, int enable);

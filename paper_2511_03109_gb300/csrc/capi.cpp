@@ -19,32 +19,35 @@ namespace {
 
 thread_local std::string g_last_error;
 
-ph_status fail(ph_handle* h, ph_status s, const std::string& msg) {
-    g_last_error = msg;
-    if (h) h->last_error = msg;
-    return s;
-}
-
-template <typename F>
-ph_status guarded(ph_handle* h, F&& f) {
-    try {
-        return f();
-    } catch (const ph::Error& e) {
-        return fail(h, e.status, e.what());
-    } catch (const std::bad_alloc&) {
-        return fail(h, PH_ERR_OOM, "host allocation failed");
-    } catch (const std::invalid_argument& e) {
-        return fail(h, PH_ERR_INVALID_ARG, e.what());
-    } catch (const std::exception& e) {
-        return fail(h, PH_ERR_CUDA, e.what());
-    }
-}
+using ph::fail;
+using ph::guarded;
 
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 }  // namespace
 
 namespace ph {
+
+ph_status fail(ph_handle* h, ph_status s, const std::string& msg) {
+    g_last_error = msg;
+    if (h) h->last_error = msg;
+    return s;
+}
+
+void post_timeout_flag(ph_handle* h, cudaStream_t stream) {
+    if (h->host_flags && h->d_flags)
+        PH_CUDA(cudaMemcpyAsync(h->host_flags, h->d_flags + 1, sizeof(int), cudaMemcpyDeviceToHost, stream));
+}
+
+ph_status take_timeout(ph_handle* h) {
+    if (!h->host_flags) return PH_OK;
+    const int seen = *(volatile int*)h->host_flags;
+    if (seen > h->seen_timeouts) {
+        h->seen_timeouts = seen;
+        return fail(h, PH_ERR_TIMEOUT, "a bounded device-side wait of an earlier call ran out (its result is invalid)");
+    }
+    return PH_OK;
+}
 
 void dev_free(ph_handle* h, void* p) {
     if (!p) return;
@@ -139,7 +142,6 @@ static void fill_view(ph_handle* h, DevView<T>& v, const std::vector<long>& io, 
     v.E = (const T*)h->d_E;
     v.mcap = h->mcap;
     v.Xc = (T*)h->d_Xc;
-    v.Ynear = (T*)h->d_Ynear;
     v.yfar = (T*)h->d_yfar;
     v.xhat = (T*)h->d_xhat;
     v.yhat = (T*)h->d_yhat;
@@ -343,7 +345,15 @@ void refresh_views(ph_handle* h) {
     h->d_dbl = (double*)dev_alloc(h, dbl.size() * sizeof(double));
     PH_CUDA(cudaMemcpy(h->d_dbl, dbl.data(), dbl.size() * sizeof(double), cudaMemcpyHostToDevice));
     if (!h->d_v64) h->d_v64 = (double*)dev_alloc(h, kMaxDim * kMaxPTheta * sizeof(double));
-    if (!h->d_flags) h->d_flags = (int*)dev_alloc(h, 4 * sizeof(int));
+    if (!h->d_flags) {
+        h->d_flags = (int*)dev_alloc(h, 4 * sizeof(int));
+        PH_CUDA(cudaMemset(h->d_flags, 0, 4 * sizeof(int)));
+    }
+    if (!h->host_flags) {
+        PH_CUDA(cudaHostAlloc((void**)&h->host_flags, sizeof(int), cudaHostAllocDefault));
+        *h->host_flags = 0;
+        h->seen_timeouts = 0;
+    }
     h->d_level_nodes = h->d_int + io[19];
     fill_view<float>(h, h->vf, io, lo);
     fill_view<double>(h, h->vd, io, lo);
@@ -358,10 +368,13 @@ void ensure_workspace(ph_handle* h, int m) {
     if (S <= h->mcap) return;
     const Plan& plan = h->plan;
     const size_t sc = h->scalar;
-    for (void* p : {h->d_Xc, h->d_Ynear, h->d_yfar, h->d_xhat, h->d_yhat, h->d_partials, h->d_zbuf}) dev_free(h, p);
-    h->d_zbuf = nullptr;
+    for (void* p : {h->d_Xc, h->d_yfar, h->d_xhat, h->d_yhat, h->d_partials, h->d_zbuf}) dev_free(h, p);
+    // nothing may point at the freed buffers should an allocation below fail
+    h->d_Xc = h->d_yfar = h->d_xhat = h->d_yhat = h->d_partials = h->d_zbuf = nullptr;
+    h->mcap = 0;
+    fill_view<float>(h, h->vf, h->view_io, h->view_lo);
+    fill_view<double>(h, h->vd, h->view_io, h->view_lo);
     h->d_Xc = dev_alloc(h, (size_t)plan.n * S * sc);
-    h->d_Ynear = dev_alloc(h, (size_t)plan.n * S * sc);
     h->d_partials = dev_alloc(h, std::max<size_t>(1, h->item_first.size()) * h->max_leaf * S * sc);
     h->d_yfar = nullptr;
     h->d_xhat = h->d_yhat = nullptr;
@@ -458,6 +471,11 @@ ph_status ph_offline_build(const double* points, long n, ph_kernel kernel, const
             throw ph::Error(PH_ERR_CUDA, "no CUDA device " + std::to_string(o->device));
         }
         ph::offline_build(h, points, n);
+        const size_t sc = h->scalar;
+        ph::validate_handle(*h, {(size_t)h->near_elems * sc, (size_t)h->near_theta_elems * 8,
+                                 (size_t)h->far_elems * sc, (size_t)h->far_theta_elems * 8, (size_t)h->st_elems * sc,
+                                 (size_t)n * o->d * o->p_s * sc, (size_t)2 * o->p_s * o->p_s * sc,
+                                 (size_t)h->lr_elems * sc, (size_t)h->tc_elems * 4});
         ph::refresh_views(h);
         PH_CUDA(cudaDeviceSynchronize());
         return PH_OK;
@@ -482,6 +500,7 @@ static ph_status instantiate_common(ph_handle* h, const double* theta, int deriv
         if (theta[k] < h->opts.theta_lo[k] || theta[k] > h->opts.theta_hi[k])
             return fail(h, PH_ERR_THETA_OUT_OF_BOX, "theta outside the parameter box");
     }
+    if (ph::take_timeout(h) != PH_OK) return PH_ERR_TIMEOUT;
     return guarded(h, [&]() -> ph_status {
         ph::NvtxRange range(deriv < 0 ? "ph_instantiate" : "ph_instantiate_derivative");
         PH_CUDA(cudaSetDevice(h->device));
@@ -505,7 +524,7 @@ static ph_status check_mv(ph_handle* h, const void* X, long ldx, int m, void* Y,
     if (!X || !Y || m < 1 || m > 1024 || ldx < h->plan.n || ldy < h->plan.n)
         return fail(h, PH_ERR_INVALID_ARG, "ph_matvec: invalid argument");
     if (!h->instantiated) return fail(h, PH_ERR_NOT_INSTANTIATED, "ph_matvec before ph_instantiate");
-    return PH_OK;
+    return ph::take_timeout(h);
 }
 
 ph_status ph_matvec(ph_handle* h, const void* X, long ldx, int m, void* Y, long ldy, void* stream) {
@@ -525,6 +544,7 @@ ph_status ph_matvec_batched(ph_handle* h, const double* thetas, int n_theta, con
         ldy < h->plan.n || stride_y < ldy * (long)m || deriv < -1 || deriv >= h->opts.dtheta)
         return fail(h, PH_ERR_INVALID_ARG, "ph_matvec_batched: invalid argument");
     if (h->opts.dtheta != 1) return fail(h, PH_ERR_UNSUPPORTED, "ph_matvec_batched: d_theta must be 1");
+    if (ph::take_timeout(h) != PH_OK) return PH_ERR_TIMEOUT;
     for (int t = 0; t < n_theta; ++t) {
         if (!std::isfinite(thetas[t])) return fail(h, PH_ERR_NONFINITE, "theta is not finite");
         if (thetas[t] < h->opts.theta_lo[0] || thetas[t] > h->opts.theta_hi[0])
@@ -562,6 +582,31 @@ ph_status ph_matvec_host(ph_handle* h, const void* X, long ldx, int m, void* Y, 
         PH_CUDA(cudaStreamSynchronize(st));
         return PH_OK;
     });
+}
+
+ph_status ph_check(ph_handle* h, void* stream) {
+    if (!h) return fail(nullptr, PH_ERR_INVALID_ARG, "ph_check: NULL handle");
+    ph_status st = guarded(h, [&]() -> ph_status {
+        PH_CUDA(cudaSetDevice(h->device));
+        PH_CUDA(cudaStreamSynchronize(as_stream(stream)));
+        if (h->side) PH_CUDA(cudaStreamSynchronize(h->side));
+        return PH_OK;
+    });
+    if (st != PH_OK) return st;
+    return ph::take_timeout(h);
+}
+
+ph_status ph_selftest_timeout(ph_handle* h, void* stream) {
+    if (!h) return fail(nullptr, PH_ERR_INVALID_ARG, "ph_selftest_timeout: NULL handle");
+    return guarded(h, [&]() -> ph_status {
+        PH_CUDA(cudaSetDevice(h->device));
+        return ph::handle_timeout_selftest(h, as_stream(stream));
+    });
+}
+
+ph_status ph_inject_alloc_failure(long after) {
+    ph::set_alloc_failure(after);
+    return PH_OK;
 }
 
 ph_status ph_get_info(const ph_handle* h, ph_info* info) {

@@ -4,9 +4,12 @@
 
 #include <cuda_runtime.h>
 
+#include <new>
+#include <stdexcept>
 #include <string>
 #include <vector>
 
+#include "common.cuh"
 #include "ph_internal.h"
 
 // Device pointers of the online stage for compute type T (float or double).
@@ -93,11 +96,10 @@ struct DevView {
     // workspace
     int mcap;
     T* Xc;                      // n x mcap, cluster order, row-major
-    T* Ynear;                   // n x mcap
     T* yfar;                    // n_far_levels x n x mcap (H format)
     T* xhat;                    // n_nodes x PD x mcap
     T* yhat;
-    int* flags;                 // [0]: non-finite input count
+    int* flags;                 // [0]: non-finite input count, [1]: bounded device waits that ran out
 };
 
 struct DeviceBuffer {
@@ -160,8 +162,6 @@ struct ph_handle {
     size_t ynodes_bytes = 0;
     double* d_thetas = nullptr;                 // the theta values of a batched call
     size_t thetas_cap = 0;
-    std::vector<double> host_thetas;            // source of their copy (kept until the next call)
-    void* d_Ynear = nullptr;
     void* d_yfar = nullptr;
     void* d_xhat = nullptr;
     void* d_yhat = nullptr;
@@ -181,6 +181,11 @@ struct ph_handle {
     // streams
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_thetas = nullptr;            // after the last copy out of host_thetas_pinned
+    int* host_flags = nullptr;                  // pinned copy of flags[1], written at the end of each matvec
+    int seen_timeouts = 0;                      // flags[1] already reported as PH_ERR_TIMEOUT
+    double* host_thetas_pinned = nullptr;       // pinned source of a batched call's theta copy
+    size_t host_thetas_cap = 0;
     bool instantiated = false;
     bool overlap = true;                        // far path on the side stream (ph_set_overlap)
     bool use_bulk = true;                       // bulk-copy pipelined near field and phase 2 when they apply
@@ -206,6 +211,7 @@ ph_status online_instantiate(ph_handle* h, const double* theta, cudaStream_t str
 ph_status online_matvec_batched(ph_handle* h, const double* thetas, int n_theta, const void* X, long ldx, int m,
                                 void* Y, long ldy, long stride_y, int deriv, cudaStream_t stream);
 ph_status wait_bound_selftest(int device, double* waited);  // bounded mbarrier wait on a barrier nothing completes
+ph_status handle_timeout_selftest(ph_handle* h, cudaStream_t stream);  // the same wait, counted in h's flags
 ph_status online_matvec(ph_handle* h, const void* X, long ldx, int m, void* Y, long ldy,
                         cudaStream_t stream);
 void ensure_workspace(ph_handle* h, int m);
@@ -215,6 +221,35 @@ ph_status online_matvec_view(ph_handle* h, DevView<float>& vf, DevView<double>& 
 void refresh_views(ph_handle* h);
 void free_device(ph_handle* h);
 void* dev_alloc(ph_handle* h, size_t bytes);  // throws ph::Error(PH_ERR_OOM) on failure
+// Test hook behind ph_inject_alloc_failure: after `after` more successful dev_alloc calls in
+// this process every further one fails with PH_ERR_OOM (after < 0 switches it off).
+void set_alloc_failure(long after);
+// Stream-ordered copy of the device wait-timeout counter into pinned host memory (no sync).
+void post_timeout_flag(ph_handle* h, cudaStream_t stream);
+// PH_ERR_TIMEOUT (once) when a bounded device wait of an earlier call ran out, else PH_OK.
+ph_status take_timeout(ph_handle* h);
+// Checks every offset, index and size the kernels rely on (ph_load refuses a file that fails,
+// ph_offline_build checks what it built); throws ph::Error(PH_ERR_IO) with the first violation.
+void validate_handle(const ph_handle& h, const std::vector<size_t>& arena_bytes);
+// Records msg as the last error (of h, and of the thread) and returns s.
+ph_status fail(ph_handle* h, ph_status s, const std::string& msg);
+// Runs f and maps any exception to a status recorded by fail().
+template <typename F>
+ph_status guarded(ph_handle* h, F&& f) {
+    try {
+        return f();
+    } catch (const Error& e) {
+        return fail(h, e.status, e.what());
+    } catch (const std::bad_alloc&) {
+        return fail(h, PH_ERR_OOM, "host allocation failed");
+    } catch (const std::invalid_argument& e) {
+        return fail(h, PH_ERR_INVALID_ARG, e.what());
+    } catch (const std::exception& e) {
+        return fail(h, PH_ERR_CUDA, e.what());
+    } catch (...) {
+        return fail(h, PH_ERR_CUDA, "unknown exception");
+    }
+}
 void dev_free(ph_handle* h, void* p);
 // NVTX range for tools (nsys, ncu --nvtx); a no-op unless a tool is attached.
 struct NvtxRange {

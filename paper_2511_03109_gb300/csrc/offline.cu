@@ -22,6 +22,7 @@
 #include <cusolverDn.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdint>
@@ -275,6 +276,10 @@ struct TTEngine {
     int* info = nullptr;
     size_t capT = 0, capN = 0, capWork = 0;
     ph_handle* h = nullptr;
+    ~TTEngine() {
+        if (blas) cublasDestroy(blas);
+        if (solver) cusolverDnDestroy(solver);
+    }
 
     void reserve(size_t total, size_t maxn) {
         if (total > capT) {
@@ -403,8 +408,19 @@ V* upload_vec(ph_handle* h, const std::vector<V>& v) {
 
 }  // namespace
 
+namespace {
+std::atomic<long> g_alloc_budget{-1};  // successful allocations left before injected failures (< 0: off)
+}  // namespace
+
+void set_alloc_failure(long after) { g_alloc_budget.store(after < 0 ? -1 : after); }
+
 void* dev_alloc(ph_handle* h, size_t bytes) {
     void* p = nullptr;
+    long budget = g_alloc_budget.load();
+    while (budget >= 0) {
+        if (budget == 0) throw Error(PH_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: injected failure");
+        if (g_alloc_budget.compare_exchange_weak(budget, budget - 1)) break;
+    }
     // 64 bytes of slack: bulk copies round the end of a range up to 16 bytes
     cudaError_t e = cudaMalloc(&p, bytes + 64);
     if (e != cudaSuccess) {
@@ -420,9 +436,19 @@ void free_device(ph_handle* h) {
     for (auto& b : h->buffers)
         if (b.ptr) cudaFree(b.ptr);
     h->buffers.clear();
+    if (h->host_flags) cudaFreeHost(h->host_flags);
+    if (h->host_thetas_pinned) cudaFreeHost(h->host_thetas_pinned);
+    h->host_flags = nullptr;
+    h->host_thetas_pinned = nullptr;
+    h->host_thetas_cap = 0;
     if (h->side) cudaStreamDestroy(h->side);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->ev_thetas) {
+        cudaEventSynchronize(h->ev_thetas);
+        cudaEventDestroy(h->ev_thetas);
+    }
+    h->ev_thetas = nullptr;
     h->side = nullptr;
     h->ev_fork = h->ev_join = nullptr;
 }
@@ -509,10 +535,18 @@ ph_status offline_build(ph_handle* h, const double* points, long n) {
         near_tsqr_kernel<<<nn, 256, smem>>>(nbld, d_R);
         PH_LAUNCH("near_tsqr_kernel");
         // batched Jacobi SVD of all P x P factors: R_b = U S V^T, S descending
-        cusolverDnHandle_t sol;
-        PH_SOLVER(cusolverDnCreate(&sol));
-        gesvdjInfo_t params;
-        PH_SOLVER(cusolverDnCreateGesvdjInfo(&params));
+        struct Solver {  // released on every exit path
+            cusolverDnHandle_t sol = nullptr;
+            gesvdjInfo_t params = nullptr;
+            ~Solver() {
+                if (params) cusolverDnDestroyGesvdjInfo(params);
+                if (sol) cusolverDnDestroy(sol);
+            }
+        } svd;
+        PH_SOLVER(cusolverDnCreate(&svd.sol));
+        PH_SOLVER(cusolverDnCreateGesvdjInfo(&svd.params));
+        cusolverDnHandle_t sol = svd.sol;
+        gesvdjInfo_t params = svd.params;
         PH_SOLVER(cusolverDnXgesvdjSetTolerance(params, 1e-15));
         PH_SOLVER(cusolverDnXgesvdjSetMaxSweeps(params, 100));
         PH_SOLVER(cusolverDnXgesvdjSetSortEig(params, 1));
@@ -525,8 +559,6 @@ ph_status offline_build(ph_handle* h, const double* points, long n) {
                                            d_work, lwork, d_info, params, nn));
         std::vector<int> infos(nn);
         PH_CUDA(cudaMemcpy(infos.data(), d_info, nn * sizeof(int), cudaMemcpyDeviceToHost));
-        cusolverDnDestroyGesvdjInfo(params);
-        cusolverDnDestroy(sol);
         for (int b = 0; b < nn; ++b)
             if (infos[b] != 0) throw Error(PH_ERR_CUDA, "batched Jacobi SVD did not converge");
         std::vector<double> sv((size_t)nn * P), vecs((size_t)nn * P * P);
@@ -624,8 +656,6 @@ ph_status offline_build(ph_handle* h, const double* points, long n) {
             h->key_hoff[key] = hoff;
             hoff += (long long)ranks[d] * ranks[d + dt];
         }
-        cublasDestroy(eng.blas);
-        cusolverDnDestroy(eng.solver);
     }
     // explicit factors per key (coupling mode 0, H^2): L_k^T and R_k^T, both r x PD row-major.
     // L[(i_1..i_k), s_k] = sum L[(i_1..i_{k-1}), s_{k-1}] G_k[s_{k-1}, i_k, s_k] from the left cores;

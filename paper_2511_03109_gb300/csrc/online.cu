@@ -457,6 +457,125 @@ __device__ void mode_product(const T* z, T* out, const T* E, int p, int PD, int 
     }
 }
 
+// Block-wide copy of n consecutive values from global to shared memory: 16-byte vectors when
+// both ends allow it, several loads in flight per thread.
+template <typename T>
+__device__ __forceinline__ void block_copy(T* __restrict__ dst, const T* __restrict__ src, int n) {
+    constexpr int EV = 16 / sizeof(T);
+    if (((uintptr_t)dst % 16 == 0) && ((uintptr_t)src % 16 == 0) && n % EV == 0) {
+        const int nv = n / EV;
+        const int4* s4 = reinterpret_cast<const int4*>(src);
+        int4* d4 = reinterpret_cast<int4*>(dst);
+#pragma unroll 4
+        for (int e = threadIdx.x; e < nv; e += blockDim.x) d4[e] = __ldg(s4 + e);
+    } else {
+#pragma unroll 4
+        for (int e = threadIdx.x; e < n; e += blockDim.x) dst[e] = src[e];
+    }
+}
+
+// Leaf stage of Alg. FastForward, register-tiled: xhat_s[I][c] = sum_{j in s} U_s[j][I] X[j][c]
+// with U_s[j][I] = prod_k U_{s,k}[j][i_k] (face-splitting, §3.3) formed on the fly.  For
+// p_s a multiple of 4 and p_s^d = 4 NT with NT dividing kThreads: thread (tile, group) owns
+// 4 consecutive i_1 of one (i_2, .., i_d) and all MC right-hand sides, and sums the points
+// j = group, group + JS, ... (JS = kThreads / NT groups, combined in shared memory at the end).
+// Per point the thread reads 4 factor values and the point's MC values of X (broadcast within
+// the warp) and issues 4 MC FMAs.  With `push` the leaf then applies its transfer matrix and
+// adds the result into its parent's xhat, as upsweep_leaf_kernel does.  One CTA per leaf.
+template <typename T, int MC>
+__global__ void __launch_bounds__(kThreads) upsweep_leaf_tiled_kernel(DevView<T> v, int S, int c0, int push_level) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int CH = 64;  // points staged per chunk
+    const int ps = v.p_s, d = v.d, PD = v.PD;
+    const int NT = PD / 4, JS = kThreads / NT;
+    T* su = reinterpret_cast<T*>(smem_raw);              // CH x d x p_s
+    T* sx = su + CH * d * ps;                             // CH x MC
+    T* red = sx + CH * MC;                                // JS x PD x MC (slot 0 then holds the sum)
+    T* b1 = red + (size_t)JS * PD * MC;                   // PD x MC
+    T* sE = b1 + (size_t)PD * MC;                         // 2 p^2
+    const int leaf = blockIdx.x;
+    const int node = v.leaf_node[leaf];
+    const int row0 = v.node_begin[node], ns = v.node_end[node] - row0;
+    const int tile = threadIdx.x % NT, g = threadIdx.x / NT;
+    const int q4 = tile % (ps / 4), rest = tile / (ps / 4);
+    const int I0 = 4 * q4 + ps * rest;
+    const int i2 = (d > 1) ? rest % ps : 0, i3 = (d > 2) ? rest / ps : 0;
+    T acc[4][MC];
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+#pragma unroll
+        for (int c = 0; c < MC; ++c) acc[e][c] = T(0);
+    for (int j0 = 0; j0 < ns; j0 += CH) {
+        const int nj = min(CH, ns - j0);
+        __syncthreads();
+        block_copy(su, v.U + (long long)(row0 + j0) * d * ps, nj * d * ps);
+        if (S == MC) {
+            block_copy(sx, v.Xc + (long long)(row0 + j0) * S, nj * MC);
+        } else {
+            for (int e = threadIdx.x; e < nj * MC; e += blockDim.x)
+                sx[e] = v.Xc[(long long)(row0 + j0 + e / MC) * S + c0 + e % MC];
+        }
+        __syncthreads();
+        for (int j = g; j < nj; j += JS) {
+            const T* uj = su + j * d * ps;
+            T u1[4];
+            load_ct<T, 4>(uj + 4 * q4, u1);
+            T ur = T(1);
+            if (d > 1) ur = uj[ps + i2];
+            if (d > 2) ur *= uj[2 * ps + i3];
+            T x[MC];
+            if constexpr (MC >= 4) {
+#pragma unroll
+                for (int c = 0; c < MC; c += 4) load_ct<T, 4>(sx + j * MC + c, *reinterpret_cast<T(*)[4]>(&x[c]));
+            } else {
+#pragma unroll
+                for (int c = 0; c < MC; ++c) x[c] = sx[j * MC + c];
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const T u = u1[e] * ur;
+#pragma unroll
+                for (int c = 0; c < MC; ++c) acc[e][c] += u * x[c];
+            }
+        }
+    }
+    // combine the JS point groups: slot g holds group g's sums, slot 0 receives the total
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+#pragma unroll
+        for (int c = 0; c < MC; ++c) red[((size_t)g * PD + I0 + e) * MC + c] = acc[e][c];
+    __syncthreads();
+    for (int e = threadIdx.x; e < PD * MC; e += blockDim.x) {
+        T s = red[e];
+        for (int gg = 1; gg < JS; ++gg) s += red[(size_t)gg * PD * MC + e];
+        red[e] = s;
+        v.xhat[((long long)node * PD + e / MC) * S + c0 + e % MC] = s;
+    }
+    const int parent = v.node_parent[node];
+    if (parent < 0 || v.node_level[parent] < push_level) return;
+    for (int e = threadIdx.x; e < 2 * ps * ps; e += blockDim.x) sE[e] = v.E[e];
+    const int halves = v.node_halves[node];
+    T* in = red;
+    T* out = b1;
+    int stride = 1;
+    for (int k = 0; k < d; ++k) {
+        __syncthreads();
+        mode_product<T, MC>(in, out, sE + ((halves >> k) & 1) * ps * ps, ps, PD, stride, true, false);
+        T* t = in; in = out; out = t;
+        stride *= ps;
+    }
+    __syncthreads();
+    constexpr int CT = MC < 4 ? MC : 4;
+    T* dst = v.xhat + (long long)parent * PD * S + c0;
+    for (int e = threadIdx.x; e < PD * (MC / CT); e += blockDim.x) {
+        const int I = e / (MC / CT), cq = e % (MC / CT);
+        T val[CT];
+#pragma unroll
+        for (int c = 0; c < CT; ++c) val[c] = in[I * MC + cq * CT + c];
+        atomic_add_ct<T, CT>(dst + (long long)I * S + cq * CT, val);
+    }
+}
+
 // Up-sweep (up = true): xhat_s += sum over inner children s' of (E_{s',d} (x) .. (x) E_{s',1})^T xhat_s'.
 // Down-sweep (up = false): yhat_s' += (E_{s',d} (x) .. (x) E_{s',1}) yhat_s for each inner child s'.
 // Leaf children are handled by upsweep_leaf_kernel and combine_kernel.
@@ -949,18 +1068,7 @@ __global__ void __launch_bounds__(kThreads, 2) coupling_a_staged_kernel(DevView<
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// Shared-memory matrix descriptor of a K-major operand without swizzle: core matrices of 8 rows x
-// 16 bytes, 128 bytes apart along K (leading byte offset) and 256 bytes apart along M / N
-// (stride byte offset); descriptor version 1.
-__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
-    return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(256 >> 4) << 32) |
-           ((uint64_t)1 << 46);
-}
 
-// Byte offset of element (r, k) in a chunk of an R-row K-major operand (K = 32 per chunk).
-__device__ __forceinline__ uint32_t kmajor_off(int r, int k, int R) {
-    return (k / 8) * (R * 32) + (r / 8) * 256 + ((k % 8) / 4) * 128 + (r % 8) * 16 + (k % 4) * 4;
-}
 
 __device__ __forceinline__ float tf32_rna(float x) {
     uint32_t u;
@@ -1009,26 +1117,21 @@ __global__ void wait_bound_kernel(unsigned long long* out) {
     }
 }
 
-__device__ __forceinline__ void umma_tf32(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
-    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                 " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                 "l"(da), "l"(db), "r"(idesc), "r"(acc));
+// The bounded wait of wait_bound_kernel on behalf of a handle: when it runs out it is counted in
+// the handle's flags[1] exactly as a production kernel counts a wait that ran out.
+__global__ void handle_timeout_kernel(int* flags) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    const bool done = mbar_wait(&bar, 0);
+    if (threadIdx.x == 0 && !done) atomicAdd(flags + 1, 1);
 }
+
 
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar)));
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
-}
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
@@ -1043,60 +1146,166 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                  : "memory");
 }
 
-// Phase 1 of the explicit coupling, z_b = H_k R_k^T xhat_t (§4.5; R_k from the right cores,
-// App. A.4), on the tensor cores (FP32 data, one chunk of 16 right-hand
-// sides, p_s^d a multiple of 32, r', r_d <= 64).  Persistent: CTA i takes items i, i + G, ...
-// (G = grid size) of up to 8 far blocks of one class k.  An item's columns (block, right-hand
-// side) are the 128 rows of
-//     P^T = X^T R_k,   X = [xhat_t(b)]  (p_s^d x 128),  R_k (p_s^d x r'),
-// computed by tcgen05.mma kind::tf32 with split operands (3xTF32: x = x_hi + x_lo, products
-// hi*hi + hi*lo + lo*hi).  K = p_s^d runs in chunks of 32 (a "task" is one chunk of one item):
-//   * thread 0 streams each task's inputs with bulk copies into a ring of NS stages: the eight
-//     2 KB slices of xhat (raw FP32) and the chunk of R_k already split and in operand layout;
-//   * all threads split the raw slices into the hi / lo A operands (double-buffered), then
-//     thread 0 issues the 12 MMAs of the chunk into its own tensor-memory region (two regions);
-//   * while the tensor cores run chunk c, the threads read chunk c - 1's partial product from
-//     tensor memory and add it to P in registers (FP32, round to nearest), so the tensor cores
-//     never accumulate more than one chunk; after an item's last chunk they form
-//     z_b = H_k P for their column, overlapped with the next item's MMAs.
-// Every wait is bounded: on a timeout the kernel counts it in flags[1], stops issuing work,
-// waits (bounded) for the copies and MMAs it started and frees its tensor memory.
-namespace tc1 {
-constexpr int NS = 3;                        // stages of the bulk-copy ring
-constexpr int XSTRIDE = 512 + 16;            // floats per block slice in a stage (bank padding)
-constexpr int XST_BYTES = 8 * XSTRIDE * 4;   // raw xhat slices of one stage
-constexpr int BST_BYTES = 2 * 32 * 64 * 4;   // R_k chunk, hi + lo, r'_16 <= 64
-constexpr int A_BYTES = 128 * 32 * 4;        // one part of the A operand
-constexpr int SMEM = NS * XST_BYTES + NS * BST_BYTES + 2 * 2 * A_BYTES + 64 * 64 * 4;
-}  // namespace tc1
+// Bounded wait for phase `parity` of an mbarrier that also gives up as soon as *abort is set
+// (another role of the CTA stopped).  Returns true when the phase completed.
+__device__ __forceinline__ bool mbar_wait_ab(uint64_t* bar, uint32_t parity, volatile int* abort) {
+    uint32_t done = 0;
+    const uint64_t t0 = global_ns();
+    for (int it = 0; !done; ++it) {
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done)
+                     : "r"(smem_u32(bar)), "r"(parity));
+        if (!done && (it & 63) == 63 &&
+            (*abort || global_ns() - t0 > 1000000000ull || it >= (1 << 28) - 1))
+            break;
+    }
+    return done != 0;
+}
 
-__global__ void __launch_bounds__(128, 1) coupling_a_tc_kernel(DevView<float> v) {
-    using namespace tc1;
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char* xst = smem_raw;                             // NS x XST_BYTES
-    unsigned char* bst = xst + NS * XST_BYTES;                 // NS x BST_BYTES
-    unsigned char* abuf = bst + NS * BST_BYTES;                // 2 x (hi, lo)
-    float* Hs = reinterpret_cast<float*>(abuf + 4 * A_BYTES);  // r_d x r' (<= 64 x 64)
-    __shared__ __align__(8) uint64_t fullbar[NS];
-    __shared__ __align__(8) uint64_t mmabar[2];
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Shared-memory matrix descriptor, K-major without swizzle: core matrices of 8 rows x 16 bytes,
+// `lbo` bytes apart along K and `sbo` bytes apart along M / N; descriptor version 1.
+__device__ __forceinline__ uint64_t umma_desc2(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+
+// D (tensor memory) [+]= A (shared memory) x B (shared memory), kind::tf32, one CTA.
+__device__ __forceinline__ void umma_tf32_ss(uint32_t d_tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+                 "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+
+
+
+// Each thread of the warp reads 32 consecutive 32-bit columns of its own lane (load and wait in
+// one statement).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+        "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+
+
+// Phase 1 of the explicit coupling, z_b = H_k R_k^T xhat_t (§4.5; R_k from the right cores,
+// App. A.4), on the tensor cores: FP32 data, one chunk of 16 right-hand sides, p_s^d a multiple
+// of 32, r_d, r' <= 64.  Persistent: CTA i takes items i, i + G, ... (G = grid size) of up to 8
+// far blocks of one class k; the item's 128 (block, right-hand side) pairs are the rows of
+//     P^T = X^T R_k,   X = [xhat_t(b)] (p_s^d x 128),  R_k (p_s^d x r'),
+// formed by tcgen05.mma kind::tf32 with split operands (3xTF32: x = x_hi + x_lo, products
+// hi*hi + hi*lo + lo*hi, so the result keeps FP32 accuracy).  K = p_s^d runs in chunks of 32;
+// a task is one chunk of one item.  Warp roles:
+//   * warp 0 (producer): bulk copies of each task's inputs into a ring of NS stages: the raw
+//     2 KB xhat slices of the item's blocks, and the chunk of R_k stored split (hi, lo) in the
+//     K-major no-swizzle operand layout (8-row x 16-byte core matrices, 128 bytes apart along K,
+//     256 bytes apart along N, K slices of 8 r'_16 * 32 bytes apart);
+//   * warps 2-9 (workers, two per 32-lane quarter of tensor memory): each thread owns one row
+//     (block b, right-hand side c) and one half of the chunk's K values; it splits its 16 xhat
+//     values and writes hi / lo into one of NA shared-memory A buffers in the same K-major
+//     operand layout as B (an MMA that reads A from tensor memory cost several times more per
+//     instruction at these small shapes, measured); LAG tasks after a group of KACC
+//     chunks it reads its half of the group's product columns back and adds them to P in FP32
+//     registers, so the tensor cores never accumulate more than KACC chunks (accumulating all
+//     of K on the tensor cores lost accuracy); after an item's last chunk it hands its half of
+//     P to the epilogue warps through a shared buffer;
+//   * warp 1 (MMA): one thread issues the 12 MMAs of each chunk (4 K slices of 8 x 3 products)
+//     into one of NACC accumulator regions (KACC consecutive chunks of an item share one) and
+//     commits them to mbarriers that free the stage, the A buffer and, after a region's last
+//     chunk, hand the region to the workers;
+//   * warps 10-13 (epilogue): stage H_k in shared memory, then z_b[s][c] = sum_q H_k[s, q]
+//     P^T[(b, c), q] for one row each, stored to the far blocks' z buffer, overlapped with the
+//     next item's MMAs.  The epilogue warps decide together (a barrier reduction) whether to go
+//     on, so their barriers never diverge; no other role waits on them except through the P
+//     buffers, so no wait can close a cycle.
+// Every wait is bounded (about a second): the role that runs out counts it in flags[1] and sets
+// a shared abort flag; every role stops issuing work, waits (bounded) for the copies and MMAs it
+// started, and the CTA frees its tensor memory before it exits.
+namespace tc2 {
+constexpr int NS = 3;                          // stages of the bulk-copy ring
+constexpr int NA = 2;                          // shared-memory A buffers (hi + lo, 128 x 32 each)
+constexpr int NACC = 4;                        // tensor-memory accumulator regions (64 columns each)
+constexpr int KACC = 2;                        // chunks of 32 accumulated in one region before it is read
+constexpr int LAG = 3;                         // a group is drained after the A operand LAG tasks later is stored
+constexpr int NW = 8;                          // worker warps
+constexpr int XROW = 2048 + 64;                // bytes per block slice in a stage (bank padding)
+constexpr int XS_BYTES = 8 * XROW;             // raw xhat slices of one stage
+constexpr int BS_BYTES = 2 * 32 * 64 * 4;      // R_k chunk, hi + lo, r'_16 <= 64
+constexpr int STAGE = XS_BYTES + BS_BYTES;
+constexpr int PROW = 65;                       // floats per row of a P hand-off buffer (bank padding)
+constexpr int PS_BYTES = 128 * PROW * 4;
+constexpr int HS_BYTES = 64 * 64 * 4;          // H_k staged by the epilogue: [q][s], s padded to 64
+constexpr int APART = 128 * 32 * 4;            // one part (hi or lo) of an A buffer
+constexpr int SMEM = NS * STAGE + NA * 2 * APART + PS_BYTES + HS_BYTES;
+constexpr int EPI0 = 2 + NW;                   // first epilogue warp
+constexpr int THREADS = 32 * (EPI0 + 4);
+constexpr uint32_t ACC_COL = 0;                // accumulators at columns [0, 256)
+constexpr int TMEM_COLS = 256;
+}  // namespace tc2
+
+// Barrier `id` over `n` threads that also returns the AND of every participant's `v`.
+__device__ __forceinline__ bool bar_and(bool v, int id, int n) {
+    int r;
+    asm volatile("{\n .reg .pred p, q;\n setp.ne.b32 q, %1, 0;\n bar.red.and.pred p, %2, %3, q;\n"
+                 " selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(r)
+                 : "r"((int)v), "r"(id), "r"(n)
+                 : "memory");
+    return r != 0;
+}
+
+__global__ void __launch_bounds__(tc2::THREADS, 1) coupling_a_umma_kernel(DevView<float> v) {
+    using namespace tc2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char* abuf = smem_raw + NS * STAGE;                         // NA x (hi, lo)
+    float* pbuf = reinterpret_cast<float*>(abuf + NA * 2 * APART);       // 128 x PROW
+    float* hs = pbuf + 128 * PROW;                                       // 64 x 64
+    __shared__ __align__(8) uint64_t full[NS], sempty[NS], aready[NA], aempty[NA], accfull[NACC], accempty[NACC];
+    __shared__ __align__(8) uint64_t pfull, pempty;
     __shared__ uint32_t tmem_holder;
-    const int tid = threadIdx.x, warp = tid / 32;
-    const int PD = v.PD, nchunks = PD / 32;
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    const int PD = v.PD, nchunks = PD / 32, ngroups = (nchunks + KACC - 1) / KACC;
     const int G = gridDim.x;
     const int my_items = (v.n_tcitems - (int)blockIdx.x + G - 1) / G;
     const int T = my_items * nchunks;
-    const int b = tid / 16, c = tid % 16;  // my row of X^T: column (block b, right-hand side c)
+    volatile int* abortp = &abort_flag;
 
     if (tid == 0) {
-        for (int i = 0; i < NS; ++i) mbar_init(&fullbar[i], 1);
-        mbar_init(&mmabar[0], 1);
-        mbar_init(&mmabar[1], 1);
+        for (int i = 0; i < NS; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&sempty[i], 1 + NW);  // MMA commit (B read) + the worker warps (xhat read)
+        }
+        for (int i = 0; i < NA; ++i) {
+            mbar_init(&aready[i], NW);
+            mbar_init(&aempty[i], 1);
+        }
+        for (int i = 0; i < NACC; ++i) {
+            mbar_init(&accfull[i], 1);
+            mbar_init(&accempty[i], NW);
+        }
+        mbar_init(&pfull, NW);
+        mbar_init(&pempty, 4);
+        abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    __syncwarp();
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
-                     "r"(128));
+                     "r"(TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -1104,165 +1313,278 @@ __global__ void __launch_bounds__(128, 1) coupling_a_tc_kernel(DevView<float> v)
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_holder;
 
-    // thread 0: bulk copies of task t into stage t % NS
-    int issued = 0;  // tasks whose copies were issued (thread 0 only)
-    auto issue = [&](int t) {
-        if (t >= T) return;
-        const int item = (int)blockIdx.x + (t / nchunks) * G, ch = t % nchunks;
-        const int key = v.tcitem_key[item], first = v.tcitem_first[item], cnt = v.tcitem_count[item];
-        const int rp = v.key_ranks[(size_t)key * (v.Delta + 1) + v.d + 1], r16 = (rp + 15) & ~15;
-        const int st = t % NS;
-        const uint32_t bbytes = 2u * 32u * (uint32_t)r16 * 4u;
-        mbar_expect_tx(&fullbar[st], (uint32_t)cnt * 2048u + bbytes);
-        for (int i = 0; i < cnt; ++i) {
-            const float* src = v.xhat + (long long)v.fb_t[v.kb_list[first + i]] * PD * 16 + (long long)ch * 512;
-            bulk_g2s(xst + st * XST_BYTES + i * XSTRIDE * 4, src, 2048u, &fullbar[st]);
-        }
-        bulk_g2s(bst + st * BST_BYTES, v.far_tc + v.key_tcoff[key] + (size_t)ch * 2 * 32 * r16, bbytes, &fullbar[st]);
-        issued = t + 1;
+    // the item of local index j and its class data (every role loads the next item's data one
+    // item ahead, so that these dependent global loads never stall the pipeline)
+    struct Item {
+        int key, first, cnt, rd, rp;
+        long long hoff, tcoff;
     };
-    if (tid == 0)
-        for (int t = 0; t < NS - 1; ++t) issue(t);
+    auto item_at = [&](int j) {
+        Item it;
+        const int idx = (int)blockIdx.x + min(j, my_items - 1) * G;
+        it.key = v.tcitem_key[idx];
+        it.first = v.tcitem_first[idx];
+        it.cnt = v.tcitem_count[idx];
+        const int* rk = v.key_ranks + (size_t)it.key * (v.Delta + 1);
+        it.rd = rk[v.d];
+        it.rp = rk[v.d + 1];
+        it.hoff = v.key_hoff[it.key];
+        it.tcoff = v.key_tcoff[it.key];
+        return it;
+    };
+    auto fail = [&]() {
+        if (atomicExch(&abort_flag, 1) == 0) atomicAdd(v.flags + 1, 1);
+    };
+    auto group_of = [&](int t) { return (t / nchunks) * ngroups + (t % nchunks) / KACC; };
+    auto group_end = [&](int t) {
+        const int ch = t % nchunks;
+        return (ch % KACC == KACC - 1) || ch == nchunks - 1;
+    };
 
-    float P[64];
+    if (warp == 0) {
+        // ------------------------------------------------------------------ producer
+        if (lane == 0) {
+            int issued = 0;
+            Item it{}, nxt = item_at(0);
+            int src[8], nsrc[8];
+            auto load_src = [&](const Item& x, int (&o)[8]) {
 #pragma unroll
-    for (int q = 0; q < 64; ++q) P[q] = 0.0f;
-    bool ok = true;
-    int mma_issued = 0;  // tasks whose MMAs were issued (uniform)
-    int landed = 0;      // tasks whose copies this thread saw complete
-
-    // add the partial product of task t (its chunk) to P; after the item's last chunk form z_b
-    auto drain = [&](int t) {
-        const int item = (int)blockIdx.x + (t / nchunks) * G, ch = t % nchunks;
-        const int key = v.tcitem_key[item], first = v.tcitem_first[item], cnt = v.tcitem_count[item];
-        const int* rk = v.key_ranks + (size_t)key * (v.Delta + 1);
-        const int rd = rk[v.d], rp = rk[v.d + 1], r16 = (rp + 15) & ~15;
-        const uint32_t region = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)((t & 1) * 64);
-        __syncwarp();
+                for (int i = 0; i < 8; ++i) o[i] = (i < x.cnt) ? v.kb_list[x.first + i] : 0;
 #pragma unroll
-        for (int q0 = 0; q0 < 64; q0 += 16) {
-            if (q0 < r16) {
-                float pv[16];
-                tmem_ld16(region + q0, pv);
+                for (int i = 0; i < 8; ++i) o[i] = (i < x.cnt) ? v.fb_t[o[i]] : 0;
+            };
+            load_src(nxt, nsrc);
+            for (int t = 0; t < T; ++t) {
+                const int st = t % NS, ch = t % nchunks;
+                if (ch == 0) {
+                    it = nxt;
 #pragma unroll
-                for (int j = 0; j < 16; ++j) P[q0 + j] += pv[j];
+                    for (int i = 0; i < 8; ++i) src[i] = nsrc[i];
+                    nxt = item_at(t / nchunks + 1);
+                    load_src(nxt, nsrc);
+                }
+                if (t >= NS && !mbar_wait_ab(&sempty[st], (uint32_t)((t / NS - 1) & 1), abortp)) {
+                    fail();
+                    break;
+                }
+                if (*abortp) break;
+                const int r16 = (it.rp + 15) & ~15;
+                const uint32_t bbytes = 2u * 32u * (uint32_t)r16 * 4u;
+                unsigned char* stg = smem_raw + st * STAGE;
+                mbar_expect_tx(&full[st], (uint32_t)it.cnt * 2048u + bbytes);
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    if (i < it.cnt)
+                        bulk_g2s(stg + i * XROW, v.xhat + (long long)src[i] * PD * 16 + (long long)ch * 512, 2048u,
+                                 &full[st]);
+                bulk_g2s(stg + XS_BYTES, v.far_tc + it.tcoff + (size_t)ch * 2 * 32 * r16, bbytes, &full[st]);
+                issued = t + 1;
+            }
+            // before the shared memory goes: wait (bounded) for the copies still in flight
+            for (int u = max(0, issued - NS); u < issued; ++u) mbar_wait(&full[u % NS], (uint32_t)((u / NS) & 1));
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            int issued = 0, gdone = 0;
+            uint32_t idesc = 0, r16 = 16;
+            Item nxt = item_at(0);
+            for (int t = 0; t < T; ++t) {
+                const int st = t % NS, a = t % NA, ch = t % nchunks;
+                const int g = group_of(t), r = g % NACC;
+                const bool gfirst = ch % KACC == 0, glast = group_end(t);
+                if (ch == 0) {
+                    const Item it = nxt;
+                    nxt = item_at(t / nchunks + 1);
+                    r16 = (uint32_t)((it.rp + 15) & ~15);
+                    idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((r16 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+                }
+                bool ok = mbar_wait_ab(&full[st], (uint32_t)((t / NS) & 1), abortp);
+                ok = ok && mbar_wait_ab(&aready[a], (uint32_t)((t / NA) & 1), abortp);
+                if (ok && gfirst && g >= NACC)
+                    ok = mbar_wait_ab(&accempty[r], (uint32_t)((g / NACC - 1) & 1), abortp);
+                if (!ok || *abortp) {
+                    fail();
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t b_hi = smem_u32(smem_raw + st * STAGE + XS_BYTES);
+                const uint32_t b_lo = b_hi + 32u * r16 * 4u;
+                const uint32_t a_hi = smem_u32(abuf + a * 2 * APART), a_lo = a_hi + APART;
+                const uint32_t d = tmem + ACC_COL + (uint32_t)r * 64u;
+#pragma unroll
+                for (int s = 0; s < 4; ++s) {
+                    const uint32_t bo = (uint32_t)s * r16 * 32u, ao = (uint32_t)s * 128u * 32u;
+                    umma_tf32_ss(d, umma_desc2(a_hi + ao, 128, 256), umma_desc2(b_hi + bo, 128, 256), idesc,
+                                 (s == 0 && gfirst) ? 0u : 1u);
+                    umma_tf32_ss(d, umma_desc2(a_hi + ao, 128, 256), umma_desc2(b_lo + bo, 128, 256), idesc, 1u);
+                    umma_tf32_ss(d, umma_desc2(a_lo + ao, 128, 256), umma_desc2(b_hi + bo, 128, 256), idesc, 1u);
+                }
+                umma_commit(&sempty[st]);
+                umma_commit(&aempty[a]);
+                if (glast) {
+                    umma_commit(&accfull[r]);
+                    gdone = g + 1;
+                }
+                issued = t + 1;
+            }
+            // the MMAs issued last complete before the tensor memory is freed: after an abort in
+            // the middle of a group, commit what was issued to that group's region first
+            if (issued > 0) {
+                const int gl = group_of(issued - 1);
+                if (gdone <= gl) umma_commit(&accfull[gl % NACC]);
+                mbar_wait(&accfull[gl % NACC], (uint32_t)((gl / NACC) & 1));
             }
         }
-        asm volatile("tcgen05.fence::before_thread_sync;");  // the region is rewritten after the next barrier
-        if (ch != nchunks - 1) return;
-        // epilogue of the item: z_b[r][c] = sum_q H_k[r, q] P^T[(b, c), q]
-        __syncthreads();  // Hs of the previous item is no longer read
-        const float* H = v.H + v.key_hoff[key];
-        // column q of H_k in row q of Hs, padded to 64 with zeros (16-byte reads below)
-        for (int e = tid; e < rp * 64; e += blockDim.x) {
-            const int q = e / 64, r = e % 64;
-            Hs[e] = (r < rd) ? H[r + rd * q] : 0.0f;
+    } else if (warp < EPI0) {
+        // ------------------------------------------------------------------ workers
+        const int q = warp & 3;              // tensor-memory lane quarter of this warp
+        const int hh = (warp - 2) / 4;       // half of the K values (split) and of the columns (drain)
+        const int row = 32 * q + lane;       // (block b, right-hand side c)
+        const int b = row / 16, c = row % 16;
+        const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+        float P[32];
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) P[jj] = 0.0f;
+        bool ok = true;
+        Item cur{}, nxt = item_at(0);  // item of the task being split, and the one after it
+        Item drn{}, dnxt = nxt;        // item of the group being drained, and the one after it
+        // adds this warp's half of the product columns of the group ending with task u to P;
+        // after an item's last chunk, hands P to the epilogue warps
+        auto drain = [&](int u) -> bool {
+            const int ch = u % nchunks, j = u / nchunks;
+            const int g = group_of(u), r = g % NACC;
+            if (!mbar_wait_ab(&accfull[r], (uint32_t)((g / NACC) & 1), abortp)) return false;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            if (ch < KACC) {
+                drn = dnxt;
+                dnxt = item_at(j + 1);
+            }
+            if (32 * hh < drn.rp) {  // warp-uniform
+                float pv[32];
+                tmem_ld32(tmem + lane_base + ACC_COL + (uint32_t)r * 64u + 32u * hh, pv);
+#pragma unroll
+                for (int jj = 0; jj < 32; ++jj) P[jj] += (32 * hh + jj < drn.rp) ? pv[jj] : 0.0f;
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&accempty[r]);
+            if (ch != nchunks - 1) return true;
+            if (j >= 1 && !mbar_wait_ab(&pempty, (uint32_t)((j - 1) & 1), abortp)) return false;
+            float* dst = pbuf + row * PROW + 32 * hh;
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) {
+                dst[jj] = P[jj];
+                P[jj] = 0.0f;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&pfull);
+            return true;
+        };
+        for (int t = 0; t < T && ok; ++t) {
+            const int st = t % NS, a = t % NA;
+            if (t % nchunks == 0) {
+                cur = nxt;
+                nxt = item_at(t / nchunks + 1);
+            }
+            ok = mbar_wait_ab(&full[st], (uint32_t)((t / NS) & 1), abortp);
+            if (ok && t >= NA) ok = mbar_wait_ab(&aempty[a], (uint32_t)((t / NA - 1) & 1), abortp);
+            if (!ok) break;
+            const float* xs = reinterpret_cast<const float*>(smem_raw + st * STAGE + b * XROW) + 16 * 16 * hh + c;
+            float hi[16], lo[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const float x = (b < cur.cnt) ? xs[i * 16] : 0.0f;
+                hi[i] = tf32_rna(x);
+                lo[i] = tf32_rna(x - hi[i]);
+            }
+            // element (row, k) of a part at (k / 8) 4096 + (row / 8) 256 + ((k % 8) / 4) 128 +
+            // (row % 8) 16 + (k % 4) 4 bytes: 8-row x 16-byte core matrices, 128 bytes apart along
+            // K, 256 bytes apart along M, K slices of 8 4096 bytes apart
+            unsigned char* ahi = abuf + a * 2 * APART;
+#pragma unroll
+            for (int g4 = 0; g4 < 4; ++g4) {
+                const int k = 16 * hh + 4 * g4;
+                const uint32_t off = (k / 8) * 4096 + (row / 8) * 256 + ((k % 8) / 4) * 128 + (row % 8) * 16;
+                *reinterpret_cast<float4*>(ahi + off) = make_float4(hi[4 * g4], hi[4 * g4 + 1], hi[4 * g4 + 2], hi[4 * g4 + 3]);
+                *reinterpret_cast<float4*>(ahi + APART + off) =
+                    make_float4(lo[4 * g4], lo[4 * g4 + 1], lo[4 * g4 + 2], lo[4 * g4 + 3]);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor cores
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&aready[a]);
+                mbar_arrive(&sempty[st]);
+            }
+            // drain the group that ended LAG tasks ago, so that the MMAs of the last few tasks run
+            // while this warp splits the next operands (LAG < NA keeps the A buffers flowing)
+            if (t >= LAG && group_end(t - LAG)) {
+                ok = drain(t - LAG);
+                if (!ok) break;
+            }
         }
-        __syncthreads();
-        if (b < cnt) {
-            float z[64];
+        for (int u = max(0, T - LAG); u < T && ok; ++u)
+            if (group_end(u)) ok = drain(u);
+        if (!ok) fail();
+    } else {
+        // ------------------------------------------------------------------ epilogue
+        const int row = tid - 32 * EPI0;
+        const int b = row / 16, c = row % 16;
+        Item nxt = item_at(0);
+        int nfb = (b < nxt.cnt) ? v.kb_list[nxt.first + b] : 0;
+        for (int j = 0; j < my_items; ++j) {
+            const Item it = nxt;
+            const int fb = nfb;
+            nxt = item_at(j + 1);
+            nfb = (b < nxt.cnt) ? v.kb_list[nxt.first + b] : 0;
+            // one decision for all epilogue warps (a barrier that also guarantees that every
+            // epilogue thread is done with the previous item's H_k)
+            const bool ok = bar_and(mbar_wait_ab(&pfull, (uint32_t)(j & 1), abortp), 1, 128);
+            if (!ok) {
+                fail();
+                break;
+            }
+            // H_k (r_d x r', column-major in global memory) into hs[q][s], s padded to 64
+            const float* H = v.H + it.hoff;
+            for (int e = row; e < it.rd * it.rp; e += 128) {
+                const int s = e % it.rd, qq = e / it.rd;
+                hs[qq * 64 + s] = H[e];
+            }
+            float Pr[64];
+            const float* pr = pbuf + row * PROW;
 #pragma unroll
-            for (int r = 0; r < 64; ++r) z[r] = 0.0f;
-            const float4* H4 = reinterpret_cast<const float4*>(Hs);
+            for (int qq = 0; qq < 64; ++qq) Pr[qq] = (qq < it.rp) ? pr[qq] : 0.0f;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&pempty);
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            if (b < it.cnt) {
+                float* dst = v.zbuf + (long long)fb * v.zstride * 16 + c;
+                for (int s0 = 0; s0 < it.rd; s0 += 4) {
+                    // four rows s0..s0+3 of H_k per shared-memory vector read
+                    float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-            for (int q = 0; q < 64; ++q) {
-                if (q < rp) {
-#pragma unroll
-                    for (int i = 0; i < 16; ++i)
-                        if (4 * i < rd) {
-                            const float4 hv = H4[q * 16 + i];
-                            z[4 * i] += hv.x * P[q];
-                            z[4 * i + 1] += hv.y * P[q];
-                            z[4 * i + 2] += hv.z * P[q];
-                            z[4 * i + 3] += hv.w * P[q];
+                    for (int qq = 0; qq < 64; ++qq) {
+                        if (qq < it.rp) {
+                            const float4 h4 = *reinterpret_cast<const float4*>(hs + qq * 64 + s0);
+                            z[0] = fmaf(h4.x, Pr[qq], z[0]);
+                            z[1] = fmaf(h4.y, Pr[qq], z[1]);
+                            z[2] = fmaf(h4.z, Pr[qq], z[2]);
+                            z[3] = fmaf(h4.w, Pr[qq], z[3]);
                         }
+                    }
+                    const int ns = min(4, it.rd - s0);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (e < ns) dst[(long long)(s0 + e) * 16] = z[e];
                 }
             }
-            const int fb = v.kb_list[first + b];
-            float* dst = v.zbuf + (long long)fb * v.zstride * 16 + c;
-#pragma unroll
-            for (int r = 0; r < 64; ++r)
-                if (r < rd) dst[(long long)r * 16] = z[r];
         }
-#pragma unroll
-        for (int q = 0; q < 64; ++q) P[q] = 0.0f;
-    };
-
-    for (int t = 0; t < T && ok; ++t) {
-        const int item = (int)blockIdx.x + (t / nchunks) * G;
-        const int key = v.tcitem_key[item], cnt = v.tcitem_count[item];
-        const int rp = v.key_ranks[(size_t)key * (v.Delta + 1) + v.d + 1], r16 = (rp + 15) & ~15;
-        const int st = t % NS;
-        ok = mbar_wait(&fullbar[st], (uint32_t)((t / NS) & 1));
-        if (ok) landed = t + 1;
-        // split the raw slice of my row into the hi / lo A operands of buffer t & 1 (its MMAs of
-        // task t - 2 finished: waited for in the previous iteration)
-        unsigned char* ahi = abuf + (t & 1) * 2 * A_BYTES;
-        const float* raw = reinterpret_cast<const float*>(xst + st * XST_BYTES) + b * XSTRIDE + c;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            float x[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) x[j] = (b < cnt) ? raw[(4 * q + j) * 16] : 0.0f;
-            float4 hi, lo;
-            hi.x = tf32_rna(x[0]); hi.y = tf32_rna(x[1]); hi.z = tf32_rna(x[2]); hi.w = tf32_rna(x[3]);
-            lo.x = tf32_rna(x[0] - hi.x); lo.y = tf32_rna(x[1] - hi.y);
-            lo.z = tf32_rna(x[2] - hi.z); lo.w = tf32_rna(x[3] - hi.w);
-            const uint32_t off = kmajor_off(tid, 4 * q, 128);
-            *reinterpret_cast<float4*>(ahi + off) = hi;
-            *reinterpret_cast<float4*>(ahi + A_BYTES + off) = lo;
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        ok = __syncthreads_and(ok);
-        if (!ok) break;
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t a_hi = smem_u32(ahi), a_lo = a_hi + A_BYTES;
-            const uint32_t b_hi = smem_u32(bst + st * BST_BYTES), b_lo = b_hi + 32u * (uint32_t)r16 * 4u;
-            const uint32_t idesc =
-                (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(r16 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-            const uint32_t dt = tmem + (uint32_t)((t & 1) * 64);
-#pragma unroll
-            for (int s = 0; s < 4; ++s) {
-                const uint32_t ao = s * 128 * 32, bo = s * r16 * 32;
-                umma_tf32(dt, umma_desc(a_hi + ao), umma_desc(b_hi + bo), idesc, s == 0 ? 0u : 1u);
-                umma_tf32(dt, umma_desc(a_hi + ao), umma_desc(b_lo + bo), idesc, 1u);
-                umma_tf32(dt, umma_desc(a_lo + ao), umma_desc(b_hi + bo), idesc, 1u);
-            }
-            umma_commit(&mmabar[t & 1]);
-        }
-        mma_issued = t + 1;
-        if (t >= 1) {
-            ok = mbar_wait(&mmabar[(t - 1) & 1], (uint32_t)(((t - 1) >> 1) & 1));
-            ok = __syncthreads_and(ok);
-            if (!ok) break;
-        }
-        // the stage of task t - 1 is free: its slices were split and its MMAs are done
-        if (tid == 0) issue(t + NS - 1);
-        if (t >= 1) {
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            drain(t - 1);
-        }
-    }
-    if (ok && T > 0) {
-        ok = mbar_wait(&mmabar[(T - 1) & 1], (uint32_t)(((T - 1) >> 1) & 1));
-        ok = __syncthreads_and(ok);
-        if (ok) {
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            drain(T - 1);
-        }
-    }
-    if (!ok && tid == 0) {
-        atomicAdd(v.flags + 1, 1);
-        // bounded waits for everything this CTA started before its shared and tensor memory go
-        for (int t = landed; t < issued; ++t) mbar_wait(&fullbar[t % NS], (uint32_t)((t / NS) & 1));
-        if (mma_issued > 0) mbar_wait(&mmabar[(mma_issued - 1) & 1], (uint32_t)(((mma_issued - 1) >> 1) & 1));
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 1) {
         __syncwarp();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
     }
 }
 
@@ -1683,6 +2005,115 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(DevView<T> v, T* __re
     }
 }
 
+// Y[perm[i] + c ldy] = sum of the leaf's near partials + (U_s yhat_s)[i][c] for the H^2 format,
+// register-tiled (MC a multiple of 4, d = 2 or 3): yhat_s first receives its parent's share
+// (E_{s,d} (x) .. (x) E_{s,1}) yhat_parent (last level of Alg. FastBackward) as in
+// combine_kernel; then thread (row i, part) sums U_s[i][I] yhat_s[I][0..MC) over the I whose
+// outermost index falls in its part (two parts, combined in shared memory), with
+// U_s[i][I] = prod_k U_{s,k}[i][i_k] formed on the fly and yhat_s read as broadcast vectors.
+// One CTA per leaf, rows in passes of 128.
+template <typename T, int MC>
+__global__ void __launch_bounds__(kThreads) combine_tiled_kernel(DevView<T> v, T* __restrict__ Y, long long ldy,
+                                                                 int m, int S, int c0, int pull_level) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int RB = kThreads / 2;
+    const int ps = v.p_s, d = v.d, PD = v.PD;
+    const int US = d * ps + 1;                              // padded factor row (bank spread)
+    T* sy = reinterpret_cast<T*>(smem_raw);                 // PD x MC
+    T* sE = sy + (size_t)PD * MC;                           // 2 p^2 (padded to 4)
+    T* b0 = sE + ((2 * ps * ps + 3) & ~3);                  // PD x MC (pull scratch)
+    T* b1 = b0 + (size_t)PD * MC;                           // PD x MC
+    T* su = b0;                                             // RB x US (reuses the pull scratch)
+    T* red = su + (((size_t)RB * US + 3) & ~(size_t)3);     // RB x MC
+    const int leaf = blockIdx.x;
+    const int node = v.leaf_node[leaf];
+    const int row0 = v.node_begin[node], ns = v.node_end[node] - row0;
+    const int parent = v.node_parent[node];
+    const bool pull = parent >= 0 && v.node_level[parent] >= pull_level;
+    if (S == MC) {
+        block_copy(sy, v.yhat + (long long)node * PD * S, PD * MC);
+        if (pull) block_copy(b0, v.yhat + (long long)parent * PD * S, PD * MC);
+    } else {
+        for (int e = threadIdx.x; e < PD * MC; e += blockDim.x)
+            sy[e] = v.yhat[((long long)node * PD + e / MC) * S + c0 + e % MC];
+        if (pull)
+            for (int e = threadIdx.x; e < PD * MC; e += blockDim.x)
+                b0[e] = v.yhat[((long long)parent * PD + e / MC) * S + c0 + e % MC];
+    }
+    if (pull) {
+        for (int e = threadIdx.x; e < 2 * ps * ps; e += blockDim.x) sE[e] = v.E[e];
+        const int halves = v.node_halves[node];
+        T* in = b0;
+        T* out = b1;
+        int stride = 1;
+        for (int k = 0; k < d; ++k) {
+            __syncthreads();
+            const bool last = (k == d - 1);
+            mode_product<T, MC>(in, last ? sy : out, sE + ((halves >> k) & 1) * ps * ps, ps, PD, stride, false, last);
+            T* t = in; in = out; out = t;
+            stride *= ps;
+        }
+    }
+    const int r = threadIdx.x % RB, part = threadIdx.x / RB;
+    const int outer0 = part * (ps / 2), outer1 = part == 0 ? ps / 2 : ps;  // outermost index range
+    const int mid = (d == 3) ? ps : 1;
+    for (int p0 = 0; p0 < ns; p0 += RB) {
+        const int nr = min(RB, ns - p0);
+        __syncthreads();  // sy complete; su / red free
+        for (int e = threadIdx.x; e < nr * d * ps; e += blockDim.x)
+            su[(e / (d * ps)) * US + e % (d * ps)] = v.U[(long long)(row0 + p0) * d * ps + e];
+        __syncthreads();
+        T acc[MC];
+#pragma unroll
+        for (int c = 0; c < MC; ++c) acc[c] = T(0);
+        if (r < nr) {
+            const T* u = su + r * US;
+            for (int o = outer0; o < outer1; ++o) {
+                const T wo = u[(d - 1) * ps + o];
+                for (int i2 = 0; i2 < mid; ++i2) {
+                    const T wm = (d == 3) ? wo * u[ps + i2] : wo;
+                    const int Ib = ((d == 3) ? (o * ps + i2) : o) * ps;
+                    for (int i1 = 0; i1 < ps; ++i1) {
+                        const T w = wm * u[i1];
+                        const T* yv = sy + (size_t)(Ib + i1) * MC;
+#pragma unroll
+                        for (int c = 0; c < MC; c += 4) {
+                            T y4[4];
+                            load_ct<T, 4>(yv + c, y4);
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) acc[c + e] += w * y4[e];
+                        }
+                    }
+                }
+            }
+        }
+        if (part == 1) {
+#pragma unroll
+            for (int c = 0; c < MC; ++c) red[r * MC + c] = acc[c];
+        }
+        __syncthreads();
+        if (part == 0 && r < nr) {
+            const int i = p0 + r;
+#pragma unroll
+            for (int c = 0; c < MC; ++c) acc[c] += red[r * MC + c];
+            for (int q = v.items_by_leaf[leaf]; q < v.items_by_leaf[leaf + 1]; ++q) {
+                const T* pp = v.partials + ((long long)q * v.part_stride + i) * S + c0;
+#pragma unroll
+                for (int c = 0; c < MC; c += 4) {
+                    T x[4];
+                    load_ct<T, 4>(pp + c, x);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) acc[c + e] += x[e];
+                }
+            }
+            const int orig = v.perm[row0 + i];
+#pragma unroll
+            for (int c = 0; c < MC; ++c)
+                if (c0 + c < m) Y[orig + (long long)(c0 + c) * ldy] = acc[c];
+        }
+    }
+}
+
 int pick_mc(int m) {
     if (m <= 1) return 1;
     if (m <= 2) return 2;
@@ -1885,10 +2316,19 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
         for (int c0 = 0; c0 < S; c0 += MC) {
             if (h2) {
                 PH_CUDA(cudaMemsetAsync(v.xhat, 0, (size_t)v.n_nodes * PD * S * sizeof(T), far));
-                size_t sm_leaf = ((size_t)32 * kMaxDim * kMaxPs + 32 * MC + ((2 * v.p_s * v.p_s + 3) & ~3) +
-                                  2 * (size_t)PD * MC) * sizeof(T);
-                set_smem<T, MC>((const void*)upsweep_leaf_kernel<T, MC>, sm_leaf);
-                {
+                // register-tiled leaf kernel when p_s is a multiple of 4 and p_s^d / 4 divides the CTA
+                const int nt4 = PD / 4;
+                const bool tiled = (v.p_s % 4 == 0) && nt4 >= 1 && nt4 <= kThreads && kThreads % nt4 == 0;
+                const size_t sm_tiled = ((size_t)64 * v.d * v.p_s + 64 * MC + (size_t)(kThreads / std::max(1, nt4)) * PD * MC +
+                                         (size_t)PD * MC + 2 * v.p_s * v.p_s) * sizeof(T);
+                if (tiled && sm_tiled <= 200 * 1024) {
+                    set_smem<T, MC>((const void*)upsweep_leaf_tiled_kernel<T, MC>, sm_tiled);
+                    ProfScope ps(h, 3, far);
+                    upsweep_leaf_tiled_kernel<T, MC><<<nleaves, kThreads, sm_tiled, far>>>(v, S, c0, h->min_far_level);
+                } else {
+                    size_t sm_leaf = ((size_t)32 * kMaxDim * kMaxPs + 32 * MC + ((2 * v.p_s * v.p_s + 3) & ~3) +
+                                      2 * (size_t)PD * MC) * sizeof(T);
+                    set_smem<T, MC>((const void*)upsweep_leaf_kernel<T, MC>, sm_leaf);
                     ProfScope ps(h, 3, far);
                     upsweep_leaf_kernel<T, MC><<<nleaves, kThreads, sm_leaf, far>>>(v, S, c0, h->min_far_level);
                 }
@@ -1913,10 +2353,10 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
                         bool launched = false;
                         if constexpr (std::is_same<T, float>::value && MC == 16) {
                             if (tc && S == 16) {
-                                PH_CUDA(cudaFuncSetAttribute(coupling_a_tc_kernel,
-                                                             cudaFuncAttributeMaxDynamicSharedMemorySize, tc1::SMEM));
+                                PH_CUDA(cudaFuncSetAttribute(coupling_a_umma_kernel,
+                                                             cudaFuncAttributeMaxDynamicSharedMemorySize, tc2::SMEM));
                                 const int grid = std::min(v.n_tcitems, h->num_sms);
-                                coupling_a_tc_kernel<<<grid, 128, tc1::SMEM, far>>>(v);
+                                coupling_a_umma_kernel<<<grid, tc2::THREADS, tc2::SMEM, far>>>(v);
                                 h->last_variants |= 4;
                                 launched = true;
                             }
@@ -2028,13 +2468,25 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
         PH_CUDA(cudaStreamWaitEvent(stream, h->ev_join, 0));
     }
     for (int c0 = 0; c0 < S; c0 += MC) {
-        size_t sm = ((size_t)PD * MC + std::max((size_t)2 * PD * MC + ((2 * v.p_s * v.p_s + 3) & ~3),
-                                                (size_t)kThreads * v.d * v.p_s)) * sizeof(T);
-        set_smem<T, MC>((const void*)combine_kernel<T, MC>, sm);
+        const bool h2far = h2 && !plan.far_targets.empty();
+        const int RB = kThreads / 2;
+        const size_t sm_t = ((size_t)PD * MC + ((2 * v.p_s * v.p_s + 3) & ~3) +
+                             std::max((size_t)2 * PD * MC, (((size_t)RB * (v.d * v.p_s + 1) + 3) & ~(size_t)3) +
+                                                               (size_t)RB * MC)) * sizeof(T);
         ProfScope ps(h, 8, stream);
-        combine_kernel<T, MC><<<nleaves, kThreads, sm, stream>>>(v, Y, ldy, m, S, c0,
-                                                                 (h2 && !plan.far_targets.empty()) ? 1 : 0,
-                                                                 h->min_far_level);
+        if (h2far && MC >= 4 && (v.d == 2 || v.d == 3) && v.p_s % 2 == 0 && sm_t <= 200 * 1024) {
+            if constexpr (MC >= 4) {
+                set_smem<T, MC>((const void*)combine_tiled_kernel<T, MC>, sm_t);
+                combine_tiled_kernel<T, MC><<<nleaves, kThreads, sm_t, stream>>>(v, Y, ldy, m, S, c0,
+                                                                                 h->min_far_level);
+            }
+        } else {
+            size_t sm = ((size_t)PD * MC + std::max((size_t)2 * PD * MC + ((2 * v.p_s * v.p_s + 3) & ~3),
+                                                    (size_t)kThreads * v.d * v.p_s)) * sizeof(T);
+            set_smem<T, MC>((const void*)combine_kernel<T, MC>, sm);
+            combine_kernel<T, MC><<<nleaves, kThreads, sm, stream>>>(v, Y, ldy, m, S, c0, h2far ? 1 : 0,
+                                                                     h->min_far_level);
+        }
         PH_LAUNCH("combine_kernel");
     }
 }
@@ -2046,7 +2498,7 @@ ph_status matvec_typed(ph_handle* h, DevView<T>& v, const T* X, long long ldx, i
     const int S = (int)ceil_div(m, MC) * MC;
     const bool h2 = (h->opts.fmt == PH_FMT_H2);
     const int check = h->opts.check_finite ? 1 : 0;
-    if (check) PH_CUDA(cudaMemsetAsync(v.flags, 0, 2 * sizeof(int), stream));
+    if (check) PH_CUDA(cudaMemsetAsync(v.flags, 0, sizeof(int), stream));  // flags[1] counts on
     const long long total = (long long)v.n * S;
     int grid = (int)std::min<long long>(ceil_div(total, kThreads), 152 * 16);
     {
@@ -2065,12 +2517,16 @@ ph_status matvec_typed(ph_handle* h, DevView<T>& v, const T* X, long long ldx, i
         case 8: run_matvec<T, 8>(h, v, X, ldx, m, Y, ldy, stream, S); break;
         default: run_matvec<T, 16>(h, v, X, ldx, m, Y, ldy, stream, S); break;
     }
+    post_timeout_flag(h, stream);
     if (check) {
         int bad[2] = {0, 0};
         PH_CUDA(cudaMemcpyAsync(bad, v.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, stream));
         PH_CUDA(cudaStreamSynchronize(stream));
         if (bad[0]) throw Error(PH_ERR_NONFINITE, "X has non-finite entries");
-        if (bad[1]) throw Error(PH_ERR_TIMEOUT, "a bounded tensor-core wait ran out");
+        if (bad[1] > h->seen_timeouts) {
+            h->seen_timeouts = bad[1];
+            throw Error(PH_ERR_TIMEOUT, "a bounded device-side wait ran out");
+        }
     }
     return PH_OK;
 }
@@ -2141,6 +2597,13 @@ ph_status wait_bound_selftest(int device, double* waited) {
     return hres[0] ? PH_OK : PH_ERR_TIMEOUT;
 }
 
+ph_status handle_timeout_selftest(ph_handle* h, cudaStream_t stream) {
+    handle_timeout_kernel<<<1, 32, 0, stream>>>(h->d_flags);
+    PH_LAUNCH("handle_timeout_kernel");
+    post_timeout_flag(h, stream);
+    return PH_OK;
+}
+
 ph_status online_instantiate(ph_handle* h, const double* theta, cudaStream_t stream, int deriv) {
     if (h->opts.prec == PH_FP32) instantiate_typed<float>(h, h->vf, theta, deriv, stream);
     else instantiate_typed<double>(h, h->vd, theta, deriv, stream);
@@ -2186,9 +2649,21 @@ ph_status online_matvec_batched(ph_handle* h, const double* thetas, int n_theta,
         online_instantiate(h, &eta, stream, -1);
         online_matvec(h, X, ldx, m, (char*)h->d_ynodes + (size_t)q * n * m * sc, n, stream);
     }
-    h->host_thetas.assign(thetas, thetas + n_theta);
-    PH_CUDA(cudaMemcpyAsync(h->d_thetas, h->host_thetas.data(), (size_t)n_theta * sizeof(double),
+    // pinned staging of the thetas: wait until the previous call's copy out of it has run, then
+    // refill it and copy asynchronously
+    if (h->ev_thetas) PH_CUDA(cudaEventSynchronize(h->ev_thetas));
+    else PH_CUDA(cudaEventCreateWithFlags(&h->ev_thetas, cudaEventDisableTiming));
+    if ((size_t)n_theta > h->host_thetas_cap) {
+        if (h->host_thetas_pinned) PH_CUDA(cudaFreeHost(h->host_thetas_pinned));
+        h->host_thetas_pinned = nullptr;
+        h->host_thetas_cap = 0;
+        PH_CUDA(cudaHostAlloc((void**)&h->host_thetas_pinned, (size_t)n_theta * sizeof(double), cudaHostAllocDefault));
+        h->host_thetas_cap = (size_t)n_theta;
+    }
+    std::copy(thetas, thetas + n_theta, h->host_thetas_pinned);
+    PH_CUDA(cudaMemcpyAsync(h->d_thetas, h->host_thetas_pinned, (size_t)n_theta * sizeof(double),
                             cudaMemcpyHostToDevice, stream));
+    PH_CUDA(cudaEventRecord(h->ev_thetas, stream));
     const long long nel = (long long)n * m;
     dim3 grid((unsigned)std::max<long long>(1, std::min<long long>(ceil_div(nel, kThreads), (long long)h->num_sms * 4)),
               (unsigned)ceil_div(n_theta, 32));

@@ -15,6 +15,7 @@
 namespace {
 
 const char kMagic[8] = {'P', 'H', 'L', 'I', 'B', '0', '0', '3'};  // 003: tensor-core R_k layout
+constexpr int kArenas = 9;  // near, near theta, far, far theta, S/T, U, E, L/R, tensor-core R (this order)
 
 struct Writer {
     FILE* f;
@@ -56,13 +57,6 @@ struct Reader {
         if (n > left / sizeof(T)) throw ph::Error(PH_ERR_IO, "corrupt file");
         v.resize(n);
         raw(v.data(), n * sizeof(T));
-    }
-    void* dev(ph_handle* h) {
-        std::vector<unsigned char> tmp;
-        vec(tmp);
-        void* p = ph::dev_alloc(h, tmp.size());
-        if (!tmp.empty()) PH_CUDA(cudaMemcpy(p, tmp.data(), tmp.size(), cudaMemcpyHostToDevice));
-        return p;
     }
 };
 
@@ -121,7 +115,7 @@ void scalars_io(IO& io, H& h) {
 }  // namespace
 
 extern "C" ph_status ph_save(const ph_handle* hc, const char* path) {
-    if (!hc || !path) return PH_ERR_INVALID_ARG;
+    if (!hc || !path) return ph::fail(nullptr, PH_ERR_INVALID_ARG, "ph_save: NULL argument");
     ph_handle* h = const_cast<ph_handle*>(hc);
     FILE* f = fopen(path, "wb");
     if (!f) {
@@ -162,28 +156,50 @@ extern "C" ph_status ph_save(const ph_handle* hc, const char* path) {
 }
 
 extern "C" ph_status ph_load(const char* path, int device, ph_handle** out) {
-    if (!path || !out) return PH_ERR_INVALID_ARG;
+    if (!path || !out) return ph::fail(nullptr, PH_ERR_INVALID_ARG, "ph_load: NULL argument");
     *out = nullptr;
     FILE* f = fopen(path, "rb");
-    if (!f) return PH_ERR_IO;
-    ph_handle* h = new ph_handle();
-    ph_status st = PH_OK;
+    if (!f) return ph::fail(nullptr, PH_ERR_IO, std::string("cannot open ") + path);
+    ph_handle* h = nullptr;
     try {
+        h = new ph_handle();
+    } catch (...) {
+        fclose(f);
+        return ph::fail(nullptr, PH_ERR_OOM, "host allocation failed");
+    }
+    // everything is read and checked on the host before the device is touched
+    ph_status st = ph::guarded(nullptr, [&]() -> ph_status {
         Reader r(f);
         char magic[8];
         r.raw(magic, 8);
-        if (std::memcmp(magic, kMagic, 8) != 0) throw ph::Error(PH_ERR_IO, "not a libph file");
+        if (std::memcmp(magic, kMagic, 8) != 0) throw ph::Error(PH_ERR_IO, "not a libph file of this version");
         scalars_io(r, *h);
         h->device = device;
         h->opts.device = device;
         plan_io(r, h->plan);
         unsigned long long nn = 0;
         r.val(nn);
+        // a node takes at least its fixed fields: refuse a count the file cannot hold
+        if (nn > r.left / (6 * sizeof(int) + 6 * sizeof(double) + 8)) throw ph::Error(PH_ERR_IO, "corrupt file");
         h->plan.nodes.resize(nn);
         for (auto& nd : h->plan.nodes) {
             r.val(nd.level); r.val(nd.parent); r.val(nd.halves); r.val(nd.begin); r.val(nd.end); r.val(nd.leaf);
             r.raw(nd.lo, sizeof(nd.lo)); r.raw(nd.hi, sizeof(nd.hi));
             r.vec(nd.children);
+        }
+        std::vector<std::vector<unsigned char>> arenas(kArenas);
+        std::vector<size_t> sizes(kArenas);
+        for (int i = 0; i < kArenas; ++i) {
+            r.vec(arenas[i]);
+            sizes[i] = arenas[i].size();
+        }
+        if (r.left != 0) throw ph::Error(PH_ERR_IO, "trailing bytes after the last arena");
+        ph::validate_handle(*h, sizes);
+
+        int ndev = 0;
+        if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+            cudaGetLastError();
+            throw ph::Error(PH_ERR_CUDA, "no CUDA device " + std::to_string(device));
         }
         PH_CUDA(cudaSetDevice(device));
         // the far-field chain is the longer path of a matvec: its stream gets the highest priority so
@@ -195,23 +211,19 @@ extern "C" ph_status ph_load(const char* path, int device, ph_handle** out) {
         }
         PH_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
         PH_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
-        h->d_near = r.dev(h);
-        h->d_near_theta = (double*)r.dev(h);
-        h->d_far = r.dev(h);
-        h->d_far_theta = (double*)r.dev(h);
-        h->d_st = r.dev(h);
-        h->d_U = r.dev(h);
-        h->d_E = r.dev(h);
-        h->d_lr = r.dev(h);
-        h->d_tc = r.dev(h);
+        void** dst[kArenas] = {&h->d_near, (void**)&h->d_near_theta, &h->d_far, (void**)&h->d_far_theta,
+                               &h->d_st,   &h->d_U,                  &h->d_E,   &h->d_lr,
+                               &h->d_tc};
+        for (int i = 0; i < kArenas; ++i) {
+            *dst[i] = ph::dev_alloc(h, arenas[i].size());
+            if (!arenas[i].empty())
+                PH_CUDA(cudaMemcpy(*dst[i], arenas[i].data(), arenas[i].size(), cudaMemcpyHostToDevice));
+        }
         h->d_H = ph::dev_alloc(h, (h->H_elems > 0 ? h->H_elems : 1) * h->scalar);
         h->d_w = ph::dev_alloc(h, (h->w_elems > 0 ? h->w_elems : 1) * h->scalar);
         ph::refresh_views(h);
-    } catch (const ph::Error& e) {
-        st = e.status;
-    } catch (...) {
-        st = PH_ERR_IO;
-    }
+        return PH_OK;
+    });
     fclose(f);
     if (st != PH_OK) {
         ph::free_device(h);

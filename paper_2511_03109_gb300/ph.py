@@ -91,6 +91,9 @@ _SIGS = {
     "ph_set_tensor_cores": (C.c_int, [_H, C.c_int]),
     "ph_profile_read": (C.c_int, [_H, C.POINTER(C.c_double), C.POINTER(C.c_long)]),
     "ph_selftest_wait_bound": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
+    "ph_check": (C.c_int, [_H, _P]),
+    "ph_inject_alloc_failure": (C.c_int, [C.c_long]),
+    "ph_selftest_timeout": (C.c_int, [_H, _P]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -231,6 +234,10 @@ class ParametricMatrix:
         s = torch.cuda.current_stream(X.device).cuda_stream if stream is None else stream
         self.matvec_ptr(Xc.data_ptr(), n, m, Y.data_ptr(), n, s)
         return Y
+
+    def check(self, stream=0):
+        """ph_check: synchronise and report a device wait that ran out in an earlier call."""
+        return check(ph_check(self.h, C.c_void_p(stream)), self.h)
 
     def set_overlap(self, enable=True):
         return check(ph_set_overlap(self.h, 1 if enable else 0), self.h)

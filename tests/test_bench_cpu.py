@@ -31,7 +31,7 @@ def test_variant_bits_pick_the_launched_kernels(bench):
     assert bench.kernel_of("near", {"kernel_variants": 1}) == "near_tma_kernel"
     assert bench.kernel_of("near", {"kernel_variants": 0}) == "near_kernel"
     assert bench.kernel_of("coupling_b", {"kernel_variants": 2}) == "coupling_b_tma_kernel"
-    assert bench.kernel_of("coupling", {"kernel_variants": 4}) == "coupling_a_tc_kernel"
+    assert bench.kernel_of("coupling", {"kernel_variants": 4}) == "coupling_a_umma_kernel"
     assert bench.kernel_of("coupling", {"kernel_variants": 3}) == "coupling_a_staged_kernel"
 
 
@@ -42,7 +42,7 @@ def test_traffic_records_follow_the_kernel_sources(bench):
     kernels = [k for k in rec if not k.startswith("_")]
     assert kernels
     kind_of = {"near_tma_kernel": ("near", 1), "near_kernel": ("near", 0),
-               "coupling_a_staged_kernel": ("coupling", 0), "coupling_a_tc_kernel": ("coupling", 4),
+               "coupling_a_staged_kernel": ("coupling", 0), "coupling_a_umma_kernel": ("coupling", 4),
                "coupling_b_tma_kernel": ("coupling_b", 2), "coupling_b_kernel": ("coupling_b", 0)}
     for name in kernels:
         assert rec[name]["bytes_per_launch"] > 0

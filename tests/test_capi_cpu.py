@@ -112,3 +112,104 @@ def test_load_rejects_missing_foreign_old_and_corrupt_files(tmp_path):
     # gets an impossible one
     (tmp_path / "huge.ph").write_bytes(b"PHLIB003" + struct.pack("<Q", 1 << 40) * 4096)
     assert load(tmp_path / "huge.ph") == ph.PH_ERR_IO
+
+
+def _handle_file(mutate=None):
+    """Bytes of a small, consistent handle file in the library's format (one leaf of 4 points in
+    1-D, one near block of rank 1, no far field, FP64), with `mutate(fields)` applied to the
+    fields first.  Built here from the format's definition, not by the library."""
+    import struct
+
+    f = {
+        "opts": ph.make_opts(1, [0.1], [1.0], [1], 2, 0, 1.0, 1e-6, fmt="h2", prec="fp64"),
+        "PD": 2, "Delta": 3, "P": 2, "scalar": 8,
+        "nb_rank": [1], "nb_off": [0], "nb_toff": [0], "nb_woff": [0, 1],
+        "near_elems": 16, "near_theta_elems": 2, "w_elems": 1,
+        "perm": [0, 1, 2, 3], "leaves": [0], "near_s": [0], "near_t": [0], "near_by_leaf": [0, 1],
+        "far_by_target": [0],
+        "node": {"level": 0, "parent": -1, "halves": 0, "begin": 0, "end": 4, "leaf": 0},
+        "arenas": [16 * 8, 2 * 8, 0, 0, 0, 4 * 1 * 2 * 8, 2 * 2 * 2 * 8, 0, 0],
+    }
+    if mutate:
+        mutate(f)
+    out = bytearray(b"PHLIB003")
+    vec = lambda fmt, xs: struct.pack("<Q", len(xs)) + struct.pack("<%d%s" % (len(xs), fmt), *xs)
+    out += struct.pack("<i", 0)  # kernel: Gaussian
+    out += bytes(f["opts"])
+    out += struct.pack("<iii", f["PD"], f["Delta"], f["P"])
+    out += struct.pack("<Qd", f["scalar"], 0.0)
+    out += vec("i", f["nb_rank"]) + vec("q", f["nb_off"]) + vec("q", f["nb_toff"]) + vec("i", f["nb_woff"])
+    out += vec("i", []) + vec("q", []) + vec("q", [])          # key ranks, core offsets, H offsets
+    out += vec("q", []) + vec("q", [])                           # S_b, T_b offsets
+    out += vec("q", []) + struct.pack("<q", 0)                   # L/R offsets, L/R elements
+    out += vec("q", []) + struct.pack("<q", 0)                   # tensor-core offsets, elements
+    out += struct.pack("<7q", f["near_elems"], f["near_theta_elems"], 0, 0, 0, 0, f["w_elems"])
+    out += vec("d", [0.0] * 96) + vec("d", [0.0] * 96) + vec("d", [0.0] * 8)
+    out += struct.pack("<iqi", 1, 4, 0)                          # plan: d, n, depth
+    for key in ("perm", "leaves", "near_s", "near_t"):
+        out += vec("i", f[key])
+    out += vec("i", []) * 4                                      # far_s, far_t, far_key, key_rep
+    out += vec("i", f["near_by_leaf"]) + vec("i", []) + vec("i", f["far_by_target"])
+    nd = f["node"]
+    out += struct.pack("<Q6i", 1, nd["level"], nd["parent"], nd["halves"], nd["begin"], nd["end"], nd["leaf"])
+    out += struct.pack("<6d", 0, 0, 0, 1, 0, 0) + vec("i", [])
+    for nbytes in f["arenas"]:
+        out += vec("B", [0] * nbytes)
+    return bytes(out)
+
+
+def _set(key, value, index=None):
+    def mutate(f):
+        if index is None:
+            f[key] = value
+        else:
+            f[key][index] = value
+    return mutate
+
+
+def _node_end(f):
+    f["node"]["end"] = 5
+
+
+def _short_near_arena(f):
+    f["arenas"][0] -= 8
+
+
+def _other_p_s(f):
+    f["opts"].p_s = 3
+
+
+@pytest.mark.parametrize("mutate", [
+    _set("nb_off", [1]),            # the block's cores would end one entry past the arena
+    _set("perm", 4, 0),             # a permutation entry outside 0..n-1
+    _set("near_t", 5, 0),           # a near source that is not a node
+    _set("nb_woff", [0, 2]),        # weight offsets that disagree with the rank
+    _set("nb_rank", [40]),          # a rank above the kernels' limit
+    _set("leaves", 1, 0),           # a leaf id that is not a node
+    _node_end,                      # a node range past n
+    _short_near_arena,              # an arena shorter than its element count (length still consistent)
+    _other_p_s,                     # options from another build (p_s^d no longer the stored PD)
+], ids=["nb_off", "perm", "near_t", "nb_woff", "rank", "leaves", "node_end", "arena", "p_s"])
+def test_load_refuses_corrupt_contents(tmp_path, mutate):
+    """ph_load checks every stored offset, index and size on the host before it touches a
+    device: one flipped value in an otherwise consistent file is refused with PH_ERR_IO."""
+    good = tmp_path / "good.ph"
+    good.write_bytes(_handle_file())
+    h = C.c_void_p()
+    st = ph.ph_load(str(good).encode(), 0, C.byref(h))
+    # without a GPU the good file passes every check and fails only at the device
+    assert st in (ph.PH_OK, ph.PH_ERR_CUDA), ph.ph_last_error(None)
+    if st == ph.PH_OK:
+        ph.ph_destroy(h)
+    bad = tmp_path / "bad.ph"
+    bad.write_bytes(_handle_file(mutate))
+    h = C.c_void_p()
+    assert ph.ph_load(str(bad).encode(), 0, C.byref(h)) == ph.PH_ERR_IO
+    assert b"inconsistent handle data" in ph.ph_last_error(None)
+    assert not h.value
+
+
+def test_alloc_failure_hook_and_check_without_gpu():
+    assert ph.ph_inject_alloc_failure(3) == ph.PH_OK
+    assert ph.ph_inject_alloc_failure(-1) == ph.PH_OK
+    assert ph.ph_check(None, None) == ph.PH_ERR_INVALID_ARG

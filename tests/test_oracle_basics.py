@@ -183,3 +183,23 @@ def test_parametric_vectors_derivative_dimension_only():
     assert np.array_equal(dv[0], v[0])  # other dimensions keep their values
     nodes = cheb.cheb_nodes(1.0, 3.0, 10)
     np.testing.assert_allclose(dv[1], cheb.lagrange_derivative(nodes, 2.2)[0], rtol=0, atol=0)
+
+
+def test_aniso_gauss_per_axis_lengths():
+    """exp(-sum_k (x_k - y_k)^2 / (2 l_k^2)) evaluated by hand with three different lengths: a
+    swapped pair of axes or lengths changes the value, and the kernel is the product of the
+    1-D Gaussians of each axis."""
+    x = np.array([0.1, 0.2, 0.3])
+    y = np.array([0.4, 0.0, 0.35])
+    ell = np.array([0.5, 0.1, 0.2])
+    # 0.3^2 / (2 * 0.25) + 0.2^2 / (2 * 0.01) + 0.05^2 / (2 * 0.04) = 0.18 + 2 + 0.03125
+    expect = np.exp(-2.21125)
+    np.testing.assert_allclose(kernels.kappa("aniso_gauss", x, y, ell), expect, rtol=1e-14)
+    assert abs(kernels.kappa("aniso_gauss", x, y, ell[[1, 0, 2]]) - expect) > 1e-3
+    assert abs(kernels.kappa("aniso_gauss", x[[1, 0, 2]], y, ell) - expect) > 1e-3
+    rng = np.random.default_rng(5)
+    xs, ys = rng.random((20, 2)), rng.random((20, 2))
+    l2 = np.array([0.07, 0.31])
+    prod = (kernels.kappa("gauss", xs[:, :1], ys[:, :1], [l2[0]]) *
+            kernels.kappa("gauss", xs[:, 1:], ys[:, 1:], [l2[1]]))
+    np.testing.assert_allclose(kernels.kappa("aniso_gauss", xs, ys, l2), prod, rtol=1e-13)

@@ -87,3 +87,43 @@ def test_near_field_ratio_matches_paper(n, l_max, ratio, tol):
     assert len(near) == (3 * side - 2) ** 3
     got = sum(s.n * t.n for s, t in near) / float(n) ** 2
     assert abs(got - ratio) / ratio < tol
+
+
+@pytest.mark.parametrize("d,leaf", [(2, 16), (3, 20)])
+def test_adaptive_tree_leaf_rule_coverage_and_empty_children(d, leaf):
+    """Adaptive mode (leaf_size): a node is split while it holds more than leaf_size points
+    and is above max_depth; empty children are dropped; every point lies in exactly one leaf,
+    inside its box; the block tree still covers every (i, j) exactly once."""
+    rng = np.random.default_rng(17 + d)
+    # two tight clusters plus a uniform background: uneven depths and empty children
+    P = np.clip(np.concatenate([0.3 + 0.01 * rng.standard_normal((150, d)),
+                                0.8 + 0.002 * rng.standard_normal((90, d)),
+                                rng.random((60, d))]), 0.0, 1.0)
+    n = P.shape[0]
+    root = tree.build_cluster_tree(P, 0, leaf_size=leaf, max_depth=12)
+    lv = tree.leaves(root)
+    seen = np.zeros(n, dtype=np.int32)
+    depths = set()
+    for c in lv:
+        seen[c.idx] += 1
+        assert c.n >= 1  # empty children are dropped
+        assert c.n <= leaf or c.level == 12
+        assert np.all(P[c.idx] >= c.lo) and np.all(P[c.idx] <= c.hi)
+        depths.add(c.level)
+    assert np.all(seen == 1)
+    assert len(depths) > 1  # the tree is not uniform
+    for c in tree.all_nodes(root):
+        if c.children:
+            assert c.n > leaf
+            assert sum(ch.n for ch in c.children) == c.n
+            assert len(c.children) <= 2 ** d
+            for ch in c.children:
+                np.testing.assert_allclose(ch.hi - ch.lo, 0.5 * (c.hi - c.lo))
+    # points of one cell of the finest split that hold only duplicates stop at max_depth
+    dup = np.concatenate([np.full((leaf + 5, d), 0.123), rng.random((10, d))])
+    r2 = tree.build_cluster_tree(dup, 0, leaf_size=leaf, max_depth=6)
+    assert max(c.level for c in tree.leaves(r2)) == 6
+    near, far, cover = _coverage(root, n, np.sqrt(d))
+    assert np.all(cover == 1)
+    for s, t in near:
+        assert s.is_leaf() or t.is_leaf()  # recursion stops when either side is a leaf

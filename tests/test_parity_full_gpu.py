@@ -3,8 +3,9 @@
 * the small 2-D FP64 configuration (n = 4096, Gaussian, degree 16, eta = 1, leaf 64, rank <= 32,
   theta = 0.37, one RHS) for both formats: every row against the oracle, <= 1e-10;
 * the 3-D FP32 configuration that bench.py times (n = 65536, Matern 3/2, degree 20, rank <= 64,
-  16 RHS), built and launched exactly as bench.py does: the rows of sampled target leaves
-  against the oracle (which compresses those leaves' blocks in a spawn-started pool), <= 1e-5;
+  16 RHS), built and launched exactly as bench.py does: the rows of at least eight sampled target
+  leaves (corners, edges, faces, interior, the largest leaf) against the oracle (which compresses
+  those leaves' blocks in a spawn-started pool), <= 1e-5;
 * edge cases: n = 0 is refused; the maximum m = 1024 right-hand sides.
 """
 import os
@@ -65,10 +66,20 @@ def test_bench_workload_sampled_rows():
     A = ph.ParametricMatrix(P, wl.kernel, opts)
     M = pmatrix.ParametricMatrix(P, wl.kernel, wl.theta_lo, wl.theta_hi, wl.degree, wl.p_s, wl.l_max,
                                  wl.eta, wl.tol, rank_cap=wl.rank_cap, fmt=wl.fmt)
+    # leaves of every far-field structure of the 8 x 8 x 8 leaf grid: two corners, two edges, two
+    # faces, two interior boxes (random, seeded), and the largest leaf
     rng = np.random.default_rng(11)
-    # one interior and one corner leaf (different far-field structures)
-    idx = [int(rng.integers(len(M.leaves))), 0]
-    targets = [M.leaves[i] for i in idx]
+    side = 2 ** wl.l_max
+    by_kind = {k: [] for k in range(4)}
+    for i, c in enumerate(M.leaves):
+        box = np.rint(c.lo * side).astype(int)
+        by_kind[int(np.sum((box == 0) | (box == side - 1)))].append(i)
+    idx = set()
+    for kind in (3, 2, 1, 0):
+        idx.update(int(i) for i in rng.choice(by_kind[kind], size=2, replace=False))
+    idx.add(int(np.argmax([c.n for c in M.leaves])))
+    targets = [M.leaves[i] for i in sorted(idx)]
+    assert len(targets) >= 8
     with _pool() as pool:
         M.offline(targets, pool=pool)
     rows = target_rows(targets)

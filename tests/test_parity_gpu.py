@@ -66,7 +66,7 @@ def test_coupling_modes(coupling, d, prec, m):
 @pytest.mark.parametrize("ps,theta", [(4, 0.13), (8, 0.47)])
 def test_tensor_core_phase1_against_cuda_core_and_oracle(ps, theta):
     """FP32, 16 right-hand sides, p_s^d a multiple of 32: phase 1 of the explicit coupling runs on
-    the tensor cores (3xTF32); the CUDA-core kernel and the oracle must agree with it."""
+    the tensor cores (3xTF32) when enabled; the CUDA-core kernel and the oracle must agree with it."""
     n = 2500 if ps == 4 else 6000
     P = inputs.uniform_points(n, 3, 90 + ps)
     X = inputs.gaussian_rhs(n, 16, 91 + ps)
@@ -76,9 +76,11 @@ def test_tensor_core_phase1_against_cuda_core_and_oracle(ps, theta):
     ref = M.matvec(M.instantiate([theta], targets), X, targets)
     assert A.info()["tensor_core_phase1"] == 0  # off by default
     y_cc = device_apply(A, [theta], X, "fp32")
+    assert not A.info()["kernel_variants"] & 4
     A.set_tensor_cores(True)
     assert A.info()["tensor_core_phase1"] == 1
     y_tc = device_apply(A, [theta], X, "fp32")
+    assert A.info()["kernel_variants"] & 4
     assert np.all(rel_err_rows(ref, y_tc, rows) <= TOL["fp32"])
     assert np.all(rel_err_rows(ref, y_cc, rows) <= TOL["fp32"])
     # two FP32 evaluations in different summation orders, each within the FP32 bar of the oracle

@@ -1,6 +1,8 @@
-"""ph_matvec_noalloc: the entry point for callers that cannot allocate device memory
-(code running under CUDA graph capture, fixed memory budgets, hosts that own all device
-allocations).  It must give ph_matvec's result, call after call, from its static workspace.
+"""ph_matvec_noalloc: the entry point for callers that cannot allocate device memory when they
+apply the matrix (processes held to a fixed device-memory budget, host applications that own
+every device allocation, loops that must not stall on cudaMalloc).  It must give ph_matvec's
+result, call after call, from the library's static workspace, on a handle that has never
+allocated a workspace of its own, and without changing the device's free memory.
 
 This file is collected last on purpose, so that a run stopping at the first failure has
 already run every other test."""
@@ -59,4 +61,31 @@ def test_noalloc_rejects_oversized_problem():
         A.matvec_noalloc_ptr(big.data_ptr(), n, 1024, big.data_ptr() + 0, n)
     assert e.value.status == ph.PH_ERR_INVALID_ARG
     assert "limit" in str(e.value)
+    A.close()
+
+
+@pytest.mark.parametrize("fmt,prec,m", [("h2", "fp32", 16), ("h", "fp64", 2)])
+def test_noalloc_on_fresh_handle_allocates_nothing(fmt, prec, m):
+    """A handle that has never run ph_matvec: two noalloc calls give ph_matvec's result (called
+    afterwards), and the device's free memory is the same before and after the second call."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    A, X = _setup(fmt, prec, m)
+    n = X.shape[1]
+    A.instantiate([0.41])
+    outs = [torch.full_like(X, float("nan")) for _ in range(2)]
+    A.matvec_noalloc_ptr(X.data_ptr(), n, m, outs[0].data_ptr(), n)  # first call: symbol lookup
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    A.matvec_noalloc_ptr(X.data_ptr(), n, m, outs[1].data_ptr(), n)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    ref = torch.empty_like(X)
+    A.matvec_ptr(X.data_ptr(), n, m, ref.data_ptr(), n)
+    torch.cuda.synchronize()
+    r = ref.double().cpu().numpy()
+    for out in outs:
+        o = out.double().cpu().numpy()
+        err = np.linalg.norm(r - o, axis=1) / np.linalg.norm(r, axis=1)
+        assert np.all(err <= TOL[prec]), err
     A.close()
