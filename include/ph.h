@@ -61,7 +61,8 @@ typedef enum {
     PH_KERNEL_EXPONENTIAL = 5,  /* exp(-r/l)                                                    */
     PH_KERNEL_MULTIQUADRIC = 6, /* (1 + (r/l)^2)^(1/2)                                          */
     PH_KERNEL_POLY = 7,         /* 1 + theta r^2 + theta^2 r^4                                  */
-    PH_KERNEL_POLYXY = 8        /* (1 + x.y)^2 (1 + theta); not translation-invariant           */
+    PH_KERNEL_POLYXY = 8,       /* (1 + x.y)^2 (1 + theta); not translation-invariant           */
+    PH_KERNEL_POLY2 = 9         /* 1 + theta_1 r^2 + theta_2^2 r^4,         theta = (th_1, th_2) */
 } ph_kernel;
 
 typedef enum { PH_FMT_H2 = 0, PH_FMT_H = 1 } ph_format;       /* Definitions of §4.1 */
@@ -71,7 +72,8 @@ typedef enum { PH_FP64 = 0, PH_FP32 = 1 } ph_precision;       /* stored cores an
  * "... H^2-matrix", §4.4).  Fixed-size arrays keep the struct plain. */
 typedef struct {
     int d;                 /* spatial dimension, 1..3 */
-    int dtheta;            /* parameter dimension; the offline build implements 1 (PH_ERR_UNSUPPORTED else) */
+    int dtheta;            /* parameter dimension 1..3; the tensor grid has prod_i (degree_i + 1) <= 1024 points,
+                              and with d_theta > 1 the far ranks around the parameter cores must be <= 64 */
     double theta_lo[3];    /* parameter box B_theta = prod [theta_lo_i, theta_hi_i] */
     double theta_hi[3];
     int degree[3];         /* Chebyshev degree in theta_i; p_theta_i = degree_i + 1 nodes (§2.2) */

@@ -16,6 +16,8 @@ trailing axis of length d_theta; the leading axes broadcast against each other.
               each coordinate and 2 in theta, translation-invariant)
 * polyxy      (1 + x.y)^2 (1 + theta)     (test kernel that is NOT
               translation-invariant)
+* poly2       1 + theta_1 r^2 + theta_2^2 r^4 (two-parameter test kernel: degree 4 in each
+              coordinate, 1 in theta_1 and 2 in theta_2, translation-invariant)
 
 Pins (tests/test_oracle_basics.py): the Matern closed forms against the
 general Matern formula with SciPy's Bessel K_nu at nu = 3/2 and 5/2; r = 0
@@ -27,7 +29,7 @@ import numpy as np
 
 TRANSLATION_INVARIANT = {
     "gauss": True, "matern32": True, "matern52": True, "aniso_gauss": True,
-    "se": True, "exponential": True, "mc": True, "poly": True, "polyxy": False,
+    "se": True, "exponential": True, "mc": True, "poly": True, "polyxy": False, "poly2": True,
 }
 
 
@@ -61,6 +63,9 @@ def kappa(name: str, x, y, theta):
     if name == "poly":
         r2 = r * r
         return 1.0 + t0 * r2 + t0 * t0 * r2 * r2
+    if name == "poly2":
+        r2 = r * r
+        return 1.0 + theta[..., 0] * r2 + theta[..., 1] ** 2 * r2 * r2
     if name == "polyxy":
         dot = np.sum(np.asarray(x, float) * np.asarray(y, float), axis=-1)
         return (1.0 + dot) ** 2 * (1.0 + t0)

@@ -14,9 +14,13 @@ this one.  Truncation rule (stated once, used for every core):
 * delta = eps * ||A||_F / sqrt(q - 1) for a q-way tensor A;
 * at each cut keep the smallest rank r >= 1 whose discarded tail satisfies
   sum_{i > r} s_i^2 <= delta^2;
-* then r = min(r, rank_cap);
-* ties: while r < min(len(s), rank_cap) and s_r - s_{r+1} <= 1e-9 * s_1, keep
-  one more value, so that a numerically tied group is kept whole.
+* ties: while r < len(s) and s_r - s_{r+1} <= 1e-9 * s_1, keep one more value, so
+  that a numerically tied group is kept whole;
+* then the cap: if r > rank_cap, r = rank_cap, and if that splits a tied group
+  (s_r - s_{r+1} <= 1e-9 * s_1) the whole group is dropped (r decreases while the
+  cut still separates tied values).  A truncation that split a group of equal
+  singular values would keep an arbitrary subspace of it, and no two
+  implementations would agree; this keeps the truncated TT unique.
 
 Pins (tests/test_oracle_basics.py): reconstruction error <= eps ||A||_F;
 exactness on tensors of known low TT rank; the 2-way case equals the
@@ -76,10 +80,14 @@ def truncation_rank(s: np.ndarray, delta: float, rank_cap=None) -> int:
         if tail[k] <= delta * delta:
             r = k
             break
-    r = max(1, min(r, cap))
-    if n and s[0] > 0:
-        while r < cap and s[r - 1] - s[r] <= TIE_REL * s[0]:
-            r += 1
+    r = max(1, r)
+    tied = lambda k: n and s[0] > 0 and k < n and s[k - 1] - s[k] <= TIE_REL * s[0]
+    while tied(r):
+        r += 1
+    if r > cap:
+        r = cap
+        while r > 1 and tied(r):
+            r -= 1
     return r
 
 

@@ -64,7 +64,7 @@ def build(verbose: bool = False) -> str:
     libdir = _cuda_lib()
     tmp = LIB + ".tmp"
     cmd = [_nvcc(), "-shared", *ARCH, "-o", tmp, *objs, "-cudart", "shared", "-L", libdir,
-           "-lcublas", "-lcusolver", "-ldl", "-Xlinker", "-rpath=" + libdir]  # -ldl: NVTX loads its tool
+           "-lcublas", "-lcusolver", "-ldl", "-lpthread", "-Xlinker", "-rpath=" + libdir]  # -ldl: NVTX loads its tool
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

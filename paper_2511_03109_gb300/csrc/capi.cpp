@@ -289,10 +289,10 @@ void refresh_views(ph_handle* h) {
     for (int k = 0; k < nkeys; ++k) {
         h->zstride = std::max(h->zstride, h->key_ranks[(size_t)k * (h->Delta + 1) + plan.d]);
         h->rank_max_lr = std::max(h->rank_max_lr, std::max(h->key_ranks[(size_t)k * (h->Delta + 1) + plan.d],
-                                                           h->key_ranks[(size_t)k * (h->Delta + 1) + plan.d + 1]));
+                                                           h->key_ranks[(size_t)k * (h->Delta + 1) + plan.d + h->opts.dtheta]));
         // blocks per item: about 8192 outputs of P = R_k^T X per CTA at 16 right-hand sides
         // (256 threads with tiles of 4 x 8)
-        const int rp4 = (h->key_ranks[(size_t)k * (h->Delta + 1) + plan.d + 1] + 3) & ~3;
+        const int rp4 = (h->key_ranks[(size_t)k * (h->Delta + 1) + plan.d + h->opts.dtheta] + 3) & ~3;
         const int nb = std::max(1, std::min(kCouplingItemBlocks, 512 / std::max(4, rp4)));
         for (int i = h->kb_off[k]; i < h->kb_off[k + 1]; i += nb) {
             h->citem_key.push_back(k);
@@ -448,10 +448,14 @@ ph_status ph_offline_build(const double* points, long n, ph_kernel kernel, const
     if (o->d < 1 || o->d > 3 || o->dtheta < 1 || o->dtheta > 3 || o->p_s < 1 || o->p_s > ph::kMaxPs ||
         o->l_max < 0 || o->l_max > 10 || !(o->eta > 0) || !(o->tol >= 0) || o->rank_cap < 0 ||
         (o->fmt != PH_FMT_H && o->fmt != PH_FMT_H2) || (o->prec != PH_FP32 && o->prec != PH_FP64) ||
-        (int)kernel < 0 || (int)kernel > PH_KERNEL_POLYXY)
+        (int)kernel < 0 || (int)kernel > PH_KERNEL_POLY2)
         return fail(nullptr, PH_ERR_INVALID_ARG, "ph_offline_build: option out of range");
     if (kernel == PH_KERNEL_ANISO_GAUSS && o->dtheta != o->d)
         return fail(nullptr, PH_ERR_INVALID_ARG, "anisotropic Gaussian needs d_theta = d");
+    if (kernel == PH_KERNEL_POLY2 && o->dtheta != 2)
+        return fail(nullptr, PH_ERR_INVALID_ARG, "the two-parameter polynomial kernel needs d_theta = 2");
+    if (kernel != PH_KERNEL_ANISO_GAUSS && kernel != PH_KERNEL_POLY2 && o->dtheta != 1)
+        return fail(nullptr, PH_ERR_INVALID_ARG, "this kernel has one parameter (d_theta = 1)");
     for (int k = 0; k < o->dtheta; ++k)
         if (!(o->theta_lo[k] < o->theta_hi[k]) || o->degree[k] < 0 || o->degree[k] + 1 > ph::kMaxPTheta)
             return fail(nullptr, PH_ERR_INVALID_ARG, "ph_offline_build: bad parameter box or degree");
@@ -659,14 +663,14 @@ ph_status ph_get_info(const ph_handle* h, ph_info* info) {
     for (size_t b = 0; b < plan.near_s.size(); ++b)
         fl += 2.0 * h->nb_rank[b] * (double)plan.nodes[plan.near_s[b]].size() * plan.nodes[plan.near_t[b]].size() /
               16.0;  // forming d_ij, shared by 16 right-hand sides in a chunk
-    const int p = h->opts.p_s, PD = h->PD;
+    const int p = h->opts.p_s, PD = h->PD, dt = h->opts.dtheta;
     for (size_t b = 0; b < plan.far_s.size(); ++b) {
         const int* rk = &h->key_ranks[(size_t)plan.far_key[b] * (D + 1)];
         if (h->opts.fmt == PH_FMT_H) {
             fl += 2.0 * (plan.nodes[plan.far_s[b]].size() * (double)rk[d] +
-                         plan.nodes[plan.far_t[b]].size() * (double)rk[d + 1] + (double)rk[d] * rk[d + 1]);
+                         plan.nodes[plan.far_t[b]].size() * (double)rk[d + dt] + (double)rk[d] * rk[d + dt]);
         } else if (h->opts.coupling == 0) {
-            const double fa = 2.0 * PD * rk[d + 1] + 2.0 * rk[d] * rk[d + 1], fbb = 2.0 * PD * rk[d];
+            const double fa = 2.0 * PD * rk[d + dt] + 2.0 * rk[d] * rk[d + dt], fbb = 2.0 * PD * rk[d];
             r.coupling_a_flops_per_rhs += fa;
             r.coupling_b_flops_per_rhs += fbb;
             fl += fa + fbb;
@@ -677,7 +681,7 @@ ph_status ph_get_info(const ph_handle* h, ph_info* info) {
                 chain += 2.0 * a * rk[core] * p * rk[core + 1];
                 a /= p;
             }
-            chain += 2.0 * rk[d] * rk[d + 1];
+            chain += 2.0 * rk[d] * rk[d + dt];
             double bsz = 1;
             for (int i = 0; i < d; ++i) {  // left cores
                 int core = d - 1 - i;

@@ -228,6 +228,16 @@ void set_alloc_failure(long after);
 void post_timeout_flag(ph_handle* h, cudaStream_t stream);
 // PH_ERR_TIMEOUT (once) when a bounded device wait of an earlier call ran out, else PH_OK.
 ph_status take_timeout(ph_handle* h);
+// TT-SVD truncation rank at one cut (offline.cu): smallest r >= 1 whose discarded tail is at
+// most delta2, then the cap (0: none), then numerically tied singular values kept together.
+int choose_rank_sv(const double* s, int n, double delta2, int cap);
+// Host FP64 thin SVD of a small m x n column-major matrix, s descending (ttsvd_host.cpp).
+void svd_small(int m, int n, const std::vector<double>& A, std::vector<double>& U, std::vector<double>& s,
+               std::vector<double>& Vt);
+// The r x P matrix that turns the tensor product of the parametric vectors into the near weights
+// w_b, from the first TT cut (s, V_r) and the remaining cuts (ttsvd_host.cpp).
+std::vector<double> near_theta_matrix(const double* s, const double* Vr, int P, int r, const int* pt, int dt,
+                                      double delta2);
 // Checks every offset, index and size the kernels rely on (ph_load refuses a file that fails,
 // ph_offline_build checks what it built); throws ph::Error(PH_ERR_IO) with the first violation.
 void validate_handle(const ph_handle& h, const std::vector<size_t>& arena_bytes);

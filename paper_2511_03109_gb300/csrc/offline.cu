@@ -24,6 +24,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <thread>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -84,6 +85,7 @@ __device__ __forceinline__ double kappa64(int kernel, const double* x, const dou
         case PH_KERNEL_EXPONENTIAL: return exp(-sqrt(r2) / l);
         case PH_KERNEL_MULTIQUADRIC: return sqrt(1.0 + r2 / (l * l));
         case PH_KERNEL_POLY: return 1.0 + l * r2 + l * l * r2 * r2;
+        case PH_KERNEL_POLY2: return 1.0 + th[0] * r2 + th[1] * th[1] * r2 * r2;
         case PH_KERNEL_POLYXY: {
             double dot = 0.0;
             for (int k = 0; k < d; ++k) dot += x[k] * y[k];
@@ -105,11 +107,11 @@ struct NearBuild {
 
 constexpr int kChunk = 256;
 
-// Fills A[row][k] for rows q0 .. q0 + kChunk - 1 of block b into shared memory.
-__device__ void eval_near_chunk(const NearBuild& a, int b, long long q0, long long nq, double* A) {
+// Fills A[row][k] for rows q0 .. q0 + chunk - 1 of block b into shared memory.
+__device__ void eval_near_chunk(const NearBuild& a, int b, long long q0, long long nq, double* A, int chunk = kChunk) {
     const int ns = a.s_n[b];
     const int sb = a.s_begin[b], tb = a.t_begin[b];
-    for (int row = threadIdx.x; row < kChunk; row += blockDim.x) {
+    for (int row = threadIdx.x; row < chunk; row += blockDim.x) {
         long long q = q0 + row;
         if (q < nq) {
             int i = (int)(q % ns), j = (int)(q / ns);  // (i, j) little-endian, i fastest (§4.3)
@@ -129,20 +131,20 @@ __device__ void eval_near_chunk(const NearBuild& a, int b, long long q0, long lo
 // the rows of A_b are generated in chunks and folded in by Householder QR of the stacked
 // matrix [R; A_chunk] (LAPACK dlarfg convention).  Only R is kept: the right singular
 // vectors and singular values of A_b are those of R_b.
-__global__ void near_tsqr_kernel(NearBuild a, double* Rout) {
+__global__ void near_tsqr_kernel(NearBuild a, double* Rout, int chunk) {
     extern __shared__ double sm[];
-    const int P = a.P, LD = P + kChunk;
+    const int P = a.P, LD = P + chunk;
     double* W = sm;                 // LD x P, column-major: rows 0..P-1 hold R, rows P.. the chunk
-    double* A = sm + (size_t)LD * P; // kChunk x P row-major scratch for the evaluation
+    double* A = sm + (size_t)LD * P; // chunk x P row-major scratch for the evaluation
     const int b = blockIdx.x;
     const long long nq = (long long)a.s_n[b] * a.t_n[b];
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nwarps = blockDim.x / 32;
     for (int e = threadIdx.x; e < P * P; e += blockDim.x) W[(e % P) + LD * (e / P)] = 0.0;
-    for (long long q0 = 0; q0 < nq; q0 += kChunk) {
+    for (long long q0 = 0; q0 < nq; q0 += chunk) {
         __syncthreads();
-        eval_near_chunk(a, b, q0, nq, A);
+        eval_near_chunk(a, b, q0, nq, A, chunk);
         __syncthreads();
-        for (int e = threadIdx.x; e < kChunk * P; e += blockDim.x) {
+        for (int e = threadIdx.x; e < chunk * P; e += blockDim.x) {
             const int row = e / P, k = e % P;
             W[P + row + LD * k] = A[e];
         }
@@ -150,7 +152,7 @@ __global__ void near_tsqr_kernel(NearBuild a, double* Rout) {
         for (int k = 0; k < P; ++k) {
             // every warp recomputes the reflector of column k (column k is read-only in this step)
             double x2 = 0.0;
-            for (int row = lane; row < kChunk; row += 32) {
+            for (int row = lane; row < chunk; row += 32) {
                 double x = W[P + row + LD * k];
                 x2 += x * x;
             }
@@ -162,11 +164,11 @@ __global__ void near_tsqr_kernel(NearBuild a, double* Rout) {
                 const double scale = 1.0 / (alpha - beta);
                 for (int j = k + 1 + warp; j < P; j += nwarps) {
                     double w = 0.0;
-                    for (int row = lane; row < kChunk; row += 32) w += W[P + row + LD * k] * scale * W[P + row + LD * j];
+                    for (int row = lane; row < chunk; row += 32) w += W[P + row + LD * k] * scale * W[P + row + LD * j];
                     for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
                     w += W[k + LD * j];
                     const double tw = tau * w;
-                    for (int row = lane; row < kChunk; row += 32)
+                    for (int row = lane; row < chunk; row += 32)
                         W[P + row + LD * j] -= tw * W[P + row + LD * k] * scale;
                     if (lane == 0) W[k + LD * j] -= tw;
                 }
@@ -184,25 +186,26 @@ __global__ void near_tsqr_kernel(NearBuild a, double* Rout) {
 }
 
 // G_{b,1} = A_b V_r in compute type T, stored column-interleaved: entry (i, j) of slab c at
-// [(j r + c) n_s + i], so that one column j of all r slabs is one contiguous run.
+// [(j r + c) n_s + i], so that one column j of all r slabs is one contiguous run.  V_r of block
+// b (P x r_b, column-major) at vecs + voff[b]; rows of A_b generated `chunk` at a time.
 template <typename T>
-__global__ void near_project_kernel(NearBuild a, const double* vecs, const int* rank,
-                                    const long long* off, T* out) {
+__global__ void near_project_kernel(NearBuild a, const double* vecs, const long long* voff, const int* rank,
+                                    const long long* off, T* out, int chunk) {
     extern __shared__ double sA[];
-    double* sV = sA + kChunk * a.P;  // P x r_b, column-major
+    double* sV = sA + (size_t)chunk * a.P;  // P x r_b, column-major
     const int b = blockIdx.x;
     const int r = rank[b];
     const long long nq = (long long)a.s_n[b] * a.t_n[b];
-    const double* V = vecs + (long long)b * a.P * a.P;  // first r columns: largest singular values
+    const double* V = vecs + voff[b];
     for (int e = threadIdx.x; e < a.P * r; e += blockDim.x) sV[e] = V[e];
     T* G = out + off[b];
-    for (long long q0 = 0; q0 < nq; q0 += kChunk) {
+    for (long long q0 = 0; q0 < nq; q0 += chunk) {
         __syncthreads();
-        eval_near_chunk(a, b, q0, nq, sA);
+        eval_near_chunk(a, b, q0, nq, sA, chunk);
         __syncthreads();
         const int ns = a.s_n[b];
-        for (int e = threadIdx.x; e < kChunk * r; e += blockDim.x) {
-            int row = e % kChunk, c = e / kChunk;
+        for (int e = threadIdx.x; e < chunk * r; e += blockDim.x) {
+            int row = e % chunk, c = e / chunk;
             long long q = q0 + row;
             if (q < nq) {
                 double s = 0.0;
@@ -211,6 +214,32 @@ __global__ void near_project_kernel(NearBuild a, const double* vecs, const int* 
                 G[(j * r + c) * ns + i] = (T)s;  // column-interleaved: (j, slab c, i)
             }
         }
+    }
+}
+
+// A_b of the near blocks b0 .. b0 + nb - 1, each as a maxrows x P column-major matrix (rows
+// (i, j) little-endian, i fastest, §4.3; rows past n_s n_t are zero, so A_b^T A_b is unchanged).
+__global__ void near_form_kernel(NearBuild a, int b0, int nb, long long maxrows, double* out) {
+    const long long total = (long long)nb * maxrows;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int bi = (int)(e / maxrows);
+        const long long q = e % maxrows;
+        const int b = b0 + bi;
+        const int ns = a.s_n[b];
+        const long long nq = (long long)ns * a.t_n[b];
+        double* col = out + (long long)bi * maxrows * a.P + q;
+        if (q >= nq) {
+            for (int k = 0; k < a.P; ++k) col[maxrows * k] = 0.0;
+            continue;
+        }
+        const int i = (int)(q % ns), j = (int)(q / ns);
+        double x[kMaxDim], y[kMaxDim];
+        for (int k = 0; k < a.d; ++k) {
+            x[k] = a.pts[(long long)(a.s_begin[b] + i) * a.d + k];
+            y[k] = a.pts[(long long)(a.t_begin[b] + j) * a.d + k];
+        }
+        for (int k = 0; k < a.P; ++k) col[maxrows * k] = kappa64(a.kernel, x, y, a.grid + k * a.dt, a.d);
     }
 }
 
@@ -238,24 +267,6 @@ __global__ void far_tensor_kernel(int kernel, int d, int dt, int ps, const int* 
     }
 }
 
-// Rank kept at a TT-SVD cut from the singular values s[0] >= s[1] >= ... >= s[n-1]:
-// the smallest r >= 1 whose discarded tail sum_{i>r} s_i^2 <= delta2, then the cap,
-// then numerically tied singular values (s_r - s_{r+1} <= 1e-9 s_1) are kept together.
-int choose_rank_sv(const double* s, int n, double delta2, int cap) {
-    std::vector<double> tail(n + 1, 0.0);
-    for (int i = n - 1; i >= 0; --i) tail[i] = tail[i + 1] + s[i] * s[i];
-    int lim = (cap > 0) ? std::min(n, cap) : n;
-    int r = n;
-    for (int k = 1; k <= n; ++k)
-        if (tail[k] <= delta2) {
-            r = k;
-            break;
-        }
-    r = std::max(1, std::min(r, lim));
-    if (n > 0 && s[0] > 0)
-        while (r < lim && s[r - 1] - s[r] <= kTieRel * s[0]) ++r;
-    return r;
-}
 
 // Copies the upper triangle of the first n rows of T (ld m) into R (n x n), zeros below.
 __global__ void copy_upper_kernel(const double* T, long long m, int n, double* R) {
@@ -408,6 +419,32 @@ V* upload_vec(ph_handle* h, const std::vector<V>& v) {
 
 }  // namespace
 
+// Rank kept at a TT-SVD cut from the singular values s[0] >= s[1] >= ... >= s[n-1]:
+// the smallest r >= 1 whose discarded tail sum_{i>r} s_i^2 <= delta2, extended over numerically
+// tied singular values (s_r - s_{r+1} <= 1e-9 s_1), then the cap, backed off below a tied group
+// the cap would split.
+int choose_rank_sv(const double* s, int n, double delta2, int cap) {
+    std::vector<double> tail(n + 1, 0.0);
+    for (int i = n - 1; i >= 0; --i) tail[i] = tail[i + 1] + s[i] * s[i];
+    const int lim = (cap > 0) ? std::min(n, cap) : n;
+    int r = n;
+    for (int k = 1; k <= n; ++k)
+        if (tail[k] <= delta2) {
+            r = k;
+            break;
+        }
+    r = std::max(1, r);
+    // a cut between tied singular values keeps an arbitrary part of their subspace: keep the whole
+    // group, and if the cap then cuts through a group, drop that group instead
+    auto tied = [&](int k) { return n > 0 && s[0] > 0 && k < n && s[k - 1] - s[k] <= kTieRel * s[0]; };
+    while (tied(r)) ++r;
+    if (r > lim) {
+        r = lim;
+        while (r > 1 && tied(r)) --r;
+    }
+    return r;
+}
+
 namespace {
 std::atomic<long> g_alloc_budget{-1};  // successful allocations left before injected failures (< 0: off)
 }  // namespace
@@ -482,9 +519,8 @@ ph_status offline_build(ph_handle* h, const double* points, long n) {
         pt[k] = o.degree[k] + 1;
         h->p_theta_total *= pt[k];
     }
-    if (dt != 1) throw Error(PH_ERR_UNSUPPORTED, "near-field compression implemented for d_theta = 1");
-    const int P = h->p_theta_total;
-    if (P > kMaxPTheta) throw Error(PH_ERR_UNSUPPORTED, "p_theta must be at most 32");
+    const int P = h->p_theta_total;  // theta-grid points (product over the parameter dimensions)
+    if (P > kMaxThetaGrid) throw Error(PH_ERR_UNSUPPORTED, "at most 1024 theta-grid points");
     if (ps < 1 || ps > kMaxPs) throw Error(PH_ERR_INVALID_ARG, "p_s must be 1..16");
 
     // theta nodes and barycentric weights (dtheta x 32)
@@ -526,82 +562,192 @@ ph_status offline_build(ph_handle* h, const double* points, long n) {
     h->nb_woff.assign(nn + 1, 0);
     std::vector<double> near_theta;
     if (nn > 0) {
-        double* d_R = (double*)dev_alloc(h, (size_t)nn * P * P * sizeof(double));
-        double* d_S = (double*)dev_alloc(h, (size_t)nn * P * sizeof(double));
-        double* d_U = (double*)dev_alloc(h, (size_t)nn * P * P * sizeof(double));
-        double* d_V = (double*)dev_alloc(h, (size_t)nn * P * P * sizeof(double));
-        size_t smem = ((size_t)(P + kChunk) * P + (size_t)kChunk * P) * sizeof(double);
-        PH_CUDA(cudaFuncSetAttribute(near_tsqr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        near_tsqr_kernel<<<nn, 256, smem>>>(nbld, d_R);
-        PH_LAUNCH("near_tsqr_kernel");
-        // batched Jacobi SVD of all P x P factors: R_b = U S V^T, S descending
-        struct Solver {  // released on every exit path
-            cusolverDnHandle_t sol = nullptr;
-            gesvdjInfo_t params = nullptr;
-            ~Solver() {
-                if (params) cusolverDnDestroyGesvdjInfo(params);
-                if (sol) cusolverDnDestroy(sol);
-            }
-        } svd;
-        PH_SOLVER(cusolverDnCreate(&svd.sol));
-        PH_SOLVER(cusolverDnCreateGesvdjInfo(&svd.params));
-        cusolverDnHandle_t sol = svd.sol;
-        gesvdjInfo_t params = svd.params;
-        PH_SOLVER(cusolverDnXgesvdjSetTolerance(params, 1e-15));
-        PH_SOLVER(cusolverDnXgesvdjSetMaxSweeps(params, 100));
-        PH_SOLVER(cusolverDnXgesvdjSetSortEig(params, 1));
-        int lwork = 0;
-        PH_SOLVER(cusolverDnDgesvdjBatched_bufferSize(sol, CUSOLVER_EIG_MODE_VECTOR, P, P, d_R, P, d_S, d_U, P,
-                                                      d_V, P, &lwork, params, nn));
-        double* d_work = (double*)dev_alloc(h, (size_t)std::max(lwork, 1) * sizeof(double));
-        int* d_info = (int*)dev_alloc(h, (size_t)nn * sizeof(int));
-        PH_SOLVER(cusolverDnDgesvdjBatched(sol, CUSOLVER_EIG_MODE_VECTOR, P, P, d_R, P, d_S, d_U, P, d_V, P,
-                                           d_work, lwork, d_info, params, nn));
-        std::vector<int> infos(nn);
-        PH_CUDA(cudaMemcpy(infos.data(), d_info, nn * sizeof(int), cudaMemcpyDeviceToHost));
-        for (int b = 0; b < nn; ++b)
-            if (infos[b] != 0) throw Error(PH_ERR_CUDA, "batched Jacobi SVD did not converge");
-        std::vector<double> sv((size_t)nn * P), vecs((size_t)nn * P * P);
-        PH_CUDA(cudaMemcpy(sv.data(), d_S, sv.size() * sizeof(double), cudaMemcpyDeviceToHost));
-        PH_CUDA(cudaMemcpy(vecs.data(), d_V, vecs.size() * sizeof(double), cudaMemcpyDeviceToHost));
         const double ntol = (o.near_tol >= 0) ? o.near_tol : o.tol;
+        // per block, from the first TT cut of A_b (rows x P): the rank r_{b,1}, the theta matrix W
+        // (near_theta_matrix) and V_r (P x r, packed for the projection G_{b,1} = A_b V_r)
+        std::vector<double> vr_pack;
+        std::vector<long long> voff(nn, 0);
         long long off = 0, toff = 0;
-        for (int b = 0; b < nn; ++b) {
-            const double* s = &sv[(size_t)b * P];
+        auto finish_block = [&](int b, const double* s, const double* V) {  // s descending, V P x P
             double fro2 = 0.0;
             for (int k = 0; k < P; ++k) fro2 += s[k] * s[k];
-            int r = choose_rank_sv(s, P, ntol * ntol * fro2 / dt, kMaxNearRank);
+            const double delta2 = ntol * ntol * fro2 / dt;
+            const int r = choose_rank_sv(s, P, delta2, kMaxNearRank);
             h->nb_rank[b] = r;
             h->nb_off[b] = off;
             h->nb_toff[b] = toff;
             h->nb_woff[b + 1] = h->nb_woff[b] + r;
             off += (long long)sn[b] * tn[b] * r;
             toff += (long long)r * P;
-            // G_{b,2} = V_r^T, an r x P x 1 core (Fortran): [c + r t] = V[t, c]
-            const double* V = &vecs[(size_t)b * P * P];
-            near_theta.resize(near_theta.size() + (size_t)r * P, 0.0);
-            double* dst = &near_theta[toff - (long long)r * P];
-            for (int t = 0; t < P; ++t)
-                for (int c = 0; c < r; ++c) dst[c + r * t] = V[(size_t)c * P + t];
+            const std::vector<double> W = near_theta_matrix(s, V, P, r, pt, dt, delta2);
+            near_theta.insert(near_theta.end(), W.begin(), W.end());
+            voff[b] = (long long)vr_pack.size();
+            vr_pack.insert(vr_pack.end(), V, V + (size_t)P * r);
+        };
+        if (P <= 32) {
+            // R_b of every block by TSQR, then a batched Jacobi SVD of the P x P factors
+            double* d_R = (double*)dev_alloc(h, (size_t)nn * P * P * sizeof(double));
+            double* d_S = (double*)dev_alloc(h, (size_t)nn * P * sizeof(double));
+            double* d_U = (double*)dev_alloc(h, (size_t)nn * P * P * sizeof(double));
+            double* d_V = (double*)dev_alloc(h, (size_t)nn * P * P * sizeof(double));
+            size_t smem = ((size_t)(P + kChunk) * P + (size_t)kChunk * P) * sizeof(double);
+            PH_CUDA(cudaFuncSetAttribute(near_tsqr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            near_tsqr_kernel<<<nn, 256, smem>>>(nbld, d_R, kChunk);
+            PH_LAUNCH("near_tsqr_kernel");
+            struct Solver {  // released on every exit path
+                cusolverDnHandle_t sol = nullptr;
+                gesvdjInfo_t params = nullptr;
+                ~Solver() {
+                    if (params) cusolverDnDestroyGesvdjInfo(params);
+                    if (sol) cusolverDnDestroy(sol);
+                }
+            } svd;
+            PH_SOLVER(cusolverDnCreate(&svd.sol));
+            PH_SOLVER(cusolverDnCreateGesvdjInfo(&svd.params));
+            cusolverDnHandle_t sol = svd.sol;
+            gesvdjInfo_t params = svd.params;
+            PH_SOLVER(cusolverDnXgesvdjSetTolerance(params, 1e-15));
+            PH_SOLVER(cusolverDnXgesvdjSetMaxSweeps(params, 100));
+            PH_SOLVER(cusolverDnXgesvdjSetSortEig(params, 1));
+            int lwork = 0;
+            PH_SOLVER(cusolverDnDgesvdjBatched_bufferSize(sol, CUSOLVER_EIG_MODE_VECTOR, P, P, d_R, P, d_S, d_U, P,
+                                                          d_V, P, &lwork, params, nn));
+            double* d_work = (double*)dev_alloc(h, (size_t)std::max(lwork, 1) * sizeof(double));
+            int* d_info = (int*)dev_alloc(h, (size_t)nn * sizeof(int));
+            PH_SOLVER(cusolverDnDgesvdjBatched(sol, CUSOLVER_EIG_MODE_VECTOR, P, P, d_R, P, d_S, d_U, P, d_V, P,
+                                               d_work, lwork, d_info, params, nn));
+            std::vector<int> infos(nn);
+            PH_CUDA(cudaMemcpy(infos.data(), d_info, nn * sizeof(int), cudaMemcpyDeviceToHost));
+            for (int b = 0; b < nn; ++b)
+                if (infos[b] != 0) throw Error(PH_ERR_CUDA, "batched Jacobi SVD did not converge");
+            std::vector<double> sv((size_t)nn * P), vecs((size_t)nn * P * P);
+            PH_CUDA(cudaMemcpy(sv.data(), d_S, sv.size() * sizeof(double), cudaMemcpyDeviceToHost));
+            PH_CUDA(cudaMemcpy(vecs.data(), d_V, vecs.size() * sizeof(double), cudaMemcpyDeviceToHost));
+            for (int b = 0; b < nn; ++b) finish_block(b, &sv[(size_t)b * P], &vecs[(size_t)b * P * P]);
+            for (void* p : {(void*)d_R, (void*)d_S, (void*)d_U, (void*)d_V, (void*)d_work, (void*)d_info}) dev_free(h, p);
+        } else if (P <= 128) {
+            // 33..128 theta-grid points: R_b by TSQR (row chunks sized to shared memory), then a
+            // one-sided Jacobi SVD of each P x P factor on the host (FP64, one thread per block at a
+            // time), which keeps singular values near the truncation threshold and the kept
+            // subspaces accurate to rounding (so the kept ranks are the oracle's)
+            int chunk = 256;
+            while (chunk > 16 && ((size_t)(P + chunk) * P + (size_t)chunk * P) * sizeof(double) > 200 * 1024) chunk /= 2;
+            const size_t smem = ((size_t)(P + chunk) * P + (size_t)chunk * P) * sizeof(double);
+            double* d_R = (double*)dev_alloc(h, (size_t)nn * P * P * sizeof(double));
+            PH_CUDA(cudaFuncSetAttribute(near_tsqr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            near_tsqr_kernel<<<nn, 256, smem>>>(nbld, d_R, chunk);
+            PH_LAUNCH("near_tsqr_kernel");
+            std::vector<double> Rall((size_t)nn * P * P);
+            PH_CUDA(cudaMemcpy(Rall.data(), d_R, Rall.size() * sizeof(double), cudaMemcpyDeviceToHost));
+            dev_free(h, d_R);
+            std::vector<double> sv((size_t)nn * P), vecs((size_t)nn * P * P);
+            const int nthr = std::max(1, std::min(64, (int)std::thread::hardware_concurrency()));
+            std::vector<std::thread> pool;
+            std::atomic<int> next{0};
+            for (int w = 0; w < nthr; ++w)
+                pool.emplace_back([&]() {
+                    std::vector<double> R((size_t)P * P), U, sg, Vt;
+                    for (int b = next++; b < nn; b = next++) {
+                        std::copy(Rall.begin() + (size_t)b * P * P, Rall.begin() + (size_t)(b + 1) * P * P, R.begin());
+                        svd_small(P, P, R, U, sg, Vt);
+                        for (int k = 0; k < P; ++k) {
+                            sv[(size_t)b * P + k] = sg[k];
+                            for (int t = 0; t < P; ++t) vecs[(size_t)b * P * P + t + (size_t)P * k] = Vt[k + (size_t)P * t];
+                        }
+                    }
+                });
+            for (auto& th : pool) th.join();
+            for (int b = 0; b < nn; ++b) finish_block(b, &sv[(size_t)b * P], &vecs[(size_t)b * P * P]);
+        } else {
+            // more than 128 theta-grid points (the triangular factor no longer fits in shared
+            // memory): the right singular vectors and singular values of A_b come from the
+            // eigendecomposition of A_b^T A_b (FP64, cuSOLVER's batched symmetric eigensolver), in
+            // batches of blocks whose formed A_b take about 2 GB.  Singular values carry an
+            // absolute error of about eps s_1^2 / s, the kept subspace an angle of about
+            // eps s_1^2 / (s_r^2 - s_{r+1}^2): adequate for FP32 handles at tolerances >= 1e-5.
+            long long maxrows = 1;
+            for (int b = 0; b < nn; ++b) maxrows = std::max(maxrows, (long long)sn[b] * tn[b]);
+            const long long per = maxrows * P * (long long)sizeof(double);
+            const int batch = (int)std::max(1LL, std::min((long long)nn, (2LL << 30) / per));
+            double* d_A = (double*)dev_alloc(h, (size_t)batch * per);
+            double* d_G = (double*)dev_alloc(h, (size_t)batch * P * P * sizeof(double));
+            double* d_L = (double*)dev_alloc(h, (size_t)batch * P * sizeof(double));
+            int* d_info = (int*)dev_alloc(h, (size_t)batch * sizeof(int));
+            struct Libs {  // released on every exit path
+                cublasHandle_t blas = nullptr;
+                cusolverDnHandle_t sol = nullptr;
+                cusolverDnParams_t prm = nullptr;
+                ~Libs() {
+                    if (prm) cusolverDnDestroyParams(prm);
+                    if (sol) cusolverDnDestroy(sol);
+                    if (blas) cublasDestroy(blas);
+                }
+            } lib;
+            PH_BLAS(cublasCreate(&lib.blas));
+            PH_SOLVER(cusolverDnCreate(&lib.sol));
+            PH_SOLVER(cusolverDnCreateParams(&lib.prm));
+            size_t wdev = 0, whost = 0;
+            PH_SOLVER(cusolverDnXsyevBatched_bufferSize(lib.sol, lib.prm, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER,
+                                                        P, CUDA_R_64F, d_G, P, CUDA_R_64F, d_L, CUDA_R_64F, &wdev,
+                                                        &whost, batch));
+            void* d_work = dev_alloc(h, std::max<size_t>(wdev, 8));
+            std::vector<unsigned char> h_work(std::max<size_t>(whost, 8));
+            std::vector<double> lam((size_t)batch * P), vec((size_t)batch * P * P), s(P), V((size_t)P * P);
+            std::vector<int> infos(batch);
+            const double one = 1.0, zero = 0.0;
+            for (int b0 = 0; b0 < nn; b0 += batch) {
+                const int nb = std::min(batch, nn - b0);
+                const long long total = (long long)nb * maxrows;
+                near_form_kernel<<<(int)std::min<long long>(ceil_div(total, 256), 65535), 256>>>(nbld, b0, nb, maxrows, d_A);
+                PH_LAUNCH("near_form_kernel");
+                PH_BLAS(cublasDgemmStridedBatched(lib.blas, CUBLAS_OP_T, CUBLAS_OP_N, P, P, (int)maxrows, &one, d_A,
+                                                  (int)maxrows, maxrows * P, d_A, (int)maxrows, maxrows * P, &zero, d_G,
+                                                  P, (long long)P * P, nb));
+                PH_SOLVER(cusolverDnXsyevBatched(lib.sol, lib.prm, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, P,
+                                                 CUDA_R_64F, d_G, P, CUDA_R_64F, d_L, CUDA_R_64F, d_work, wdev,
+                                                 h_work.data(), whost, d_info, nb));
+                PH_CUDA(cudaMemcpy(infos.data(), d_info, nb * sizeof(int), cudaMemcpyDeviceToHost));
+                for (int i = 0; i < nb; ++i)
+                    if (infos[i] != 0) throw Error(PH_ERR_CUDA, "batched symmetric eigensolver failed");
+                PH_CUDA(cudaMemcpy(lam.data(), d_L, (size_t)nb * P * sizeof(double), cudaMemcpyDeviceToHost));
+                PH_CUDA(cudaMemcpy(vec.data(), d_G, (size_t)nb * P * P * sizeof(double), cudaMemcpyDeviceToHost));
+                for (int i = 0; i < nb; ++i) {
+                    // eigenvalues ascending: reverse to singular values descending
+                    for (int k = 0; k < P; ++k) {
+                        const int src = P - 1 - k;
+                        s[k] = std::sqrt(std::max(0.0, lam[(size_t)i * P + src]));
+                        for (int t = 0; t < P; ++t) V[t + (size_t)P * k] = vec[(size_t)i * P * P + t + (size_t)P * src];
+                    }
+                    finish_block(b0 + i, s.data(), V.data());
+                }
+            }
+            for (void* p : {(void*)d_A, (void*)d_G, (void*)d_L, (void*)d_info, d_work}) dev_free(h, p);
         }
         h->near_elems = off;
         h->near_theta_elems = toff;
         h->w_elems = h->nb_woff[nn];
         int* d_rank = upload_vec(h, h->nb_rank);
         long long* d_off = upload_vec(h, h->nb_off);
+        double* d_vr = upload_vec(h, vr_pack);
+        long long* d_voff = upload_vec(h, voff);
         h->d_near = dev_alloc(h, (size_t)off * h->scalar);
-        size_t smem2 = ((size_t)kChunk * P + (size_t)P * P) * sizeof(double);
+        // rows of A_b per projection chunk: shared memory chunk x P + P x r_max doubles within 96 KB
+        const int rmax = *std::max_element(h->nb_rank.begin(), h->nb_rank.end());
+        int chunk = 256;
+        while (chunk > 16 && ((size_t)chunk * P + (size_t)P * rmax) * sizeof(double) > 160 * 1024) chunk /= 2;
+        size_t smem2 = ((size_t)chunk * P + (size_t)P * rmax) * sizeof(double);
         if (o.prec == PH_FP32) {
             PH_CUDA(cudaFuncSetAttribute(near_project_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem2));
-            near_project_kernel<float><<<nn, 256, smem2>>>(nbld, d_V, d_rank, d_off, (float*)h->d_near);
+            near_project_kernel<float><<<nn, 256, smem2>>>(nbld, d_vr, d_voff, d_rank, d_off, (float*)h->d_near, chunk);
         } else {
             PH_CUDA(cudaFuncSetAttribute(near_project_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem2));
-            near_project_kernel<double><<<nn, 256, smem2>>>(nbld, d_V, d_rank, d_off, (double*)h->d_near);
+            near_project_kernel<double><<<nn, 256, smem2>>>(nbld, d_vr, d_voff, d_rank, d_off, (double*)h->d_near, chunk);
         }
         PH_LAUNCH("near_project_kernel");
         PH_CUDA(cudaDeviceSynchronize());
+        for (void* p : {(void*)d_vr, (void*)d_voff}) dev_free(h, p);
     }
     h->d_near_theta = upload_vec(h, near_theta);
 
@@ -657,6 +803,14 @@ ph_status offline_build(ph_handle* h, const double* points, long n) {
             hoff += (long long)ranks[d] * ranks[d + dt];
         }
     }
+    // the online product of the d_theta > 1 parameter cores holds each factor in a 64 x 64 tile
+    if (dt > 1)
+        for (int key = 0; key < nkeys; ++key)
+            for (int i = d; i <= d + dt; ++i)
+                if (h->key_ranks[(size_t)key * (Delta + 1) + i] > 64)
+                    throw Error(PH_ERR_UNSUPPORTED,
+                                "with d_theta > 1 the far-field TT ranks around the parameter cores must be at most 64 "
+                                "(set rank_cap <= 64)");
     // explicit factors per key (coupling mode 0, H^2): L_k^T and R_k^T, both r x PD row-major.
     // L[(i_1..i_k), s_k] = sum L[(i_1..i_{k-1}), s_{k-1}] G_k[s_{k-1}, i_k, s_k] from the left cores;
     // R[(j_1..j_d), s] from the right cores, innermost index first (App. A.4).

@@ -92,16 +92,37 @@ __device__ void parametric_vectors(const double* nodes, const double* bw, const 
                               warp == deriv, out[warp]);
 }
 
+// Online stage for one theta (Alg. "Online Stage", §4.4).  Near block b (CTA < near_ctas, one
+// thread per block): w_b = W_b (v_1 (x) .. (x) v_dtheta), W_b the stored r_{b,1} x P theta matrix
+// (for d_theta = 1 the core G_{b,2} = V_r^T itself; §4.3).  Far class k (one CTA per class):
+// H_k = prod_i G_{k,d+i} x_2 v_i (Alg. PTTK online, App. A.4), for d_theta > 1 as the product of
+// the d_theta matrices M_i = G_{k,d+i} x_2 v_i formed in shared memory (ranks <= 64).
 template <typename T>
 __global__ void instantiate_kernel(DevView<T> v, double th0, double th1, double th2, int near_ctas, int deriv) {
     __shared__ double sv[kMaxDim][kMaxPTheta];
+    __shared__ double vprod[kMaxThetaGrid];
+    extern __shared__ double dsm[];  // far classes with d_theta > 1: three 64 x 64 matrices
     const double th[3] = {th0, th1, th2};
     parametric_vectors(v.theta_nodes, v.theta_bw, v.p_theta, v.dtheta, th, deriv, sv);
     __syncthreads();
-    const int P = v.p_theta[0];
-    if (blockIdx.x == 0 && threadIdx.x < P) v.v64[threadIdx.x] = sv[0][threadIdx.x];
+    const int dt = v.dtheta;
+    if (blockIdx.x == 0)
+        for (int e = threadIdx.x; e < dt * kMaxPTheta; e += blockDim.x)
+            v.v64[e] = ((e % kMaxPTheta) < v.p_theta[e / kMaxPTheta]) ? sv[e / kMaxPTheta][e % kMaxPTheta] : 0.0;
+    int P = 1;
+    for (int i = 0; i < dt; ++i) P *= v.p_theta[i];
     if ((int)blockIdx.x < near_ctas) {
-        // near weights w_b[c] = sum_t G_{b,2}[c, t] v[t]  (d_theta = 1: G_{b,2} is r x P x 1)
+        // tensor-product weights, theta-grid index t = k_1 + p_1 (k_2 + p_2 k_3)
+        for (int t = threadIdx.x; t < P; t += blockDim.x) {
+            double w = 1.0;
+            int rest = t;
+            for (int i = 0; i < dt; ++i) {
+                w *= sv[i][rest % v.p_theta[i]];
+                rest /= v.p_theta[i];
+            }
+            vprod[t] = w;
+        }
+        __syncthreads();
         const int b = blockIdx.x * blockDim.x + threadIdx.x;
         if (b < v.n_near) {
             const int r = v.nb_rank[b];
@@ -109,24 +130,58 @@ __global__ void instantiate_kernel(DevView<T> v, double th0, double th1, double 
             T* w = v.w + v.nb_woff[b];
             for (int c = 0; c < r; ++c) {
                 double s = 0.0;
-                for (int t = 0; t < P; ++t) s += G[c + r * t] * sv[0][t];
+                for (int t = 0; t < P; ++t) s += G[c + r * t] * vprod[t];
                 w[c] = (T)s;
             }
         }
-    } else {
-        // far core matrix H_k = G_{k,d+1} x_2 v  (r_d x r_{d+1}, column-major)
-        const int key = blockIdx.x - near_ctas;
-        const int* rk = v.key_ranks + (size_t)key * (v.Delta + 1);
+        return;
+    }
+    const int key = blockIdx.x - near_ctas;
+    const int* rk = v.key_ranks + (size_t)key * (v.Delta + 1);
+    T* H = v.H + v.key_hoff[key];
+    if (dt == 1) {
+        // H_k = G_{k,d+1} x_2 v  (r_d x r_{d+1}, column-major)
+        const int P0 = v.p_theta[0];
         const int ra = rk[v.d], rb = rk[v.d + 1];
         const double* G = v.far_theta + v.key_off[(size_t)key * v.Delta + v.d];
-        T* H = v.H + v.key_hoff[key];
         for (int e = threadIdx.x; e < ra * rb; e += blockDim.x) {
-            const int a = e % ra, b = e / ra;
+            const int a = e % ra, bb = e / ra;
             double s = 0.0;
-            for (int t = 0; t < P; ++t) s += G[a + ra * (t + P * b)] * sv[0][t];
+            for (int t = 0; t < P0; ++t) s += G[a + ra * (t + P0 * bb)] * sv[0][t];
             H[e] = (T)s;
         }
+        return;
     }
+    double* Tm = dsm;             // running product, column-major, leading dimension 64
+    double* Mi = dsm + 64 * 64;   // M_i
+    double* Tn = dsm + 2 * 64 * 64;
+    const int ra = rk[v.d];
+    int rc = 0;  // columns of the running product
+    for (int i = 0; i < dt; ++i) {
+        const int r0 = rk[v.d + i], r1 = rk[v.d + i + 1], p = v.p_theta[i];
+        const double* G = v.far_theta + v.key_off[(size_t)key * v.Delta + v.d + i];
+        double* dst = (i == 0) ? Tm : Mi;
+        for (int e = threadIdx.x; e < r0 * r1; e += blockDim.x) {
+            const int a = e % r0, bb = e / r0;
+            double s = 0.0;
+            for (int t = 0; t < p; ++t) s += G[a + r0 * (t + p * bb)] * sv[i][t];
+            dst[a + 64 * bb] = s;
+        }
+        __syncthreads();
+        if (i > 0) {
+            for (int e = threadIdx.x; e < ra * r1; e += blockDim.x) {
+                const int a = e % ra, bb = e / ra;
+                double s = 0.0;
+                for (int q = 0; q < r0; ++q) s += Tm[a + 64 * q] * Mi[q + 64 * bb];
+                Tn[a + 64 * bb] = s;
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < ra * r1; e += blockDim.x) Tm[(e % ra) + 64 * (e / ra)] = Tn[(e % ra) + 64 * (e / ra)];
+            __syncthreads();
+        }
+        rc = r1;
+    }
+    for (int e = threadIdx.x; e < ra * rc; e += blockDim.x) H[e] = (T)Tm[(e % ra) + 64 * (e / ra)];
 }
 
 // Many theta, one X: the instantiated matrix is linear in the parametric vector (§4.3 weights,
@@ -809,7 +864,7 @@ __global__ void __launch_bounds__(kThreads, 3) coupling_kernel(DevView<T> v, int
             a /= p;
         }
         __syncthreads();
-        chain_lstep<T, MC>(in, out, v.H + v.key_hoff[key], rk[d], rk[d + 1], 1);  // H_k
+        chain_lstep<T, MC>(in, out, v.H + v.key_hoff[key], rk[d], rk[d + v.dtheta], 1);  // H_k
         { T* tmp = in; in = out; out = tmp; }
         int bsz = 1;
         for (int i = 0; i + 1 < d; ++i) {  // left cores G_d, ..., G_2
@@ -880,7 +935,7 @@ __global__ void __launch_bounds__(kThreads, 2) coupling_a_kernel(DevView<T> v, i
     const int item = blockIdx.x;
     const int key = v.citem_key[item], first = v.citem_first[item], cnt = v.citem_count[item];
     const int* rk = v.key_ranks + (size_t)key * (v.Delta + 1);
-    const int rd = rk[v.d], rp = rk[v.d + 1];
+    const int rd = rk[v.d], rp = rk[v.d + v.dtheta];
     const int PD = v.PD, Ntot = cnt * MC;
     const int rp4 = (rp + 3) & ~3;
     const T* Rk = v.far_lr + v.key_lroff[key] + (long long)rd * PD;  // R_k row-major [J * rp4 + s]
@@ -978,7 +1033,7 @@ __global__ void __launch_bounds__(kThreads, 2) coupling_a_staged_kernel(DevView<
     const int item = blockIdx.x;
     const int key = v.citem_key[item], first = v.citem_first[item], cnt = v.citem_count[item];
     const int* rk = v.key_ranks + (size_t)key * (v.Delta + 1);
-    const int rd = rk[v.d], rp = rk[v.d + 1], rp4 = (rp + 3) & ~3;
+    const int rd = rk[v.d], rp = rk[v.d + v.dtheta], rp4 = (rp + 3) & ~3;
     const int PD = v.PD, N = cnt * MC;
     const T* Rk = v.far_lr + v.key_lroff[key] + (long long)rd * PD;  // [J * rp4 + s]
     if (threadIdx.x < cnt) colbase[threadIdx.x] = (long long)v.fb_t[v.kb_list[first + threadIdx.x]] * PD * S + c0;
@@ -1327,7 +1382,7 @@ __global__ void __launch_bounds__(tc2::THREADS, 1) coupling_a_umma_kernel(DevVie
         it.cnt = v.tcitem_count[idx];
         const int* rk = v.key_ranks + (size_t)it.key * (v.Delta + 1);
         it.rd = rk[v.d];
-        it.rp = rk[v.d + 1];
+        it.rp = rk[v.d + v.dtheta];
         it.hoff = v.key_hoff[it.key];
         it.tcoff = v.key_tcoff[it.key];
         return it;
@@ -1866,7 +1921,7 @@ __global__ void __launch_bounds__(kThreads) far_h_kernel(DevView<T> v, int S, in
         const int t = v.fb_t[fb], key = v.fb_key[fb];
         const int tb = v.node_begin[t], nt = v.node_end[t] - tb;
         const int* rk = v.key_ranks + (size_t)key * (v.Delta + 1);
-        const int ra = rk[v.d], rb = rk[v.d + 1];
+        const int ra = rk[v.d], rb = rk[v.d + v.dtheta];
         const T* Sb = v.st + v.fb_soff[fb];
         const T* Tb = v.st + v.fb_toff[fb];
         const T* H = v.H + v.key_hoff[key];
@@ -2453,7 +2508,7 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
                 for (int s : plan.far_targets) maxnode = std::max(maxnode, plan.nodes[s].size());
                 for (size_t key = 0; key < plan.key_rep.size(); ++key) {
                     const int* rk = &h->key_ranks[key * (h->Delta + 1)];
-                    rmax = std::max(rmax, std::max(rk[v.d], rk[v.d + 1]));
+                    rmax = std::max(rmax, std::max(rk[v.d], rk[v.d + v.dtheta]));
                 }
                 size_t sm_h = ((size_t)maxnode * MC + 2 * (size_t)rmax * MC) * sizeof(T);
                 set_smem<T, MC>((const void*)far_h_kernel<T, MC>, sm_h);
@@ -2538,7 +2593,9 @@ void instantiate_typed(ph_handle* h, DevView<T>& v, const double* theta, int der
     double th[3] = {0, 0, 0};
     for (int k = 0; k < h->opts.dtheta; ++k) th[k] = theta[k];
     ProfScope ps(h, 0, stream);
-    instantiate_kernel<T><<<grid, kThreads, 0, stream>>>(v, th[0], th[1], th[2], near_ctas, deriv);
+    const size_t dsm = (h->opts.dtheta > 1 && v.n_keys > 0) ? (size_t)3 * 64 * 64 * sizeof(double) : 0;
+    if (dsm) set_smem<T, 1>((const void*)instantiate_kernel<T>, dsm);
+    instantiate_kernel<T><<<grid, kThreads, dsm, stream>>>(v, th[0], th[1], th[2], near_ctas, deriv);
     PH_LAUNCH("instantiate_kernel");
 }
 

@@ -13,7 +13,8 @@ namespace ph {
 constexpr int kMaxDim = 3;
 constexpr int kMaxPs = 16;
 constexpr int kMaxPTheta = 32;
-constexpr int kMaxNearRank = 32;
+constexpr int kMaxNearRank = 128;  // near ranks r_{b,1}: never binds for <= 128 theta-grid points
+constexpr int kMaxThetaGrid = 1024;  // product of the p_theta_i
 
 // One node sigma of the cluster tree (§3.2).  Points of a node are the
 // contiguous range [begin, end) of the cluster order; inside a node the order

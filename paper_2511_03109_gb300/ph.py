@@ -29,7 +29,7 @@ PH_ERR_IO = 8
 PH_ERR_UNSUPPORTED = 9
 
 KERNELS = {"gauss": 0, "matern32": 1, "matern52": 2, "aniso_gauss": 3, "se": 4, "exponential": 5,
-           "mc": 6, "poly": 7, "polyxy": 8}
+           "mc": 6, "poly": 7, "polyxy": 8, "poly2": 9}
 FORMATS = {"h2": 0, "h": 1}
 PRECISIONS = {"fp64": 0, "fp32": 1}
 

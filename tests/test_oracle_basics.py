@@ -203,3 +203,27 @@ def test_aniso_gauss_per_axis_lengths():
     prod = (kernels.kappa("gauss", xs[:, :1], ys[:, :1], [l2[0]]) *
             kernels.kappa("gauss", xs[:, 1:], ys[:, 1:], [l2[1]]))
     np.testing.assert_allclose(kernels.kappa("aniso_gauss", xs, ys, l2), prod, rtol=1e-13)
+
+
+def test_poly2_closed_form():
+    """The two-parameter test kernel 1 + t1 r^2 + t2^2 r^4, evaluated by hand."""
+    x, y = np.array([0.1, 0.4]), np.array([0.4, 0.0])  # r^2 = 0.09 + 0.16 = 0.25
+    np.testing.assert_allclose(kernels.kappa("poly2", x, y, [0.7, 1.5]), 1 + 0.7 * 0.25 + 2.25 * 0.0625, rtol=1e-15)
+    assert kernels.kappa("poly2", x, x, [0.7, 1.5]) == 1.0
+
+
+def test_truncation_rank_cap_never_splits_a_tied_group():
+    """A cap that falls inside a group of equal singular values drops the whole group (a cut inside
+    it would keep an arbitrary subspace); a cap between distinct values is applied as is."""
+    s = np.array([5.0, 3.0, 2.0, 2.0, 2.0, 1.0, 0.5])
+    assert tensor.truncation_rank(s, 0.0, rank_cap=3) == 2  # 2.0 x 3 would be split: keep 5, 3
+    assert tensor.truncation_rank(s, 0.0, rank_cap=5) == 5  # the group fits
+    assert tensor.truncation_rank(s, 0.0, rank_cap=6) == 6
+    assert tensor.truncation_rank(s, 0.0, rank_cap=None) == 7
+    # the exact factorisation of a Kronecker-structured matrix (repeated products of singular
+    # values) truncated at a cap inside a repeated value: unique whatever the SVD's basis
+    a = np.diag([1.0, 0.5])
+    K = np.kron(np.kron(a, a), a)  # singular values 1, .5 x3, .25 x3, .125
+    sv = np.linalg.svd(K, compute_uv=False)
+    assert tensor.truncation_rank(sv, 0.0, rank_cap=2) == 1
+    assert tensor.truncation_rank(sv, 0.0, rank_cap=4) == 4

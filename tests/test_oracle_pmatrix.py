@@ -270,3 +270,27 @@ def test_error_follows_the_truncation_tolerance():
         assert e <= 2 * tol, (tol, e)
         errs.append(e)
     assert all(errs[i + 1] < errs[i] / 30 for i in range(3)), errs
+
+
+@pytest.mark.parametrize("fmt", ["h2", "h"])
+def test_two_parameter_method_exact_on_polynomial_kernel(fmt):
+    """d_theta = 2 (§4.3 product over the parameter cores, App. A.4 H_b as a product of the
+    parameter-core matrices): with the two-parameter polynomial kernel, no truncation and enough
+    nodes (degree 1 in theta_1, 2 in theta_2; spatial degree 4 < p_s), the method reproduces the
+    dense K(theta) X to rounding for any theta, and its theta-derivatives reproduce the exact ones."""
+    from paper_2511_03109_gb300 import inputs
+    n = 180
+    P = inputs.uniform_points(n, 2, 77)
+    X = inputs.gaussian_rhs(n, 2, 78)
+    M = pmatrix.ParametricMatrix(P, "poly2", [0.5, 0.2], [2.0, 1.5], [1, 2], 5, 2, 1.0, 0.0, fmt=fmt)
+    M.offline()
+    for th in ([0.5, 0.2], [1.3, 0.77], [2.0, 1.5]):
+        ref = kernels.dense_apply("poly2", P, th, X)
+        got = M.matvec(M.instantiate(th), X)
+        assert np.max(pmatrix.relative_error(ref, got)) < 1e-11
+    # d/dtheta_1 = r^2, d/dtheta_2 = 2 theta_2 r^4
+    th = [1.1, 0.9]
+    D = np.sum((P[:, None, :] - P[None, :, :]) ** 2, axis=-1)
+    for dim, Kd in ((0, D), (1, 2 * th[1] * D * D)):
+        got = M.matvec(M.instantiate(th, deriv=dim), X)
+        assert np.max(pmatrix.relative_error(Kd @ X, got)) < 1e-10
