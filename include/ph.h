@@ -160,6 +160,19 @@ ph_status ph_instantiate_derivative(ph_handle* h, const double* theta, int dim, 
 ph_status ph_matvec(ph_handle* h, const void* X, long ldx, int m, void* Y, long ldy,
                     void* stream);
 
+/* X = K_hat(theta)^T Y for the last instantiated theta (or the transpose of its theta-derivative
+ * after ph_instantiate_derivative): the adjoint of ph_matvec, the gradient of a scalar function
+ * of Y = K_hat X with respect to X.  Not in the paper (it serves gradients of GP objectives); every
+ * block enters transposed: near blocks D_b(theta)^T (§4.3), far blocks T_b H_b^T S_b^T (H format,
+ * §4.5) or C_b^T = R_b H_b^T L_b^T between the sweeps (H^2, §4.2, Alg. FastForward / FastBackward
+ * on Y).  The first call builds the transposed far structure (the far blocks regrouped by source,
+ * the factors of each class exchanged) and keeps it; later ph_instantiate calls also write H_k^T.
+ *   Y : device, n x m column-major, leading dimension ldy >= n, original point order.
+ *   X : device, n x m column-major, leading dimension ldx >= n; overwritten.
+ * Errors: as ph_matvec, plus PH_ERR_UNSUPPORTED for an H^2 handle with the TT-chain coupling
+ * (coupling = 1).  Stream-ordered and asynchronous. */
+ph_status ph_matvec_transpose(ph_handle* h, const void* Y, long ldy, int m, void* X, long ldx, void* stream);
+
 /* Many theta, one block of right-hand sides (d_theta = 1): Y_t = K_hat(theta_t) X for
  * t < n_theta, or dK_hat/dtheta(theta_t) X with deriv = 0 (deriv = -1: the matrix itself).
  * K_hat(theta) is linear in the parametric vector (§4.3 weights, App. A.4 H_b), so

@@ -82,6 +82,7 @@ static void fill_view(ph_handle* h, DevView<T>& v, const std::vector<long>& io, 
     v.node_level = I + io[8];
     v.near_by_leaf = I + io[9];
     v.nb_t = I + io[10];
+    v.nb_s = I + io[33];
     v.nb_rank = I + io[11];
     v.nb_woff = I + io[12];
     v.key_ranks = I + io[13];
@@ -134,8 +135,11 @@ static void fill_view(ph_handle* h, DevView<T>& v, const std::vector<long>& io, 
     v.far_cores = (const T*)h->d_far;
     v.far_theta = h->d_far_theta;
     v.H = (T*)h->d_H;
+    v.HT = (T*)h->d_HT;
     v.n_far = (int)plan.far_s.size();
     v.n_far_targets = (int)plan.far_targets.size();
+    v.far_max_target = 1;
+    for (int t : plan.far_targets) v.far_max_target = std::max(v.far_max_target, plan.nodes[t].size());
     v.st = (const T*)h->d_st;
     v.n_far_levels = h->n_far_levels;
     v.U = (const T*)h->d_U;
@@ -318,6 +322,7 @@ void refresh_views(ph_handle* h) {
     put(h->tcitem_key);             // 30
     put(h->tcitem_first);           // 31
     put(h->tcitem_count);           // 32
+    put(plan.near_s);               // 33
     std::vector<long long> lls;
     std::vector<long> lo;
     auto putl = [&](const std::vector<long long>& a) {
@@ -359,6 +364,7 @@ void refresh_views(ph_handle* h) {
     fill_view<double>(h, h->vd, io, lo);
     h->view_io = io;
     h->view_lo = lo;
+    refresh_transposed(h);
 }
 
 // Sizes the per-call workspace for m right-hand sides (padded to the chunk width).
@@ -383,11 +389,13 @@ void ensure_workspace(ph_handle* h, int m) {
     if (h->opts.fmt == PH_FMT_H2 && !plan.far_targets.empty()) {
         h->d_xhat = dev_alloc(h, (size_t)plan.nodes.size() * h->PD * S * sc);
         h->d_yhat = dev_alloc(h, (size_t)plan.nodes.size() * h->PD * S * sc);
-        if (h->opts.coupling == 0) h->d_zbuf = dev_alloc(h, plan.far_s.size() * (size_t)h->zstride * S * sc);
+        if (h->opts.coupling == 0)
+            h->d_zbuf = dev_alloc(h, plan.far_s.size() * (size_t)std::max(h->zstride, h->zstride_adj) * S * sc);
     }
     h->mcap = S;
     fill_view<float>(h, h->vf, h->view_io, h->view_lo);
     fill_view<double>(h, h->vd, h->view_io, h->view_lo);
+    refresh_transposed(h);
 }
 
 }  // namespace ph
@@ -538,6 +546,16 @@ ph_status ph_matvec(ph_handle* h, const void* X, long ldx, int m, void* Y, long 
         ph::NvtxRange range("ph_matvec");
         PH_CUDA(cudaSetDevice(h->device));
         return ph::online_matvec(h, X, ldx, m, Y, ldy, as_stream(stream));
+    });
+}
+
+ph_status ph_matvec_transpose(ph_handle* h, const void* Y, long ldy, int m, void* X, long ldx, void* stream) {
+    ph_status s = check_mv(h, Y, ldy, m, X, ldx);
+    if (s != PH_OK) return s;
+    return guarded(h, [&]() -> ph_status {
+        ph::NvtxRange range("ph_matvec_transpose");
+        PH_CUDA(cudaSetDevice(h->device));
+        return ph::online_matvec_transpose(h, Y, ldy, m, X, ldx, as_stream(stream));
     });
 }
 

@@ -38,6 +38,7 @@ struct DevView {
     int n_near;
     const int* near_by_leaf;    // CSR over leaves
     const int* nb_t;            // source node of each near block
+    const int* nb_s;            // target leaf node of each near block
     const int* nb_rank;
     const long long* nb_off;    // element offset of G_{b,1} (r slabs of n_s x n_t) in near_cores
     const long long* nb_toff;   // offset of the theta cores in near_theta (FP64)
@@ -61,6 +62,7 @@ struct DevView {
     const T* far_cores;
     const double* far_theta;
     T* H;
+    T* HT;                      // H_k^T per class at the same offsets (written when the adjoint is set up)
     const T* far_lr;            // explicit L_k^T (r_d x PD) then R_k^T (r_{d+1} x PD) per key, row-major
     const long long* key_lroff; // offset of L_k^T in far_lr (R_k^T follows)
     const int* kb_off;          // CSR over keys: far blocks of each key
@@ -81,6 +83,7 @@ struct DevView {
     const int* fb_t;            // source node per far block
     const int* fb_key;
     int n_far_targets;
+    int far_max_target;         // largest target node (host use: shared memory of the H-format kernel)
     const int* far_targets;     // target node ids
     const int* far_by_target;   // CSR over far_targets
     // H format
@@ -186,6 +189,18 @@ struct ph_handle {
     int seen_timeouts = 0;                      // flags[1] already reported as PH_ERR_TIMEOUT
     double* host_thetas_pinned = nullptr;       // pinned source of a batched call's theta copy
     size_t host_thetas_cap = 0;
+    // adjoint K_hat^T (ph_matvec_transpose): far blocks with targets and sources swapped and the
+    // classes' factors exchanged (L' = R_k, R' = L_k, H' = H_k^T), built on first use
+    bool adj_ready = false;
+    int* d_adj_int = nullptr;
+    long long* d_adj_ll = nullptr;
+    void* d_lrT = nullptr;
+    void* d_HT = nullptr;
+    int zstride_adj = 1;
+    std::vector<long> adj_io, adj_lo;
+    int adj_n_targets = 0, adj_max_target = 1, adj_n_citems = 0;
+    DevView<float> vfT{};
+    DevView<double> vdT{};
     bool instantiated = false;
     bool overlap = true;                        // far path on the side stream (ph_set_overlap)
     bool use_bulk = true;                       // bulk-copy pipelined near field and phase 2 when they apply
@@ -214,6 +229,13 @@ ph_status wait_bound_selftest(int device, double* waited);  // bounded mbarrier 
 ph_status handle_timeout_selftest(ph_handle* h, cudaStream_t stream);  // the same wait, counted in h's flags
 ph_status online_matvec(ph_handle* h, const void* X, long ldx, int m, void* Y, long ldy,
                         cudaStream_t stream);
+// X = K_hat(theta)^T Y (the adjoint): near blocks transposed, far field through the transposed view.
+ph_status online_matvec_transpose(ph_handle* h, const void* Y, long ldy, int m, void* X, long ldx,
+                                  cudaStream_t stream);
+// Builds the transposed far view (adjoint.cpp) and H_k^T of the current instantiation.
+void build_adjoint(ph_handle* h, cudaStream_t stream);
+void refresh_transposed(ph_handle* h);  // the transposed views after the forward views changed
+void transpose_H(ph_handle* h, cudaStream_t stream);  // online.cu: H_k^T of the current H
 void ensure_workspace(ph_handle* h, int m);
 // ph_matvec with the caller's device views (their workspace pointers replace the handle's).
 ph_status online_matvec_view(ph_handle* h, DevView<float>& vf, DevView<double>& vd, const void* X, long ldx, int m,

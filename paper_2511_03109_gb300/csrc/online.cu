@@ -149,6 +149,7 @@ __global__ void instantiate_kernel(DevView<T> v, double th0, double th1, double 
             double s = 0.0;
             for (int t = 0; t < P0; ++t) s += G[a + ra * (t + P0 * bb)] * sv[0][t];
             H[e] = (T)s;
+            if (v.HT) v.HT[v.key_hoff[key] + bb + rb * a] = (T)s;
         }
         return;
     }
@@ -181,7 +182,11 @@ __global__ void instantiate_kernel(DevView<T> v, double th0, double th1, double 
         }
         rc = r1;
     }
-    for (int e = threadIdx.x; e < ra * rc; e += blockDim.x) H[e] = (T)Tm[(e % ra) + 64 * (e / ra)];
+    for (int e = threadIdx.x; e < ra * rc; e += blockDim.x) {
+        const T hv = (T)Tm[(e % ra) + 64 * (e / ra)];
+        H[e] = hv;
+        if (v.HT) v.HT[v.key_hoff[key] + e / ra + rc * (e % ra)] = hv;
+    }
 }
 
 // Many theta, one X: the instantiated matrix is linear in the parametric vector (§4.3 weights,
@@ -2326,6 +2331,55 @@ __global__ void __launch_bounds__(kThreads + 32, 2) coupling_b_tma_kernel(DevVie
     }
 }
 
+// Adjoint near field: Xbar_t += D_b(theta)^T Ybar_s for every stored near block b = (s, t)
+// (§4.3 blocks, transposed), accumulated into the first partial slot of the source leaf t (the
+// other slots of t are zero), so that combine_kernel adds it like a forward near partial.  One CTA
+// per block; thread j owns column j of D_b: out[j][c] = sum_i (sum_k w_k G_{b,1}[(j r + k) n_s + i])
+// Ybar_s[i][c], reading its column of every slab as one contiguous run.
+template <typename T, int MC>
+__global__ void __launch_bounds__(kThreads) near_adjoint_kernel(DevView<T> v, int S, int c0, int maxleaf) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* ys = reinterpret_cast<T*>(smem_raw);  // n_s x MC
+    T* sw = ys + (size_t)maxleaf * MC;       // r
+    const int b = blockIdx.x;
+    const int snode = v.nb_s[b], tnode = v.nb_t[b];
+    const int sb = v.node_begin[snode], ns = v.node_end[snode] - sb;
+    const int tb = v.node_begin[tnode], nt = v.node_end[tnode] - tb;
+    const int r = v.nb_rank[b];
+    for (int e = threadIdx.x; e < ns * MC; e += blockDim.x) ys[e] = v.Xc[(long long)(sb + e / MC) * S + c0 + e % MC];
+    for (int k = threadIdx.x; k < r; k += blockDim.x) sw[k] = v.w[v.nb_woff[b] + k];
+    __syncthreads();
+    const int tleaf = v.node_leaf[tnode];
+    T* dst = v.partials + (long long)v.items_by_leaf[tleaf] * v.part_stride * S + c0;
+    const T* G = v.near_cores + v.nb_off[b];
+    for (int j = threadIdx.x; j < nt; j += blockDim.x) {
+        T acc[MC];
+#pragma unroll
+        for (int c = 0; c < MC; ++c) acc[c] = T(0);
+        const T* gj = G + (long long)j * r * ns;
+        for (int i = 0; i < ns; ++i) {
+            T dij = T(0);
+            for (int k = 0; k < r; ++k) dij += sw[k] * __ldg(gj + (long long)k * ns + i);
+#pragma unroll
+            for (int c = 0; c < MC; ++c) acc[c] += dij * ys[i * MC + c];
+        }
+        T* o = dst + (long long)j * S;
+        constexpr int CT = MC < 4 ? MC : 4;
+#pragma unroll
+        for (int c = 0; c < MC; c += CT) atomic_add_ct<T, CT>(o + c, *reinterpret_cast<T(*)[CT]>(&acc[c]));
+    }
+}
+
+// H_k^T of every class into HT at the offsets of H (for an adjoint set up after instantiation).
+template <typename T>
+__global__ void transpose_H_kernel(DevView<T> v, T* HT) {
+    const int key = blockIdx.x;
+    const int* rk = v.key_ranks + (size_t)key * (v.Delta + 1);
+    const int ra = rk[v.d], rb = rk[v.d + v.dtheta];
+    const long long off = v.key_hoff[key];
+    for (int e = threadIdx.x; e < ra * rb; e += blockDim.x) HT[off + e / ra + (long long)rb * (e % ra)] = v.H[off + e];
+}
+
 template <typename T, int MC>
 void set_smem(const void* fn, size_t bytes) {
     PH_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
@@ -2333,7 +2387,7 @@ void set_smem(const void* fn, size_t bytes) {
 
 template <typename T, int MC>
 void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T* Y, long long ldy,
-                cudaStream_t stream, int S) {
+                cudaStream_t stream, int S, bool adj) {
     const Plan& plan = h->plan;
     const int nleaves = (int)plan.leaves.size();
     int maxleaf = 1;
@@ -2353,7 +2407,18 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
     const bool near_tma = h->use_bulk && S == MC && (MC * sizeof(T)) % 16 == 0 && maxleaf <= kThreads &&
                           (size_t)h->near_rank_max * maxleaf * sizeof(T) <= (size_t)nt1::STAGE &&
                           sm_ntma <= 110 * 1024 && v.n_items > 0;
-    for (int c0 = 0; c0 < S; c0 += MC) {
+    if (adj && v.n_near > 0) {
+        // adjoint near field: transposed blocks accumulated into zeroed partial slots
+        PH_CUDA(cudaMemsetAsync(v.partials, 0, (size_t)std::max(1, v.n_items) * v.part_stride * S * sizeof(T), stream));
+        const size_t smem = ((size_t)maxleaf * MC + kMaxNearRank) * sizeof(T);
+        set_smem<T, MC>((const void*)near_adjoint_kernel<T, MC>, smem);
+        for (int c0 = 0; c0 < S; c0 += MC) {
+            ProfScope ps(h, 2, stream);
+            near_adjoint_kernel<T, MC><<<v.n_near, kThreads, smem, stream>>>(v, S, c0, maxleaf);
+            PH_LAUNCH("near_adjoint_kernel");
+        }
+    }
+    for (int c0 = 0; c0 < S && !adj; c0 += MC) {
         ProfScope ps(h, 2, stream);
         if (near_tma) {
             h->last_variants |= 1;
@@ -2367,7 +2432,7 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
             PH_LAUNCH("near_kernel");
         }
     }
-    if (!plan.far_targets.empty()) {
+    if (v.n_far_targets > 0) {
         for (int c0 = 0; c0 < S; c0 += MC) {
             if (h2) {
                 PH_CUDA(cudaMemsetAsync(v.xhat, 0, (size_t)v.n_nodes * PD * S * sizeof(T), far));
@@ -2438,7 +2503,7 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
                         const int nib = (itemsb + kThreads - 1) / kThreads;
                         const int nsplit = 4;
                         size_t sm_b = (size_t)8 * v.zstride * MC * sizeof(T);
-                        const int nt = (int)plan.far_targets.size() * nsplit;
+                        const int nt = v.n_far_targets * nsplit;
                         const size_t sm_btma = (size_t)cb1::NS * cb1::STB + (size_t)cb1::NS * v.zstride * MC * sizeof(T);
                         const bool b_tma = h->use_bulk && S == MC && MC >= 4 && (MC * sizeof(T)) % 16 == 0 &&
                                            PD % 8 == 0 && itemsb <= kThreads &&
@@ -2448,7 +2513,7 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
                             if (b_tma) {
                                 const int nsp = 2;
                                 set_smem<T, MC>((const void*)coupling_b_tma_kernel<T, MC>, sm_btma);
-                                coupling_b_tma_kernel<T, MC><<<(int)plan.far_targets.size() * nsp, kThreads + 32,
+                                coupling_b_tma_kernel<T, MC><<<v.n_far_targets * nsp, kThreads + 32,
                                                                sm_btma, far>>>(v, nsp);
                                 h->last_variants |= 2;
                                 b_done = true;
@@ -2478,7 +2543,7 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
                     const int nsplit = 4;
                     {
                         ProfScope ps(h, 5, far);
-                        const int nt = (int)plan.far_targets.size() * nsplit;
+                        const int nt = v.n_far_targets * nsplit;
                         if (ni <= 1) {
                             set_smem<T, MC>((const void*)coupling_kernel<T, MC, 1>, sm_c);
                             coupling_kernel<T, MC, 1><<<nt, kThreads, sm_c, far>>>(v, S, c0, zmax, nsplit);
@@ -2504,8 +2569,7 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
                     PH_LAUNCH("transfer_kernel(down)");
                 }
             } else {
-                int maxnode = 1, rmax = 1;
-                for (int s : plan.far_targets) maxnode = std::max(maxnode, plan.nodes[s].size());
+                int maxnode = v.far_max_target, rmax = 1;
                 for (size_t key = 0; key < plan.key_rep.size(); ++key) {
                     const int* rk = &h->key_ranks[key * (h->Delta + 1)];
                     rmax = std::max(rmax, std::max(rk[v.d], rk[v.d + v.dtheta]));
@@ -2513,7 +2577,7 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
                 size_t sm_h = ((size_t)maxnode * MC + 2 * (size_t)rmax * MC) * sizeof(T);
                 set_smem<T, MC>((const void*)far_h_kernel<T, MC>, sm_h);
                 ProfScope ps(h, 7, far);
-                far_h_kernel<T, MC><<<(int)plan.far_targets.size(), kThreads, sm_h, far>>>(v, S, c0, rmax);
+                far_h_kernel<T, MC><<<v.n_far_targets, kThreads, sm_h, far>>>(v, S, c0, rmax);
                 PH_LAUNCH("far_h_kernel");
             }
         }
@@ -2523,7 +2587,7 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
         PH_CUDA(cudaStreamWaitEvent(stream, h->ev_join, 0));
     }
     for (int c0 = 0; c0 < S; c0 += MC) {
-        const bool h2far = h2 && !plan.far_targets.empty();
+        const bool h2far = h2 && v.n_far_targets > 0;
         const int RB = kThreads / 2;
         const size_t sm_t = ((size_t)PD * MC + ((2 * v.p_s * v.p_s + 3) & ~3) +
                              std::max((size_t)2 * PD * MC, (((size_t)RB * (v.d * v.p_s + 1) + 3) & ~(size_t)3) +
@@ -2548,7 +2612,7 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
 
 template <typename T>
 ph_status matvec_typed(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T* Y, long long ldy,
-                       cudaStream_t stream) {
+                       cudaStream_t stream, bool adj = false) {
     const int MC = pick_mc(m);
     const int S = (int)ceil_div(m, MC) * MC;
     const bool h2 = (h->opts.fmt == PH_FMT_H2);
@@ -2561,16 +2625,16 @@ ph_status matvec_typed(ph_handle* h, DevView<T>& v, const T* X, long long ldx, i
         gather_kernel<T><<<grid, kThreads, 0, stream>>>(v, X, ldx, m, S, check);
         PH_LAUNCH("gather_kernel");
     }
-    if (h2 && !h->plan.far_targets.empty())
+    if (h2 && v.n_far_targets > 0)
         PH_CUDA(cudaMemsetAsync(v.yhat, 0, (size_t)v.n_nodes * v.PD * S * sizeof(T), stream));
     if (!h2 && v.n_far_levels > 0)
         PH_CUDA(cudaMemsetAsync(v.yfar, 0, (size_t)v.n_far_levels * v.n * S * sizeof(T), stream));
     switch (MC) {
-        case 1: run_matvec<T, 1>(h, v, X, ldx, m, Y, ldy, stream, S); break;
-        case 2: run_matvec<T, 2>(h, v, X, ldx, m, Y, ldy, stream, S); break;
-        case 4: run_matvec<T, 4>(h, v, X, ldx, m, Y, ldy, stream, S); break;
-        case 8: run_matvec<T, 8>(h, v, X, ldx, m, Y, ldy, stream, S); break;
-        default: run_matvec<T, 16>(h, v, X, ldx, m, Y, ldy, stream, S); break;
+        case 1: run_matvec<T, 1>(h, v, X, ldx, m, Y, ldy, stream, S, adj); break;
+        case 2: run_matvec<T, 2>(h, v, X, ldx, m, Y, ldy, stream, S, adj); break;
+        case 4: run_matvec<T, 4>(h, v, X, ldx, m, Y, ldy, stream, S, adj); break;
+        case 8: run_matvec<T, 8>(h, v, X, ldx, m, Y, ldy, stream, S, adj); break;
+        default: run_matvec<T, 16>(h, v, X, ldx, m, Y, ldy, stream, S, adj); break;
     }
     post_timeout_flag(h, stream);
     if (check) {
@@ -2734,6 +2798,23 @@ ph_status online_matvec_batched(ph_handle* h, const double* thetas, int n_theta,
                                                                    stride_y);
     PH_LAUNCH("node_combine_kernel");
     return PH_OK;
+}
+
+void transpose_H(ph_handle* h, cudaStream_t stream) {
+    const int nk = (int)h->plan.key_rep.size();
+    if (nk == 0 || !h->d_HT) return;
+    if (h->opts.prec == PH_FP32) transpose_H_kernel<float><<<nk, kThreads, 0, stream>>>(h->vf, (float*)h->d_HT);
+    else transpose_H_kernel<double><<<nk, kThreads, 0, stream>>>(h->vd, (double*)h->d_HT);
+    PH_LAUNCH("transpose_H_kernel");
+}
+
+ph_status online_matvec_transpose(ph_handle* h, const void* Y, long ldy, int m, void* X, long ldx,
+                                  cudaStream_t stream) {
+    build_adjoint(h, stream);
+    ensure_workspace(h, m);
+    if (h->opts.prec == PH_FP32)
+        return matvec_typed<float>(h, h->vfT, (const float*)Y, ldy, m, (float*)X, ldx, stream, true);
+    return matvec_typed<double>(h, h->vdT, (const double*)Y, ldy, m, (double*)X, ldx, stream, true);
 }
 
 ph_status online_matvec(ph_handle* h, const void* X, long ldx, int m, void* Y, long ldy, cudaStream_t stream) {

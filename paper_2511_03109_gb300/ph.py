@@ -75,6 +75,7 @@ _SIGS = {
     "ph_instantiate_derivative": (C.c_int, [_H, C.POINTER(C.c_double), C.c_int, _P]),
     "ph_matvec": (C.c_int, [_H, _P, C.c_long, C.c_int, _P, C.c_long, _P]),
     "ph_matvec_host": (C.c_int, [_H, _P, C.c_long, C.c_int, _P, C.c_long, _P]),
+    "ph_matvec_transpose": (C.c_int, [_H, _P, C.c_long, C.c_int, _P, C.c_long, _P]),
     "ph_matvec_batched": (C.c_int, [_H, C.POINTER(C.c_double), C.c_int, _P, C.c_long, C.c_int, _P, C.c_long,
                                     C.c_long, C.c_int, _P]),
     "ph_matvec_noalloc": (C.c_int, [_H, _P, C.c_long, C.c_int, _P, C.c_long, _P]),
@@ -205,6 +206,11 @@ class ParametricMatrix:
         return check(ph_matvec(self.h, C.c_void_p(x_ptr), ldx, m, C.c_void_p(y_ptr), ldy,
                                C.c_void_p(stream)), self.h)
 
+    def matvec_transpose_ptr(self, y_ptr, ldy, m, x_ptr, ldx, stream=0):
+        """ph_matvec_transpose: X = K_hat(theta)^T Y (device pointers, column-major)."""
+        return check(ph_matvec_transpose(self.h, C.c_void_p(y_ptr), ldy, m, C.c_void_p(x_ptr), ldx,
+                                         C.c_void_p(stream)), self.h)
+
     def matvec_batched_ptr(self, thetas, x_ptr, ldx, m, y_ptr, ldy, stride_y, deriv=-1, stream=0):
         """ph_matvec_batched: Y_t = K_hat(theta_t) X (or its theta-derivative with deriv = 0)."""
         import numpy as np
@@ -272,3 +278,64 @@ class ParametricMatrix:
 
 def _colmajor(X) -> bool:
     return X.dim() == 2 and X.stride(0) == 1 and X.stride(1) == X.shape[0]
+
+
+def _autograd_function():
+    """torch.autograd.Function for Y = K_hat(theta) X over one handle (built lazily so that importing
+    this module does not import torch).  Every product runs in libph: forward ph_instantiate +
+    ph_matvec; backward dX = ph_matvec_transpose(dY), and d theta_i = <dY, dK_hat/dtheta_i X> from
+    ph_instantiate_derivative + ph_matvec (the derivative of the Lagrange weights, FP64 on the
+    device), after which the handle is instantiated at theta again."""
+    import torch
+
+    class KhatApply(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, X, theta, A):
+            th = [float(t) for t in theta.detach().cpu().reshape(-1)]
+            stream = torch.cuda.current_stream(X.device).cuda_stream
+            Xc = X.t().contiguous()  # column-major n x m
+            n, m = X.shape
+            Y = torch.empty((m, n), dtype=X.dtype, device=X.device)
+            A.instantiate(th, stream)
+            A.matvec_ptr(Xc.data_ptr(), n, m, Y.data_ptr(), n, stream)
+            ctx.A, ctx.theta, ctx.dtype, ctx.tdev = A, th, theta.dtype, theta.device
+            ctx.save_for_backward(Xc)
+            return Y.t()
+
+        @staticmethod
+        def backward(ctx, dY):
+            (Xc,) = ctx.saved_tensors
+            A, th = ctx.A, ctx.theta
+            m, n = Xc.shape
+            stream = torch.cuda.current_stream(Xc.device).cuda_stream
+            dYc = dY.t().contiguous()
+            dX = dth = None
+            if ctx.needs_input_grad[0]:
+                out = torch.empty_like(dYc)
+                A.instantiate(th, stream)
+                A.matvec_transpose_ptr(dYc.data_ptr(), n, m, out.data_ptr(), n, stream)
+                dX = out.t()
+            if ctx.needs_input_grad[1]:
+                g = []
+                tmp = torch.empty_like(dYc)
+                for i in range(len(th)):
+                    A.instantiate_derivative(th, i, stream)
+                    A.matvec_ptr(Xc.data_ptr(), n, m, tmp.data_ptr(), n, stream)
+                    g.append(torch.sum(tmp.double() * dYc.double()))
+                A.instantiate(th, stream)
+                dth = torch.stack(g).to(device=ctx.tdev, dtype=ctx.dtype)
+            return dX, dth, None
+
+    return KhatApply
+
+
+_KHAT = None
+
+
+def khat_apply(A, X, theta):
+    """Y = K_hat(theta) X (X: n x m CUDA tensor, theta: tensor of d_theta values), differentiable in X
+    and theta through libph's adjoint and theta-derivative products."""
+    global _KHAT
+    if _KHAT is None:
+        _KHAT = _autograd_function()
+    return _KHAT.apply(X, theta, A)
