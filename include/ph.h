@@ -93,6 +93,11 @@ typedef struct {
                               applied as two matrix products (the alternative §4.5 mentions),
                               1 = the TT chain of Alg. "Modified H^2-Matrix MVM"; mode 0 needs
                               r_d, r_{d+d_theta} <= 64 and falls back to 1 otherwise */
+    int near_unshared;     /* 0 (default): store each unordered near pair {s, t} once and apply the
+                              mirror block as D_ts(theta) = D_st(theta)^T.  Every kernel here is
+                              symmetric, so A_ts is a row permutation of A_st and TT-SVD gives the
+                              same cores up to that permutation (§4.3): the sharing is exact and
+                              halves the near-field stream.  1: compress and store both blocks. */
 } ph_build_opts;
 
 /* Sizes and counts of a built handle; all byte counts are of stored data. */

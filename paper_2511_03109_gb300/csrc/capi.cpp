@@ -11,6 +11,7 @@
 #include <new>
 #include <stdexcept>
 #include <string>
+#include <unordered_map>
 
 #include "common.cuh"
 #include "handle.h"
@@ -83,6 +84,11 @@ static void fill_view(ph_handle* h, DevView<T>& v, const std::vector<long>& io, 
     v.near_by_leaf = I + io[9];
     v.nb_t = I + io[10];
     v.nb_s = I + io[33];
+    v.near_share = h->near_share;
+    v.n_mslots = h->n_mslots;
+    v.nb_mslot = I + io[34];
+    v.mirror_by_leaf = I + io[35];
+    v.mslot_block = I + io[36];
     v.nb_rank = I + io[11];
     v.nb_woff = I + io[12];
     v.key_ranks = I + io[13];
@@ -152,6 +158,25 @@ static void fill_view(ph_handle* h, DevView<T>& v, const std::vector<long>& io, 
     v.flags = h->d_flags;
 }
 
+void near_mirror_map(ph_handle* h) {
+    const Plan& plan = h->plan;
+    const int nn = (int)plan.near_s.size();
+    h->near_share = h->opts.near_unshared ? 0 : 1;
+    h->nb_src.resize(nn);
+    for (int b = 0; b < nn; ++b) h->nb_src[b] = b;
+    if (!h->near_share) return;
+    const long long nodes = (long long)plan.nodes.size();
+    std::unordered_map<long long, int> at;
+    at.reserve((size_t)nn * 2);
+    for (int b = 0; b < nn; ++b) at[(long long)plan.near_s[b] * nodes + plan.near_t[b]] = b;
+    for (int b = 0; b < nn; ++b) {
+        if (plan.near_s[b] <= plan.near_t[b]) continue;
+        auto it = at.find((long long)plan.near_t[b] * nodes + plan.near_s[b]);
+        if (it == at.end()) throw Error(PH_ERR_IO, "inconsistent handle data: near block without its mirror");
+        h->nb_src[b] = it->second;
+    }
+}
+
 // Packs the plan's index arrays into two device allocations and fills the views.
 void refresh_views(ph_handle* h) {
     const Plan& plan = h->plan;
@@ -205,8 +230,12 @@ void refresh_views(ph_handle* h) {
         lvl_flat.insert(lvl_flat.end(), h->level_nodes[l].begin(), h->level_nodes[l].end());
         h->level_nodes_off[l + 1] = (int)lvl_flat.size();
     }
-    // near work items: up to kNearItemBlocks consecutive near blocks of one target leaf
-    constexpr int kNearItemBlocks = 4;
+    // near work items: up to kNearItemBlocks consecutive stored near blocks of one target leaf
+    // (two with mirror sharing, whose kernel also stages x_s and a slice of D_b).  With sharing a
+    // leaf's stored blocks (s, t >= s) end its run: the plan orders a leaf's blocks by source id.
+    const int kNearItemBlocks = h->near_share ? 2 : 4;
+    const int nnear = (int)plan.near_s.size();
+    if ((int)h->nb_src.size() != nnear) near_mirror_map(h);
     h->item_first.clear();
     h->item_count.clear();
     h->item_leaf.clear();
@@ -214,12 +243,37 @@ void refresh_views(ph_handle* h) {
     h->max_leaf = 1;
     for (size_t l = 0; l < plan.leaves.size(); ++l) {
         h->max_leaf = std::max(h->max_leaf, plan.nodes[plan.leaves[l]].size());
-        for (int b = plan.near_by_leaf[l]; b < plan.near_by_leaf[l + 1]; b += kNearItemBlocks) {
-            h->item_first.push_back(b);
-            h->item_count.push_back(std::min(kNearItemBlocks, plan.near_by_leaf[l + 1] - b));
+        std::vector<int> run;
+        for (int b = plan.near_by_leaf[l]; b < plan.near_by_leaf[l + 1]; ++b)
+            if (h->nb_src[b] == b) run.push_back(b);
+        for (size_t q = 0; q < run.size();) {
+            // items cover consecutive block indices
+            size_t e = q + 1;
+            while (e < run.size() && (int)(e - q) < kNearItemBlocks && run[e] == run[e - 1] + 1) ++e;
+            h->item_first.push_back(run[q]);
+            h->item_count.push_back((int)(e - q));
             h->item_leaf.push_back((int)l);
+            q = e;
         }
         h->items_by_leaf[l + 1] = (int)h->item_first.size();
+    }
+    // mirror slots: one per stored block (s, t), s != t, grouped by the leaf t that receives them
+    h->nb_mslot.assign(nnear, -1);
+    h->mirror_by_leaf.assign(plan.leaves.size() + 1, 0);
+    h->mslot_block.clear();
+    h->n_mslots = 0;
+    if (h->near_share) {
+        std::vector<std::vector<int>> by_t(plan.leaves.size());
+        for (int b = 0; b < nnear; ++b)
+            if (h->nb_src[b] == b && plan.near_s[b] != plan.near_t[b])
+                by_t[plan.nodes[plan.near_t[b]].leaf].push_back(b);
+        for (size_t l = 0; l < plan.leaves.size(); ++l) {
+            for (int b : by_t[l]) {
+                h->nb_mslot[b] = h->n_mslots++;
+                h->mslot_block.push_back(b);
+            }
+            h->mirror_by_leaf[l + 1] = h->n_mslots;
+        }
     }
     // longest intermediate of the coupling chain kept in shared memory (all steps but the
     // first input and the last output): right-core outputs a r_out, H output, left-core outputs
@@ -323,6 +377,9 @@ void refresh_views(ph_handle* h) {
     put(h->tcitem_first);           // 31
     put(h->tcitem_count);           // 32
     put(plan.near_s);               // 33
+    put(h->nb_mslot);               // 34
+    put(h->mirror_by_leaf);         // 35
+    put(h->mslot_block);            // 36
     std::vector<long long> lls;
     std::vector<long> lo;
     auto putl = [&](const std::vector<long long>& a) {
@@ -381,7 +438,7 @@ void ensure_workspace(ph_handle* h, int m) {
     fill_view<float>(h, h->vf, h->view_io, h->view_lo);
     fill_view<double>(h, h->vd, h->view_io, h->view_lo);
     h->d_Xc = dev_alloc(h, (size_t)plan.n * S * sc);
-    h->d_partials = dev_alloc(h, std::max<size_t>(1, h->item_first.size()) * h->max_leaf * S * sc);
+    h->d_partials = dev_alloc(h, std::max<size_t>(1, h->item_first.size() + h->n_mslots) * h->max_leaf * S * sc);
     h->d_yfar = nullptr;
     h->d_xhat = h->d_yhat = nullptr;
     if (h->opts.fmt == PH_FMT_H && h->n_far_levels > 0)
@@ -678,9 +735,11 @@ ph_status ph_get_info(const ph_handle* h, ph_info* info) {
     r.kernel_variants = h->last_variants;
     // flops per right-hand side
     double fl = 2.0 * (double)r.near_entries;  // D_b x
-    for (size_t b = 0; b < plan.near_s.size(); ++b)
+    for (size_t b = 0; b < plan.near_s.size(); ++b) {
+        if (!h->nb_src.empty() && h->nb_src[b] != (int)b) continue;  // a shared pair forms d_ij once
         fl += 2.0 * h->nb_rank[b] * (double)plan.nodes[plan.near_s[b]].size() * plan.nodes[plan.near_t[b]].size() /
               16.0;  // forming d_ij, shared by 16 right-hand sides in a chunk
+    }
     const int p = h->opts.p_s, PD = h->PD, dt = h->opts.dtheta;
     for (size_t b = 0; b < plan.far_s.size(); ++b) {
         const int* rk = &h->key_ranks[(size_t)plan.far_key[b] * (D + 1)];

@@ -52,7 +52,15 @@ struct DevView {
     const int* item_leaf;
     const int* items_by_leaf;   // CSR over leaves
     int part_stride;            // rows per item in the partial buffer (max leaf size)
-    T* partials;                // n_items x part_stride x mcap
+    T* partials;                // (n_items + n_mslots) x part_stride x mcap
+    // mirror sharing: a stored block (s, t) with s != t also gives D_ts = D_st^T, whose product
+    // D_st^T x_s lands in partial slot n_items + nb_mslot[b] (-1: no mirror); the mirror slots of
+    // a leaf t are the contiguous range [mirror_by_leaf[t], mirror_by_leaf[t + 1])
+    int near_share;
+    int n_mslots;
+    const int* nb_mslot;
+    const int* mirror_by_leaf;
+    const int* mslot_block;     // the stored block of each mirror slot
     // far field
     int n_keys, Delta;
     const int* key_ranks;       // (Delta + 1) per key
@@ -171,6 +179,11 @@ struct ph_handle {
     void* d_partials = nullptr;
     std::vector<int> item_first, item_count, item_leaf, items_by_leaf;
     int max_leaf = 1;
+    // mirror sharing of near blocks (§4.3 with a symmetric kernel): nb_src[b] is the block whose
+    // stored cores b uses (b itself, or the block (t, s) when b = (s, t) is the mirrored one)
+    int near_share = 0;
+    std::vector<int> nb_src, nb_mslot, mirror_by_leaf, mslot_block;
+    int n_mslots = 0;
     int coupling_zmax = 1;                      // longest shared-memory intermediate of the TT chain
     DeviceBuffer ws;
     DeviceBuffer host_stage_x, host_stage_y;    // device staging for ph_matvec_host
@@ -241,6 +254,9 @@ void ensure_workspace(ph_handle* h, int m);
 ph_status online_matvec_view(ph_handle* h, DevView<float>& vf, DevView<double>& vd, const void* X, long ldx, int m,
                              void* Y, long ldy, cudaStream_t stream);
 void refresh_views(ph_handle* h);
+// h->near_share and h->nb_src from the options and the plan's near blocks (throws PH_ERR_IO when a
+// block's mirror is missing)
+void near_mirror_map(ph_handle* h);
 void free_device(ph_handle* h);
 void* dev_alloc(ph_handle* h, size_t bytes);  // throws ph::Error(PH_ERR_OOM) on failure
 // Test hook behind ph_inject_alloc_failure: after `after` more successful dev_alloc calls in

@@ -54,7 +54,7 @@ extern "C" ph_status ph_matvec_noalloc(ph_handle* h, const void* X, long ldx, in
         const int mc = (m <= 1) ? 1 : (m <= 2) ? 2 : (m <= 4) ? 4 : (m <= 8) ? 8 : 16;
         const size_t S = (size_t)ph::ceil_div(m, mc) * mc;
         const size_t sc = h->scalar, n = (size_t)h->plan.n;
-        const size_t items = std::max<size_t>(1, h->item_first.size());
+        const size_t items = std::max<size_t>(1, h->item_first.size() + h->n_mslots);  // item and mirror slots
         const bool h2 = (h->opts.fmt == PH_FMT_H2) && !h->plan.far_targets.empty();
         const bool hfar = (h->opts.fmt == PH_FMT_H) && h->n_far_levels > 0;
         // layout of the scratch array: Xc | partials | xhat | yhat | zbuf (H^2)  or  Xc | partials | yfar (H)

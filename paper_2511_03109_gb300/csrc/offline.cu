@@ -547,19 +547,27 @@ ph_status offline_build(ph_handle* h, const double* points, long n) {
     double* d_grid = upload_vec(h, grid);
 
     // ------------------------------------------------------------------ near field
-    const int nn = (int)plan.near_s.size();
+    // Compressed blocks: all near blocks, or with mirror sharing those (s, t) with s <= t; a
+    // mirrored block (t, s) takes the stored block's rank and offsets (its cores are read
+    // transposed).  Below, nn counts the compressed blocks and q indexes them (block bl[q]).
+    const int nnear = (int)plan.near_s.size();
+    near_mirror_map(h);
+    std::vector<int> bl;
+    for (int b = 0; b < nnear; ++b)
+        if (h->nb_src[b] == b) bl.push_back(b);
+    const int nn = (int)bl.size();
     std::vector<int> sb(nn), sn(nn), tb(nn), tn(nn);
-    for (int b = 0; b < nn; ++b) {
-        const Node& s = plan.nodes[plan.near_s[b]];
-        const Node& t = plan.nodes[plan.near_t[b]];
-        sb[b] = s.begin; sn[b] = s.size(); tb[b] = t.begin; tn[b] = t.size();
+    for (int q = 0; q < nn; ++q) {
+        const Node& s = plan.nodes[plan.near_s[bl[q]]];
+        const Node& t = plan.nodes[plan.near_t[bl[q]]];
+        sb[q] = s.begin; sn[q] = s.size(); tb[q] = t.begin; tn[q] = t.size();
     }
     NearBuild nbld{(int)h->kernel, d, P, dt, d_pts, upload_vec(h, sb), upload_vec(h, sn), upload_vec(h, tb),
                    upload_vec(h, tn), d_grid};
-    h->nb_rank.assign(nn, 0);
-    h->nb_off.assign(nn, 0);
-    h->nb_toff.assign(nn, 0);
-    h->nb_woff.assign(nn + 1, 0);
+    h->nb_rank.assign(nnear, 0);
+    h->nb_off.assign(nnear, 0);
+    h->nb_toff.assign(nnear, 0);
+    h->nb_woff.assign(nnear + 1, 0);
     std::vector<double> near_theta;
     if (nn > 0) {
         const double ntol = (o.near_tol >= 0) ? o.near_tol : o.tol;
@@ -568,20 +576,20 @@ ph_status offline_build(ph_handle* h, const double* points, long n) {
         std::vector<double> vr_pack;
         std::vector<long long> voff(nn, 0);
         long long off = 0, toff = 0;
-        auto finish_block = [&](int b, const double* s, const double* V) {  // s descending, V P x P
+        auto finish_block = [&](int q, const double* s, const double* V) {  // s descending, V P x P
             double fro2 = 0.0;
             for (int k = 0; k < P; ++k) fro2 += s[k] * s[k];
             const double delta2 = ntol * ntol * fro2 / dt;
             const int r = choose_rank_sv(s, P, delta2, kMaxNearRank);
+            const int b = bl[q];
             h->nb_rank[b] = r;
             h->nb_off[b] = off;
             h->nb_toff[b] = toff;
-            h->nb_woff[b + 1] = h->nb_woff[b] + r;
-            off += (long long)sn[b] * tn[b] * r;
+            off += (long long)sn[q] * tn[q] * r;
             toff += (long long)r * P;
             const std::vector<double> W = near_theta_matrix(s, V, P, r, pt, dt, delta2);
             near_theta.insert(near_theta.end(), W.begin(), W.end());
-            voff[b] = (long long)vr_pack.size();
+            voff[q] = (long long)vr_pack.size();
             vr_pack.insert(vr_pack.end(), V, V + (size_t)P * r);
         };
         if (P <= 32) {
@@ -723,11 +731,24 @@ ph_status offline_build(ph_handle* h, const double* points, long n) {
             }
             for (void* p : {(void*)d_A, (void*)d_G, (void*)d_L, (void*)d_info, d_work}) dev_free(h, p);
         }
+        for (int b = 0; b < nnear; ++b) {
+            const int src = h->nb_src[b];
+            h->nb_rank[b] = h->nb_rank[src];
+            h->nb_off[b] = h->nb_off[src];
+            h->nb_toff[b] = h->nb_toff[src];
+            h->nb_woff[b + 1] = h->nb_woff[b] + h->nb_rank[b];
+        }
         h->near_elems = off;
         h->near_theta_elems = toff;
-        h->w_elems = h->nb_woff[nn];
-        int* d_rank = upload_vec(h, h->nb_rank);
-        long long* d_off = upload_vec(h, h->nb_off);
+        h->w_elems = h->nb_woff[nnear];
+        std::vector<int> qrank(nn);
+        std::vector<long long> qoff(nn);
+        for (int q = 0; q < nn; ++q) {
+            qrank[q] = h->nb_rank[bl[q]];
+            qoff[q] = h->nb_off[bl[q]];
+        }
+        int* d_rank = upload_vec(h, qrank);
+        long long* d_off = upload_vec(h, qoff);
         double* d_vr = upload_vec(h, vr_pack);
         long long* d_voff = upload_vec(h, voff);
         h->d_near = dev_alloc(h, (size_t)off * h->scalar);

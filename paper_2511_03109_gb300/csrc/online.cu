@@ -1649,14 +1649,23 @@ __global__ void __launch_bounds__(tc2::THREADS, 1) coupling_a_umma_kernel(DevVie
 }
 
 // Near field Y_s += reshape(G_{b,1} w_b) X_t (§4.3, applied as in §4.5), bulk-copy pipelined
-// (FP32 / FP64, chunks of MC right-hand sides with S == MC, leaves
-// of at most kThreads points, r ns <= the stage size).  One CTA per near work item, as
-// near_kernel, with a producer warp: the cores G_{b,1} of the item's blocks are streamed in
-// chunks of whole columns j (each chunk contiguous in memory: [(j r + k) ns + i]) by 1-D bulk
-// copies into a ring of NS stages, together with the rows x_t of each block (into one buffer per
-// block).  The eight consumer warps form d_ij = sum_k w_k G[(j r + k) ns + i] from shared memory
-// and accumulate d_ij x_t[j][c] as near_kernel does; a stage is handed back through an mbarrier
-// arrival per consumer warp, so the CTA never stops at a full barrier while the cores stream.
+// (FP32 / FP64, chunks of MC right-hand sides with S == MC, leaves of at most kThreads points,
+// r ns <= the stage size).  One CTA per near work item, as near_kernel, with a producer warp: the
+// cores G_{b,1} of the item's blocks are streamed in chunks of whole columns j (each chunk
+// contiguous in memory: [(j r + k) ns + i]) by 1-D bulk copies into a ring of NS stages, together
+// with the rows x_t of each block (into one buffer per block).  The eight consumer warps form
+// d_ij = sum_k w_k G[(j r + k) ns + i] from shared memory and accumulate d_ij x_t[j][c] as
+// near_kernel does; a stage is handed back through an mbarrier arrival per consumer warp, so the
+// CTA never stops at a full barrier while the cores stream.
+//
+// Mirror sharing: a stored block (s, t) with s != t also stands for the block (t, s), whose
+// matrix is D_st^T.  The consumers then also write d_ij into a slice of up to JBM columns of D_st
+// in shared memory, and when the slice is full every warp takes a pair of its columns: lane
+// (segment, column group) sums d_ij x_s[i][c] over its segment of rows i, a butterfly over the
+// segments completes (D_st^T x_s)[j][c], and the result goes to the block's mirror slot, from
+// which combine_kernel adds it to leaf t.  One read of G_{b,1} serves both blocks.  A slice costs
+// two consumer barriers: slice complete (which also carries the abort vote) and slice read.
+//
 // Every wait is bounded: after a timeout the CTA counts it in flags[1], stops issuing copies and
 // waits (bounded) for those in flight before it exits.
 namespace nt1 {
@@ -1664,21 +1673,36 @@ constexpr int NS = 4;                    // stages
 constexpr int STAGE = 16384;             // bytes of cores per stage
 constexpr int STB = STAGE + 32;          // plus the 16-byte rounding of a chunk's start and end
 constexpr int kConsumers = kThreads / 32;
+constexpr int JBM = 2 * kConsumers;      // columns of a D slice (one pair per consumer warp)
 }  // namespace nt1
 
+// Columns of a block per stage chunk (at most `cap`).
 template <typename T>
-__device__ __forceinline__ int near_chunk_cols(int r, int ns) {
+__device__ __forceinline__ int near_chunk_cols(int r, int ns, int cap) {
     const long long colf = (long long)r * ns;
     const int J = (int)(nt1::STAGE / (colf * (long long)sizeof(T)));
-    return J < 1 ? 1 : J;
+    return J < 1 ? 1 : (J > cap ? cap : J);
+}
+
+// Shared memory of near_tma_kernel: the stages, the x_t buffers (4, or 2 with mirror sharing),
+// and with sharing x_s and a D slice of JBM columns.
+template <typename T>
+__host__ __device__ inline size_t near_tma_smem(int maxleaf, int mc, bool share) {
+    size_t b = (size_t)nt1::NS * nt1::STB + (size_t)(share ? 2 : 4) * maxleaf * mc * sizeof(T);
+    if (share) b += ((size_t)maxleaf * mc + (size_t)nt1::JBM * maxleaf) * sizeof(T);
+    return b;
 }
 
 template <typename T, int MC>
 __global__ void __launch_bounds__(kThreads + 32, 2) near_tma_kernel(DevView<T> v, int maxleaf) {
     using namespace nt1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const bool share = v.near_share != 0;
+    const int XB = share ? 2 : 4;                               // x_t buffers
     unsigned char* stg = smem_raw;                              // NS x STB
-    T* xs = reinterpret_cast<T*>(smem_raw + NS * STB);          // 4 x maxleaf x MC (one per block)
+    T* xs = reinterpret_cast<T*>(smem_raw + NS * STB);          // XB x maxleaf x MC (one per block)
+    T* xsrc = xs + (size_t)XB * maxleaf * MC;                   // maxleaf x MC: x_s (sharing)
+    T* dcur = xsrc + (size_t)maxleaf * MC;                      // JBM x maxleaf: the D slice
     T* red = reinterpret_cast<T*>(smem_raw);                    // kThreads x MC, after the stream
     __shared__ __align__(8) uint64_t full[NS], empty[NS];
     __shared__ int abort_flag;
@@ -1686,8 +1710,10 @@ __global__ void __launch_bounds__(kThreads + 32, 2) near_tma_kernel(DevView<T> v
     const int item = blockIdx.x;
     const int leaf = v.item_leaf[item];
     const int snode = v.leaf_node[leaf];
-    const int ns = v.node_end[snode] - v.node_begin[snode];
+    const int sbeg = v.node_begin[snode];
+    const int ns = v.node_end[snode] - sbeg;
     const int b0 = v.item_first[item], b1 = b0 + v.item_count[item];
+    const int jcap = share ? JBM : 1 << 20;
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) {
             mbar_init(&full[s], 1);
@@ -1708,7 +1734,7 @@ __global__ void __launch_bounds__(kThreads + 32, 2) near_tma_kernel(DevView<T> v
                 const int tnode = v.nb_t[b];
                 const int tb = v.node_begin[tnode], nt = v.node_end[tnode] - tb;
                 const long long colf = (long long)r * ns;
-                const int J = near_chunk_cols<T>(r, ns);
+                const int J = near_chunk_cols<T>(r, ns, jcap);
                 for (int j0 = 0; j0 < nt; j0 += J, ++t) {
                     const int st = t % NS;
                     if (t >= NS) ok = mbar_wait(&empty[st], (uint32_t)(((t / NS) - 1) & 1));
@@ -1722,10 +1748,12 @@ __global__ void __launch_bounds__(kThreads + 32, 2) near_tma_kernel(DevView<T> v
                     const uintptr_t s0 = a0 & ~(uintptr_t)15, e0 = (a1 + 15) & ~(uintptr_t)15;
                     uint32_t bytes = (uint32_t)(e0 - s0);
                     const uint32_t xbytes = (j0 == 0) ? (uint32_t)(nt * MC * sizeof(T)) : 0u;
-                    mbar_expect_tx(&full[st], bytes + xbytes);
+                    const uint32_t sbytes = (share && t == 0) ? (uint32_t)(ns * MC * sizeof(T)) : 0u;
+                    mbar_expect_tx(&full[st], bytes + xbytes + sbytes);
                     bulk_g2s(stg + st * STB, (const void*)s0, bytes, &full[st]);
                     if (xbytes)
                         bulk_g2s(xs + (size_t)(b - b0) * maxleaf * MC, v.Xc + (long long)tb * MC, xbytes, &full[st]);
+                    if (sbytes) bulk_g2s(xsrc, v.Xc + (long long)sbeg * MC, sbytes, &full[st]);
                 }
             }
             if (!ok) {
@@ -1744,48 +1772,97 @@ __global__ void __launch_bounds__(kThreads + 32, 2) near_tma_kernel(DevView<T> v
     const int G = kThreads / RP;
     const int i = tid % RP, g = tid / RP;
     const bool active = (g < G) && (i < ns);
+    // mirror product lanes: lane = cg + CG * seg; rows of segment seg start seglen apart (odd, so
+    // the segments of one load fall in distinct banks)
+    constexpr int VW = 16 / (int)sizeof(T);
+    constexpr int CG = MC >= VW ? MC / VW : 1, SEGS = 32 / CG;  // (launched only for MC >= VW)
+    const int seg = lane / CG, cg = lane % CG;
+    const int seglen = ((ns + SEGS - 1) / SEGS) | 1;
     T acc[MC];
 #pragma unroll
     for (int c = 0; c < MC; ++c) acc[c] = T(0);
     bool ok = true;
     int t = 0;
-    for (int b = b0; b < b1 && ok; ++b) {
+    for (int b = b0; b < b1; ++b) {
         const int r = v.nb_rank[b];
         const int tnode = v.nb_t[b];
         const int nt = v.node_end[tnode] - v.node_begin[tnode];
         const long long colf = (long long)r * ns;
-        const int J = near_chunk_cols<T>(r, ns);
+        const int J = near_chunk_cols<T>(r, ns, jcap);
+        const int mslot = share ? v.nb_mslot[b] : -1;
         constexpr int RK = 8;  // ranks up to RK use the unrolled path
         T wr[RK];
         const T* wb = v.w + v.nb_woff[b];
 #pragma unroll
         for (int k = 0; k < RK; ++k) wr[k] = (k < r) ? wb[k] : T(0);
         const T* xsb = xs + (size_t)(b - b0) * maxleaf * MC;
+        int fbase = 0;  // first column of the current D slice
         for (int j0 = 0; j0 < nt; j0 += J, ++t) {
             const int st = t % NS;
-            ok = mbar_wait(&full[st], (uint32_t)((t / NS) & 1)) && !*(volatile int*)&abort_flag;
-            if (!ok) break;
+            if (ok) ok = mbar_wait(&full[st], (uint32_t)((t / NS) & 1)) && !*(volatile int*)&abort_flag;
             const int jn = min(J, nt - j0);
-            const uintptr_t a0 = (uintptr_t)(v.near_cores + v.nb_off[b] + j0 * colf);
-            const T* Gs = reinterpret_cast<const T*>(stg + st * STB + (a0 & 15)) + i;
-            if (active) {
-                for (int jj = g; jj < jn; jj += G) {
-                    const T* gj = Gs + jj * colf;
-                    T dij = T(0);
-                    if (r <= RK) {
+            if (ok) {
+                const uintptr_t a0 = (uintptr_t)(v.near_cores + v.nb_off[b] + j0 * colf);
+                const T* Gs = reinterpret_cast<const T*>(stg + st * STB + (a0 & 15)) + i;
+                if (active) {
+                    for (int jj = g; jj < jn; jj += G) {
+                        const T* gj = Gs + jj * colf;
+                        T dij = T(0);
+                        if (r <= RK) {
 #pragma unroll
-                        for (int k = 0; k < RK; ++k)
-                            if (k < r) dij += wr[k] * gj[(long long)k * ns];
-                    } else {
-                        for (int k = 0; k < r; ++k) dij += wb[k] * gj[(long long)k * ns];
+                            for (int k = 0; k < RK; ++k)
+                                if (k < r) dij += wr[k] * gj[(long long)k * ns];
+                        } else {
+                            for (int k = 0; k < r; ++k) dij += wb[k] * gj[(long long)k * ns];
+                        }
+                        const T* xj = xsb + (j0 + jj) * MC;
+#pragma unroll
+                        for (int c = 0; c < MC; c += 2) fma_pair(acc[c], acc[c + 1], dij, dij, xj[c], xj[c + 1]);
+                        if (mslot >= 0) dcur[(size_t)(j0 + jj - fbase) * maxleaf + i] = dij;
                     }
-                    const T* xj = xsb + (j0 + jj) * MC;
+                }
+                __syncwarp();
+                if (lane == 0)
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[st])) : "memory");
+            }
+            if (mslot < 0) continue;
+            // mirror product of the slice once it is full (block-uniform decision)
+            const int jend = j0 + jn;
+            if (jend < nt && jend + min(J, nt - jend) - fbase <= JBM) continue;
+            ok = bar_and(ok, 1, kThreads);  // the slice is complete in every warp
+            const int ncols = jend - fbase, jc = 2 * warp;
+            if (ok && jc < ncols) {
+                T a0[VW], a1[VW];
 #pragma unroll
-                    for (int c = 0; c < MC; c += 2) fma_pair(acc[c], acc[c + 1], dij, dij, xj[c], xj[c + 1]);
+                for (int e = 0; e < VW; ++e) a0[e] = a1[e] = T(0);
+                const T* D0 = dcur + (size_t)jc * maxleaf;
+                const T* D1 = D0 + maxleaf;  // a column past ncols holds stale values: never stored
+                const int i0 = seg * seglen, i1 = min(ns, i0 + seglen);
+                for (int ii = i0; ii < i1; ++ii) {
+                    const T d0 = D0[ii], d1 = D1[ii];
+                    T xv[VW];
+                    load_ct<T, VW>(xsrc + (size_t)ii * MC + cg * VW, xv);
+#pragma unroll
+                    for (int e = 0; e < VW; e += 2) {
+                        fma_pair(a0[e], a0[e + 1], d0, d0, xv[e], xv[e + 1]);
+                        fma_pair(a1[e], a1[e + 1], d1, d1, xv[e], xv[e + 1]);
+                    }
+                }
+#pragma unroll
+                for (int off = CG; off < 32; off <<= 1)
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) {
+                        a0[e] += __shfl_xor_sync(0xffffffffu, a0[e], off);
+                        a1[e] += __shfl_xor_sync(0xffffffffu, a1[e], off);
+                    }
+                if (seg < 2 && jc + seg < ncols) {
+                    T* dst = v.partials + ((long long)(v.n_items + mslot) * v.part_stride + fbase + jc + seg) * MC + cg * VW;
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) dst[e] = seg == 0 ? a0[e] : a1[e];
                 }
             }
-            __syncwarp();
-            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[st])) : "memory");
+            fbase = jend;
+            asm volatile("bar.sync 1, %0;" ::"r"(kThreads) : "memory");  // the slice was read
         }
     }
     if (!ok && lane == 0) atomicExch(&abort_flag, 1);
@@ -2036,6 +2113,12 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(DevView<T> v, T* __re
 #pragma unroll
                 for (int c = 0; c < CT; ++c) acc[c] += x[c];
             }
+            for (int q = v.mirror_by_leaf[leaf]; q < v.mirror_by_leaf[leaf + 1]; ++q) {  // D_st^T x_s
+                T x[CT];
+                load_ct<T, CT>(v.partials + ((long long)(v.n_items + q) * v.part_stride + i) * S + c0 + cq * CT, x);
+#pragma unroll
+                for (int c = 0; c < CT; ++c) acc[c] += x[c];
+            }
             if (h2) {
                 const T* u = su + (it / CQ) * d * ps;
                 int I = 0;
@@ -2156,8 +2239,12 @@ __global__ void __launch_bounds__(kThreads) combine_tiled_kernel(DevView<T> v, T
             const int i = p0 + r;
 #pragma unroll
             for (int c = 0; c < MC; ++c) acc[c] += red[r * MC + c];
-            for (int q = v.items_by_leaf[leaf]; q < v.items_by_leaf[leaf + 1]; ++q) {
-                const T* pp = v.partials + ((long long)q * v.part_stride + i) * S + c0;
+            // the leaf's near item slots, then its mirror slots (D_st^T x_s)
+            const int nq = v.items_by_leaf[leaf + 1] - v.items_by_leaf[leaf];
+            const int nqm = v.mirror_by_leaf[leaf + 1] - v.mirror_by_leaf[leaf];
+            for (int u = 0; u < nq + nqm; ++u) {
+                const long long q = u < nq ? v.items_by_leaf[leaf] + u : v.n_items + v.mirror_by_leaf[leaf] + (u - nq);
+                const T* pp = v.partials + (q * v.part_stride + i) * S + c0;
 #pragma unroll
                 for (int c = 0; c < MC; c += 4) {
                     T x[4];
@@ -2331,6 +2418,44 @@ __global__ void __launch_bounds__(kThreads + 32, 2) coupling_b_tma_kernel(DevVie
     }
 }
 
+// Mirror products for the register-staged near field (mirror sharing, near_kernel): the block
+// (t, s) of a stored block (s, t), s != t, is D_st^T, so its contribution (D_st^T x_s) goes to the
+// block's mirror slot, which combine_kernel adds to leaf t.  One CTA per mirror slot; thread j
+// owns column j of D_st: out[j][c] = sum_i (sum_k w_k G_{b,1}[(j r + k) n_s + i]) x_s[i][c],
+// reading its column of every slab as one contiguous run.  (The bulk-copy near kernel forms these
+// products from the same read of G_{b,1} as the forward ones.)
+template <typename T, int MC>
+__global__ void __launch_bounds__(kThreads) near_mirror_kernel(DevView<T> v, int S, int c0, int maxleaf) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* xsm = reinterpret_cast<T*>(smem_raw);  // n_s x MC
+    T* sw = xsm + (size_t)maxleaf * MC;       // r
+    const int q = blockIdx.x;
+    const int b = v.mslot_block[q];
+    const int snode = v.nb_s[b], tnode = v.nb_t[b];
+    const int sb = v.node_begin[snode], ns = v.node_end[snode] - sb;
+    const int nt = v.node_end[tnode] - v.node_begin[tnode];
+    const int r = v.nb_rank[b];
+    for (int e = threadIdx.x; e < ns * MC; e += blockDim.x) xsm[e] = v.Xc[(long long)(sb + e / MC) * S + c0 + e % MC];
+    for (int k = threadIdx.x; k < r; k += blockDim.x) sw[k] = v.w[v.nb_woff[b] + k];
+    __syncthreads();
+    T* dst = v.partials + (long long)(v.n_items + q) * v.part_stride * S + c0;
+    const T* G = v.near_cores + v.nb_off[b];
+    for (int j = threadIdx.x; j < nt; j += blockDim.x) {
+        T acc[MC];
+#pragma unroll
+        for (int c = 0; c < MC; ++c) acc[c] = T(0);
+        const T* gj = G + (long long)j * r * ns;
+        for (int i = 0; i < ns; ++i) {
+            T dij = T(0);
+            for (int k = 0; k < r; ++k) dij += sw[k] * __ldg(gj + (long long)k * ns + i);
+#pragma unroll
+            for (int c = 0; c < MC; ++c) acc[c] += dij * xsm[i * MC + c];
+        }
+#pragma unroll
+        for (int c = 0; c < MC; ++c) dst[(long long)j * S + c] = acc[c];
+    }
+}
+
 // Adjoint near field: Xbar_t += D_b(theta)^T Ybar_s for every stored near block b = (s, t)
 // (§4.3 blocks, transposed), accumulated into the first partial slot of the source leaf t (the
 // other slots of t are zero), so that combine_kernel adds it like a forward near partial.  One CTA
@@ -2403,11 +2528,14 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
     }
     // bulk-copy pipelined near field when one chunk of right-hand sides covers X (rows of x_t
     // contiguous), rows are 16-byte multiples, leaves fit one CTA and a column of cores fits a stage
-    const size_t sm_ntma = (size_t)nt1::NS * nt1::STB + (size_t)4 * maxleaf * MC * sizeof(T);
+    const size_t sm_ntma = near_tma_smem<T>(maxleaf, MC, v.near_share != 0);
     const bool near_tma = h->use_bulk && S == MC && (MC * sizeof(T)) % 16 == 0 && maxleaf <= kThreads &&
                           (size_t)h->near_rank_max * maxleaf * sizeof(T) <= (size_t)nt1::STAGE &&
                           sm_ntma <= 110 * 1024 && v.n_items > 0;
-    if (adj && v.n_near > 0) {
+    // with mirror sharing the stored near part is symmetric (each pair applied as D and D^T): the
+    // adjoint's near field is the forward one
+    const bool near_adj = adj && !v.near_share;
+    if (near_adj && v.n_near > 0) {
         // adjoint near field: transposed blocks accumulated into zeroed partial slots
         PH_CUDA(cudaMemsetAsync(v.partials, 0, (size_t)std::max(1, v.n_items) * v.part_stride * S * sizeof(T), stream));
         const size_t smem = ((size_t)maxleaf * MC + kMaxNearRank) * sizeof(T);
@@ -2418,7 +2546,7 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
             PH_LAUNCH("near_adjoint_kernel");
         }
     }
-    for (int c0 = 0; c0 < S && !adj; c0 += MC) {
+    for (int c0 = 0; c0 < S && !near_adj; c0 += MC) {
         ProfScope ps(h, 2, stream);
         if (near_tma) {
             h->last_variants |= 1;
@@ -2430,6 +2558,12 @@ void run_matvec(ph_handle* h, DevView<T>& v, const T* X, long long ldx, int m, T
             set_smem<T, MC>((const void*)near_kernel<T, MC>, smem);
             near_kernel<T, MC><<<std::max(1, v.n_items), kThreads, smem, stream>>>(v, S, c0, maxleaf);
             PH_LAUNCH("near_kernel");
+            if (v.n_mslots > 0) {
+                const size_t sm_m = ((size_t)maxleaf * MC + kMaxNearRank) * sizeof(T);
+                set_smem<T, MC>((const void*)near_mirror_kernel<T, MC>, sm_m);
+                near_mirror_kernel<T, MC><<<v.n_mslots, kThreads, sm_m, stream>>>(v, S, c0, maxleaf);
+                PH_LAUNCH("near_mirror_kernel");
+            }
         }
     }
     if (v.n_far_targets > 0) {

@@ -14,7 +14,7 @@
 
 namespace {
 
-const char kMagic[8] = {'P', 'H', 'L', 'I', 'B', '0', '0', '3'};  // 003: tensor-core R_k layout
+const char kMagic[8] = {'P', 'H', 'L', 'I', 'B', '0', '0', '4'};  // 004: near mirror-sharing option
 constexpr int kArenas = 9;  // near, near theta, far, far theta, S/T, U, E, L/R, tensor-core R (this order)
 
 struct Writer {
@@ -194,6 +194,7 @@ extern "C" ph_status ph_load(const char* path, int device, ph_handle** out) {
             sizes[i] = arenas[i].size();
         }
         if (r.left != 0) throw ph::Error(PH_ERR_IO, "trailing bytes after the last arena");
+        ph::near_mirror_map(h);
         ph::validate_handle(*h, sizes);
 
         int ndev = 0;

@@ -122,6 +122,19 @@ void validate_handle(const ph_handle& h, const std::vector<size_t>& arena_bytes)
         need(h.nb_woff[b + 1] == h.nb_woff[b] + r, "near weight offsets");
     }
     need(h.nb_woff[nb] == h.w_elems, "near weight count");
+    // mirror sharing: a mirrored block reads the cores of its stored partner (t, s)
+    need(o.near_unshared == 0 || o.near_unshared == 1, "near sharing option");
+    need_size(h.nb_src, nb, "near core owners");
+    for (size_t b = 0; b < nb; ++b) {
+        const int src = h.nb_src[b];
+        need(src >= 0 && (size_t)src < nb, "near core owner");
+        if ((size_t)src == b) continue;
+        need(o.near_unshared == 0 && h.nb_src[src] == src && p.near_s[src] == p.near_t[b] &&
+                 p.near_t[src] == p.near_s[b],
+             "mirrored near block");
+        need(h.nb_rank[b] == h.nb_rank[src] && h.nb_off[b] == h.nb_off[src] && h.nb_toff[b] == h.nb_toff[src],
+             "mirrored near block offsets");
+    }
 
     // far blocks, translation classes and their cores
     const size_t nf = p.far_s.size();

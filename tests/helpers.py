@@ -11,12 +11,13 @@ TOL = {"fp64": 1e-10, "fp32": 1e-5}
 
 
 def build_pair(P, kernel, lo, hi, degree, p_s, l_max, eta, tol, cap, fmt, prec, dedup=True,
-               targets_every=None, pool=None, check_finite=False, coupling="explicit"):
+               targets_every=None, pool=None, check_finite=False, coupling="explicit", near_shared=True):
     """Returns (product handle, oracle model, oracle target leaves or None)."""
     from paper_2511_03109_gb300 import ph
 
     opts = ph.make_opts(P.shape[1], lo, hi, degree, p_s, l_max, eta, tol, rank_cap=cap or 0,
-                        fmt=fmt, prec=prec, dedup=dedup, check_finite=check_finite, coupling=coupling)
+                        fmt=fmt, prec=prec, dedup=dedup, check_finite=check_finite, coupling=coupling,
+                        near_shared=near_shared)
     A = ph.ParametricMatrix(P, kernel, opts)
     M = pmatrix.ParametricMatrix(P, kernel, lo, hi, degree, p_s, l_max, eta, tol,
                                  rank_cap=cap or None, fmt=fmt)

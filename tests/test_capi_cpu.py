@@ -104,13 +104,13 @@ def test_load_rejects_missing_foreign_old_and_corrupt_files(tmp_path):
     assert load(tmp_path / "missing.ph") == ph.PH_ERR_IO
     (tmp_path / "foreign.ph").write_bytes(b"not a handle at all" * 10)
     assert load(tmp_path / "foreign.ph") == ph.PH_ERR_IO
-    (tmp_path / "old.ph").write_bytes(b"PHLIB002" + bytes(4096))
+    (tmp_path / "old.ph").write_bytes(b"PHLIB003" + bytes(4096))
     assert load(tmp_path / "old.ph") == ph.PH_ERR_IO
-    (tmp_path / "short.ph").write_bytes(b"PHLIB003" + bytes(3))
+    (tmp_path / "short.ph").write_bytes(b"PHLIB004" + bytes(3))
     assert load(tmp_path / "short.ph") == ph.PH_ERR_IO
     # the right magic followed by 8-byte words of 2^40: whichever field reads a length first
     # gets an impossible one
-    (tmp_path / "huge.ph").write_bytes(b"PHLIB003" + struct.pack("<Q", 1 << 40) * 4096)
+    (tmp_path / "huge.ph").write_bytes(b"PHLIB004" + struct.pack("<Q", 1 << 40) * 4096)
     assert load(tmp_path / "huge.ph") == ph.PH_ERR_IO
 
 
@@ -132,7 +132,7 @@ def _handle_file(mutate=None):
     }
     if mutate:
         mutate(f)
-    out = bytearray(b"PHLIB003")
+    out = bytearray(b"PHLIB004")
     vec = lambda fmt, xs: struct.pack("<Q", len(xs)) + struct.pack("<%d%s" % (len(xs), fmt), *xs)
     out += struct.pack("<i", 0)  # kernel: Gaussian
     out += bytes(f["opts"])
@@ -179,6 +179,10 @@ def _other_p_s(f):
     f["opts"].p_s = 3
 
 
+def _bad_sharing_option(f):
+    f["opts"].near_unshared = 2
+
+
 @pytest.mark.parametrize("mutate", [
     _set("nb_off", [1]),            # the block's cores would end one entry past the arena
     _set("perm", 4, 0),             # a permutation entry outside 0..n-1
@@ -189,7 +193,8 @@ def _other_p_s(f):
     _node_end,                      # a node range past n
     _short_near_arena,              # an arena shorter than its element count (length still consistent)
     _other_p_s,                     # options from another build (p_s^d no longer the stored PD)
-], ids=["nb_off", "perm", "near_t", "nb_woff", "rank", "leaves", "node_end", "arena", "p_s"])
+    _bad_sharing_option,            # a near-sharing option that is neither 0 nor 1
+], ids=["nb_off", "perm", "near_t", "nb_woff", "rank", "leaves", "node_end", "arena", "p_s", "sharing"])
 def test_load_refuses_corrupt_contents(tmp_path, mutate):
     """ph_load checks every stored offset, index and size on the host before it touches a
     device: one flipped value in an otherwise consistent file is refused with PH_ERR_IO."""
