@@ -98,6 +98,10 @@ typedef struct {
                               symmetric, so A_ts is a row permutation of A_st and TT-SVD gives the
                               same cores up to that permutation (§4.3): the sharing is exact and
                               halves the near-field stream.  1: compress and store both blocks. */
+    int near_degree[3];    /* Chebyshev degree in theta_i of the near-field tensor grid (§4.3); 0 = degree[i].
+                              The near and far grids are independent: each field interpolates on its own
+                              nodes (the near field often needs fewer, e.g. 5 per dimension for
+                              d_theta = 3).  ph_matvec_batched then applies one theta at a time. */
 } ph_build_opts;
 
 /* Sizes and counts of a built handle; all byte counts are of stored data. */

@@ -184,7 +184,7 @@ class ParametricMatrix:
     """
 
     def __init__(self, points, kernel, theta_lo, theta_hi, degree, p_s, l_max, eta, tol,
-                 rank_cap=None, fmt="h2", leaf_size=None, near_tol=None):
+                 rank_cap=None, fmt="h2", leaf_size=None, near_tol=None, near_degree=None):
         self.P = np.asarray(points, float)
         self.n, self.d = self.P.shape
         self.kernel = kernel
@@ -193,6 +193,9 @@ class ParametricMatrix:
         self.dt = self.theta_lo.size
         self.degree = np.atleast_1d(np.asarray(degree, int))
         self.taxes = theta_grid(self.theta_lo, self.theta_hi, self.degree)
+        # the near field's own theta grid (§4.3 compresses A_b on a grid of its own choosing)
+        self.near_degree = self.degree if near_degree is None else np.atleast_1d(np.asarray(near_degree, int))
+        self.taxes_near = theta_grid(self.theta_lo, self.theta_hi, self.near_degree)
         self.p_s = int(p_s)
         self.eta = float(eta)
         self.tol = float(tol)
@@ -213,7 +216,7 @@ class ParametricMatrix:
     def compress_near(self, b: NearBlock):
         """TT of A_b (§4.3), delta = eps ||A_b||_F / sqrt(d_theta)."""
         if b.cores is None:
-            A = near_tensor(self.kernel, self.P, b.s, b.t, self.taxes)
+            A = near_tensor(self.kernel, self.P, b.s, b.t, self.taxes_near)
             b.cores, _ = tensor.tt_svd(A, self.near_tol, None)
         return b
 
@@ -305,12 +308,39 @@ class ParametricMatrix:
         if deriv is not None and not 0 <= int(deriv) < self.dt:
             raise ValueError("deriv is not a parameter dimension")
         vs = self.parametric_vectors(th, deriv)
+        vs_near = cheb.parametric_vectors(th, self.theta_lo, self.theta_hi, self.near_degree, deriv)
         near, far = self.blocks_for(targets)
         inst = {"theta": th, "vs": vs, "D": {}, "H": {}}
         for b in near:
-            inst["D"][id(b)] = self.near_instance(b, vs)
+            inst["D"][id(b)] = self.near_instance(b, vs_near)
         for b in far:
             inst["H"][id(b)] = H_matrix(b.cores, self.d, vs)
+        return inst
+
+    def projected_cores(self, theta, targets=None):
+        """The exact coupling core of every far block at theta in the gauge of its stored spatial
+        factors: H*_b(theta) = L_b^+ W_b(theta) (R_b^T)^+, the least-squares solution of
+        L_b H R_b^T = W_b(theta), where W_b(theta)[i, j] = kappa(eta^s_i, eta^t_j; theta) is the
+        non-parametric coupling matrix of §3.6.2 (little-endian multi-indices) evaluated at this
+        theta.  It is the target the learned surrogate of the far-field cores is trained on:
+        H_b(theta) is the only theta-dependent far-field quantity (App. A.4), and this is the best
+        one the fixed L_b, R_b admit.  With the interpolation exact (polynomial kernel, theta
+        nodes, no truncation) it equals H_b(theta)."""
+        th = self.check_theta(theta)
+        _, far = self.blocks_for(targets)
+        single = [[float(x)] for x in th]
+        out = {}
+        for b in far:
+            Wt = far_tensor(self.kernel, b.s, b.t, single, self.p_s)
+            W = tensor.freshape(Wt, (self.p_s ** self.d, self.p_s ** self.d))
+            out[id(b)] = np.linalg.pinv(b.L) @ W @ np.linalg.pinv(b.R.T)
+        return out
+
+    def instantiate_projected(self, theta, targets=None):
+        """The online stage with the far-field cores replaced by projected_cores(theta); the near
+        field as instantiate()."""
+        inst = self.instantiate(theta, targets)
+        inst["H"] = self.projected_cores(theta, targets)
         return inst
 
     def coupling(self, b: FarBlock, inst):

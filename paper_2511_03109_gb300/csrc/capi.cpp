@@ -129,8 +129,15 @@ static void fill_view(ph_handle* h, DevView<T>& v, const std::vector<long>& io, 
     v.fb_toff = L + lo[5];
     v.dtheta = h->opts.dtheta;
     for (int k = 0; k < 3; ++k) v.p_theta[k] = (k < h->opts.dtheta) ? h->opts.degree[k] + 1 : 1;
+    // d_dbl: nodes (far grid, near grid), then barycentric weights (far grid, near grid)
     v.theta_nodes = h->d_dbl;
-    v.theta_bw = h->d_dbl + kMaxDim * kMaxPTheta;
+    v.theta_nodes_near = h->d_dbl + kMaxDim * kMaxPTheta;
+    v.theta_bw = h->d_dbl + 2 * kMaxDim * kMaxPTheta;
+    v.theta_bw_near = h->d_dbl + 3 * kMaxDim * kMaxPTheta;
+    for (int k = 0; k < 3; ++k)
+        v.p_theta_near[k] = (k < h->opts.dtheta)
+                                ? (h->opts.near_degree[k] > 0 ? h->opts.near_degree[k] : h->opts.degree[k]) + 1
+                                : 1;
     v.v64 = h->d_v64;
     v.n_near = (int)plan.near_s.size();
     v.near_cores = (const T*)h->d_near;
@@ -522,8 +529,11 @@ ph_status ph_offline_build(const double* points, long n, ph_kernel kernel, const
     if (kernel != PH_KERNEL_ANISO_GAUSS && kernel != PH_KERNEL_POLY2 && o->dtheta != 1)
         return fail(nullptr, PH_ERR_INVALID_ARG, "this kernel has one parameter (d_theta = 1)");
     for (int k = 0; k < o->dtheta; ++k)
-        if (!(o->theta_lo[k] < o->theta_hi[k]) || o->degree[k] < 0 || o->degree[k] + 1 > ph::kMaxPTheta)
+        if (!(o->theta_lo[k] < o->theta_hi[k]) || o->degree[k] < 0 || o->degree[k] + 1 > ph::kMaxPTheta ||
+            o->near_degree[k] < 0 || o->near_degree[k] + 1 > ph::kMaxPTheta)
             return fail(nullptr, PH_ERR_INVALID_ARG, "ph_offline_build: bad parameter box or degree");
+    if (o->near_unshared != 0 && o->near_unshared != 1)
+        return fail(nullptr, PH_ERR_INVALID_ARG, "ph_offline_build: near_unshared must be 0 or 1");
     ph_handle* h = nullptr;
     try {
         h = new ph_handle();

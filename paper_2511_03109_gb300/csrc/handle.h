@@ -31,8 +31,11 @@ struct DevView {
     // theta
     int dtheta;
     int p_theta[3];
-    const double* theta_nodes;  // dtheta x 32
+    const double* theta_nodes;  // dtheta x 32 (far-field grid)
     const double* theta_bw;     // barycentric weights, dtheta x 32
+    const double* theta_nodes_near;  // the near-field grid's nodes and weights, dtheta x 32 each
+    const double* theta_bw_near;
+    int p_theta_near[3];
     double* v64;                // instantiated parametric vectors, dtheta x 32
     // near field
     int n_near;
@@ -124,7 +127,7 @@ struct ph_handle {
     ph_build_opts opts{};
     int device = 0;
     int num_sms = 1;  // streaming multiprocessors of the device (persistent grids)
-    int PD = 0, Delta = 0, p_theta_total = 1;
+    int PD = 0, Delta = 0, p_theta_total = 1, p_theta_near_total = 1;
     size_t scalar = 8;  // sizeof compute type
     ph::Plan plan;
     double offline_seconds = 0;
@@ -148,7 +151,7 @@ struct ph_handle {
     void* d_zbuf = nullptr;
     long long near_elems = 0, near_theta_elems = 0, far_elems = 0, far_theta_elems = 0, H_elems = 0,
               st_elems = 0, w_elems = 0;
-    std::vector<double> theta_nodes, theta_bw;  // dtheta x 32
+    std::vector<double> theta_nodes, theta_bw;  // 2 x 3 x 32: far-field grid, then near-field grid
     std::vector<double> E64;                    // 2 x p_s x p_s
     // device data
     std::vector<DeviceBuffer> buffers;          // every device allocation, freed in ph_destroy

@@ -523,28 +523,45 @@ ph_status offline_build(ph_handle* h, const double* points, long n) {
     if (P > kMaxThetaGrid) throw Error(PH_ERR_UNSUPPORTED, "at most 1024 theta-grid points");
     if (ps < 1 || ps > kMaxPs) throw Error(PH_ERR_INVALID_ARG, "p_s must be 1..16");
 
-    // theta nodes and barycentric weights (dtheta x 32)
-    h->theta_nodes.assign(kMaxDim * kMaxPTheta, 0.0);
-    h->theta_bw.assign(kMaxDim * kMaxPTheta, 0.0);
+    // the near field's own theta grid (near_degree, 0 = degree)
+    int ptn[kMaxDim] = {1, 1, 1};
+    h->p_theta_near_total = 1;
+    for (int k = 0; k < dt; ++k) {
+        ptn[k] = (o.near_degree[k] > 0 ? o.near_degree[k] : o.degree[k]) + 1;
+        h->p_theta_near_total *= ptn[k];
+    }
+    const int Pn = h->p_theta_near_total;
+    if (Pn > kMaxThetaGrid) throw Error(PH_ERR_UNSUPPORTED, "at most 1024 near-field theta-grid points");
+
+    // theta nodes and barycentric weights (3 x 32 per grid: the far-field grid, then the near-field grid)
+    constexpr int kGrid = kMaxDim * kMaxPTheta;
+    h->theta_nodes.assign(2 * kGrid, 0.0);
+    h->theta_bw.assign(2 * kGrid, 0.0);
     for (int k = 0; k < dt; ++k) {
         cheb_nodes(o.theta_lo[k], o.theta_hi[k], pt[k], &h->theta_nodes[k * kMaxPTheta]);
         bary_weights(&h->theta_nodes[k * kMaxPTheta], pt[k], &h->theta_bw[k * kMaxPTheta]);
+        cheb_nodes(o.theta_lo[k], o.theta_hi[k], ptn[k], &h->theta_nodes[kGrid + k * kMaxPTheta]);
+        bary_weights(&h->theta_nodes[kGrid + k * kMaxPTheta], ptn[k], &h->theta_bw[kGrid + k * kMaxPTheta]);
     }
-    std::vector<double> grid(P * dt);  // theta grid points, k_1 fastest
-    for (int idx = 0; idx < P; ++idx) {
-        int rest = idx;
-        for (int k = 0; k < dt; ++k) {
-            grid[idx * dt + k] = h->theta_nodes[k * kMaxPTheta + rest % pt[k]];
-            rest /= pt[k];
+    auto grid_points = [&](const int* p, int count, const double* nodes) {
+        std::vector<double> g((size_t)count * dt);  // grid points, k_1 fastest
+        for (int idx = 0; idx < count; ++idx) {
+            int rest = idx;
+            for (int k = 0; k < dt; ++k) {
+                g[(size_t)idx * dt + k] = nodes[k * kMaxPTheta + rest % p[k]];
+                rest /= p[k];
+            }
         }
-    }
+        return g;
+    };
+    const std::vector<double> gridn = grid_points(ptn, Pn, &h->theta_nodes[kGrid]);
 
     // points in cluster order
     std::vector<double> pts(n * d);
     for (long i = 0; i < n; ++i)
         for (int k = 0; k < d; ++k) pts[i * d + k] = points[(long)plan.perm[i] * d + k];
     double* d_pts = upload_vec(h, pts);
-    double* d_grid = upload_vec(h, grid);
+    double* d_gridn = upload_vec(h, gridn);
 
     // ------------------------------------------------------------------ near field
     // Compressed blocks: all near blocks, or with mirror sharing those (s, t) with s <= t; a
@@ -562,8 +579,8 @@ ph_status offline_build(ph_handle* h, const double* points, long n) {
         const Node& t = plan.nodes[plan.near_t[bl[q]]];
         sb[q] = s.begin; sn[q] = s.size(); tb[q] = t.begin; tn[q] = t.size();
     }
-    NearBuild nbld{(int)h->kernel, d, P, dt, d_pts, upload_vec(h, sb), upload_vec(h, sn), upload_vec(h, tb),
-                   upload_vec(h, tn), d_grid};
+    NearBuild nbld{(int)h->kernel, d, Pn, dt, d_pts, upload_vec(h, sb), upload_vec(h, sn), upload_vec(h, tb),
+                   upload_vec(h, tn), d_gridn};
     h->nb_rank.assign(nnear, 0);
     h->nb_off.assign(nnear, 0);
     h->nb_toff.assign(nnear, 0);
@@ -571,34 +588,34 @@ ph_status offline_build(ph_handle* h, const double* points, long n) {
     std::vector<double> near_theta;
     if (nn > 0) {
         const double ntol = (o.near_tol >= 0) ? o.near_tol : o.tol;
-        // per block, from the first TT cut of A_b (rows x P): the rank r_{b,1}, the theta matrix W
-        // (near_theta_matrix) and V_r (P x r, packed for the projection G_{b,1} = A_b V_r)
+        // per block, from the first TT cut of A_b (rows x Pn): the rank r_{b,1}, the theta matrix W
+        // (near_theta_matrix) and V_r (Pn x r, packed for the projection G_{b,1} = A_b V_r)
         std::vector<double> vr_pack;
         std::vector<long long> voff(nn, 0);
         long long off = 0, toff = 0;
-        auto finish_block = [&](int q, const double* s, const double* V) {  // s descending, V P x P
+        auto finish_block = [&](int q, const double* s, const double* V) {  // s descending, V Pn x Pn
             double fro2 = 0.0;
-            for (int k = 0; k < P; ++k) fro2 += s[k] * s[k];
+            for (int k = 0; k < Pn; ++k) fro2 += s[k] * s[k];
             const double delta2 = ntol * ntol * fro2 / dt;
-            const int r = choose_rank_sv(s, P, delta2, kMaxNearRank);
+            const int r = choose_rank_sv(s, Pn, delta2, kMaxNearRank);
             const int b = bl[q];
             h->nb_rank[b] = r;
             h->nb_off[b] = off;
             h->nb_toff[b] = toff;
             off += (long long)sn[q] * tn[q] * r;
-            toff += (long long)r * P;
-            const std::vector<double> W = near_theta_matrix(s, V, P, r, pt, dt, delta2);
+            toff += (long long)r * Pn;
+            const std::vector<double> W = near_theta_matrix(s, V, Pn, r, ptn, dt, delta2);
             near_theta.insert(near_theta.end(), W.begin(), W.end());
             voff[q] = (long long)vr_pack.size();
-            vr_pack.insert(vr_pack.end(), V, V + (size_t)P * r);
+            vr_pack.insert(vr_pack.end(), V, V + (size_t)Pn * r);
         };
-        if (P <= 32) {
-            // R_b of every block by TSQR, then a batched Jacobi SVD of the P x P factors
-            double* d_R = (double*)dev_alloc(h, (size_t)nn * P * P * sizeof(double));
-            double* d_S = (double*)dev_alloc(h, (size_t)nn * P * sizeof(double));
-            double* d_U = (double*)dev_alloc(h, (size_t)nn * P * P * sizeof(double));
-            double* d_V = (double*)dev_alloc(h, (size_t)nn * P * P * sizeof(double));
-            size_t smem = ((size_t)(P + kChunk) * P + (size_t)kChunk * P) * sizeof(double);
+        if (Pn <= 32) {
+            // R_b of every block by TSQR, then a batched Jacobi SVD of the Pn x Pn factors
+            double* d_R = (double*)dev_alloc(h, (size_t)nn * Pn * Pn * sizeof(double));
+            double* d_S = (double*)dev_alloc(h, (size_t)nn * Pn * sizeof(double));
+            double* d_U = (double*)dev_alloc(h, (size_t)nn * Pn * Pn * sizeof(double));
+            double* d_V = (double*)dev_alloc(h, (size_t)nn * Pn * Pn * sizeof(double));
+            size_t smem = ((size_t)(Pn + kChunk) * Pn + (size_t)kChunk * Pn) * sizeof(double);
             PH_CUDA(cudaFuncSetAttribute(near_tsqr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             near_tsqr_kernel<<<nn, 256, smem>>>(nbld, d_R, kChunk);
             PH_LAUNCH("near_tsqr_kernel");
@@ -618,54 +635,54 @@ ph_status offline_build(ph_handle* h, const double* points, long n) {
             PH_SOLVER(cusolverDnXgesvdjSetMaxSweeps(params, 100));
             PH_SOLVER(cusolverDnXgesvdjSetSortEig(params, 1));
             int lwork = 0;
-            PH_SOLVER(cusolverDnDgesvdjBatched_bufferSize(sol, CUSOLVER_EIG_MODE_VECTOR, P, P, d_R, P, d_S, d_U, P,
-                                                          d_V, P, &lwork, params, nn));
+            PH_SOLVER(cusolverDnDgesvdjBatched_bufferSize(sol, CUSOLVER_EIG_MODE_VECTOR, Pn, Pn, d_R, Pn, d_S, d_U, Pn,
+                                                          d_V, Pn, &lwork, params, nn));
             double* d_work = (double*)dev_alloc(h, (size_t)std::max(lwork, 1) * sizeof(double));
             int* d_info = (int*)dev_alloc(h, (size_t)nn * sizeof(int));
-            PH_SOLVER(cusolverDnDgesvdjBatched(sol, CUSOLVER_EIG_MODE_VECTOR, P, P, d_R, P, d_S, d_U, P, d_V, P,
+            PH_SOLVER(cusolverDnDgesvdjBatched(sol, CUSOLVER_EIG_MODE_VECTOR, Pn, Pn, d_R, Pn, d_S, d_U, Pn, d_V, Pn,
                                                d_work, lwork, d_info, params, nn));
             std::vector<int> infos(nn);
             PH_CUDA(cudaMemcpy(infos.data(), d_info, nn * sizeof(int), cudaMemcpyDeviceToHost));
             for (int b = 0; b < nn; ++b)
                 if (infos[b] != 0) throw Error(PH_ERR_CUDA, "batched Jacobi SVD did not converge");
-            std::vector<double> sv((size_t)nn * P), vecs((size_t)nn * P * P);
+            std::vector<double> sv((size_t)nn * Pn), vecs((size_t)nn * Pn * Pn);
             PH_CUDA(cudaMemcpy(sv.data(), d_S, sv.size() * sizeof(double), cudaMemcpyDeviceToHost));
             PH_CUDA(cudaMemcpy(vecs.data(), d_V, vecs.size() * sizeof(double), cudaMemcpyDeviceToHost));
-            for (int b = 0; b < nn; ++b) finish_block(b, &sv[(size_t)b * P], &vecs[(size_t)b * P * P]);
+            for (int b = 0; b < nn; ++b) finish_block(b, &sv[(size_t)b * Pn], &vecs[(size_t)b * Pn * Pn]);
             for (void* p : {(void*)d_R, (void*)d_S, (void*)d_U, (void*)d_V, (void*)d_work, (void*)d_info}) dev_free(h, p);
-        } else if (P <= 128) {
+        } else if (Pn <= 128) {
             // 33..128 theta-grid points: R_b by TSQR (row chunks sized to shared memory), then a
-            // one-sided Jacobi SVD of each P x P factor on the host (FP64, one thread per block at a
+            // one-sided Jacobi SVD of each Pn x Pn factor on the host (FP64, one thread per block at a
             // time), which keeps singular values near the truncation threshold and the kept
             // subspaces accurate to rounding (so the kept ranks are the oracle's)
             int chunk = 256;
-            while (chunk > 16 && ((size_t)(P + chunk) * P + (size_t)chunk * P) * sizeof(double) > 200 * 1024) chunk /= 2;
-            const size_t smem = ((size_t)(P + chunk) * P + (size_t)chunk * P) * sizeof(double);
-            double* d_R = (double*)dev_alloc(h, (size_t)nn * P * P * sizeof(double));
+            while (chunk > 16 && ((size_t)(Pn + chunk) * Pn + (size_t)chunk * Pn) * sizeof(double) > 200 * 1024) chunk /= 2;
+            const size_t smem = ((size_t)(Pn + chunk) * Pn + (size_t)chunk * Pn) * sizeof(double);
+            double* d_R = (double*)dev_alloc(h, (size_t)nn * Pn * Pn * sizeof(double));
             PH_CUDA(cudaFuncSetAttribute(near_tsqr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             near_tsqr_kernel<<<nn, 256, smem>>>(nbld, d_R, chunk);
             PH_LAUNCH("near_tsqr_kernel");
-            std::vector<double> Rall((size_t)nn * P * P);
+            std::vector<double> Rall((size_t)nn * Pn * Pn);
             PH_CUDA(cudaMemcpy(Rall.data(), d_R, Rall.size() * sizeof(double), cudaMemcpyDeviceToHost));
             dev_free(h, d_R);
-            std::vector<double> sv((size_t)nn * P), vecs((size_t)nn * P * P);
+            std::vector<double> sv((size_t)nn * Pn), vecs((size_t)nn * Pn * Pn);
             const int nthr = std::max(1, std::min(64, (int)std::thread::hardware_concurrency()));
             std::vector<std::thread> pool;
             std::atomic<int> next{0};
             for (int w = 0; w < nthr; ++w)
                 pool.emplace_back([&]() {
-                    std::vector<double> R((size_t)P * P), U, sg, Vt;
+                    std::vector<double> R((size_t)Pn * Pn), U, sg, Vt;
                     for (int b = next++; b < nn; b = next++) {
-                        std::copy(Rall.begin() + (size_t)b * P * P, Rall.begin() + (size_t)(b + 1) * P * P, R.begin());
-                        svd_small(P, P, R, U, sg, Vt);
-                        for (int k = 0; k < P; ++k) {
-                            sv[(size_t)b * P + k] = sg[k];
-                            for (int t = 0; t < P; ++t) vecs[(size_t)b * P * P + t + (size_t)P * k] = Vt[k + (size_t)P * t];
+                        std::copy(Rall.begin() + (size_t)b * Pn * Pn, Rall.begin() + (size_t)(b + 1) * Pn * Pn, R.begin());
+                        svd_small(Pn, Pn, R, U, sg, Vt);
+                        for (int k = 0; k < Pn; ++k) {
+                            sv[(size_t)b * Pn + k] = sg[k];
+                            for (int t = 0; t < Pn; ++t) vecs[(size_t)b * Pn * Pn + t + (size_t)Pn * k] = Vt[k + (size_t)Pn * t];
                         }
                     }
                 });
             for (auto& th : pool) th.join();
-            for (int b = 0; b < nn; ++b) finish_block(b, &sv[(size_t)b * P], &vecs[(size_t)b * P * P]);
+            for (int b = 0; b < nn; ++b) finish_block(b, &sv[(size_t)b * Pn], &vecs[(size_t)b * Pn * Pn]);
         } else {
             // more than 128 theta-grid points (the triangular factor no longer fits in shared
             // memory): the right singular vectors and singular values of A_b come from the
@@ -675,11 +692,11 @@ ph_status offline_build(ph_handle* h, const double* points, long n) {
             // eps s_1^2 / (s_r^2 - s_{r+1}^2): adequate for FP32 handles at tolerances >= 1e-5.
             long long maxrows = 1;
             for (int b = 0; b < nn; ++b) maxrows = std::max(maxrows, (long long)sn[b] * tn[b]);
-            const long long per = maxrows * P * (long long)sizeof(double);
+            const long long per = maxrows * Pn * (long long)sizeof(double);
             const int batch = (int)std::max(1LL, std::min((long long)nn, (2LL << 30) / per));
             double* d_A = (double*)dev_alloc(h, (size_t)batch * per);
-            double* d_G = (double*)dev_alloc(h, (size_t)batch * P * P * sizeof(double));
-            double* d_L = (double*)dev_alloc(h, (size_t)batch * P * sizeof(double));
+            double* d_G = (double*)dev_alloc(h, (size_t)batch * Pn * Pn * sizeof(double));
+            double* d_L = (double*)dev_alloc(h, (size_t)batch * Pn * sizeof(double));
             int* d_info = (int*)dev_alloc(h, (size_t)batch * sizeof(int));
             struct Libs {  // released on every exit path
                 cublasHandle_t blas = nullptr;
@@ -696,11 +713,11 @@ ph_status offline_build(ph_handle* h, const double* points, long n) {
             PH_SOLVER(cusolverDnCreateParams(&lib.prm));
             size_t wdev = 0, whost = 0;
             PH_SOLVER(cusolverDnXsyevBatched_bufferSize(lib.sol, lib.prm, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER,
-                                                        P, CUDA_R_64F, d_G, P, CUDA_R_64F, d_L, CUDA_R_64F, &wdev,
+                                                        Pn, CUDA_R_64F, d_G, Pn, CUDA_R_64F, d_L, CUDA_R_64F, &wdev,
                                                         &whost, batch));
             void* d_work = dev_alloc(h, std::max<size_t>(wdev, 8));
             std::vector<unsigned char> h_work(std::max<size_t>(whost, 8));
-            std::vector<double> lam((size_t)batch * P), vec((size_t)batch * P * P), s(P), V((size_t)P * P);
+            std::vector<double> lam((size_t)batch * Pn), vec((size_t)batch * Pn * Pn), s(Pn), V((size_t)Pn * Pn);
             std::vector<int> infos(batch);
             const double one = 1.0, zero = 0.0;
             for (int b0 = 0; b0 < nn; b0 += batch) {
@@ -708,23 +725,23 @@ ph_status offline_build(ph_handle* h, const double* points, long n) {
                 const long long total = (long long)nb * maxrows;
                 near_form_kernel<<<(int)std::min<long long>(ceil_div(total, 256), 65535), 256>>>(nbld, b0, nb, maxrows, d_A);
                 PH_LAUNCH("near_form_kernel");
-                PH_BLAS(cublasDgemmStridedBatched(lib.blas, CUBLAS_OP_T, CUBLAS_OP_N, P, P, (int)maxrows, &one, d_A,
-                                                  (int)maxrows, maxrows * P, d_A, (int)maxrows, maxrows * P, &zero, d_G,
-                                                  P, (long long)P * P, nb));
-                PH_SOLVER(cusolverDnXsyevBatched(lib.sol, lib.prm, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, P,
-                                                 CUDA_R_64F, d_G, P, CUDA_R_64F, d_L, CUDA_R_64F, d_work, wdev,
+                PH_BLAS(cublasDgemmStridedBatched(lib.blas, CUBLAS_OP_T, CUBLAS_OP_N, Pn, Pn, (int)maxrows, &one, d_A,
+                                                  (int)maxrows, maxrows * Pn, d_A, (int)maxrows, maxrows * Pn, &zero, d_G,
+                                                  Pn, (long long)Pn * Pn, nb));
+                PH_SOLVER(cusolverDnXsyevBatched(lib.sol, lib.prm, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, Pn,
+                                                 CUDA_R_64F, d_G, Pn, CUDA_R_64F, d_L, CUDA_R_64F, d_work, wdev,
                                                  h_work.data(), whost, d_info, nb));
                 PH_CUDA(cudaMemcpy(infos.data(), d_info, nb * sizeof(int), cudaMemcpyDeviceToHost));
                 for (int i = 0; i < nb; ++i)
                     if (infos[i] != 0) throw Error(PH_ERR_CUDA, "batched symmetric eigensolver failed");
-                PH_CUDA(cudaMemcpy(lam.data(), d_L, (size_t)nb * P * sizeof(double), cudaMemcpyDeviceToHost));
-                PH_CUDA(cudaMemcpy(vec.data(), d_G, (size_t)nb * P * P * sizeof(double), cudaMemcpyDeviceToHost));
+                PH_CUDA(cudaMemcpy(lam.data(), d_L, (size_t)nb * Pn * sizeof(double), cudaMemcpyDeviceToHost));
+                PH_CUDA(cudaMemcpy(vec.data(), d_G, (size_t)nb * Pn * Pn * sizeof(double), cudaMemcpyDeviceToHost));
                 for (int i = 0; i < nb; ++i) {
                     // eigenvalues ascending: reverse to singular values descending
-                    for (int k = 0; k < P; ++k) {
-                        const int src = P - 1 - k;
-                        s[k] = std::sqrt(std::max(0.0, lam[(size_t)i * P + src]));
-                        for (int t = 0; t < P; ++t) V[t + (size_t)P * k] = vec[(size_t)i * P * P + t + (size_t)P * src];
+                    for (int k = 0; k < Pn; ++k) {
+                        const int src = Pn - 1 - k;
+                        s[k] = std::sqrt(std::max(0.0, lam[(size_t)i * Pn + src]));
+                        for (int t = 0; t < Pn; ++t) V[t + (size_t)Pn * k] = vec[(size_t)i * Pn * Pn + t + (size_t)Pn * src];
                     }
                     finish_block(b0 + i, s.data(), V.data());
                 }
@@ -752,11 +769,11 @@ ph_status offline_build(ph_handle* h, const double* points, long n) {
         double* d_vr = upload_vec(h, vr_pack);
         long long* d_voff = upload_vec(h, voff);
         h->d_near = dev_alloc(h, (size_t)off * h->scalar);
-        // rows of A_b per projection chunk: shared memory chunk x P + P x r_max doubles within 96 KB
+        // rows of A_b per projection chunk: shared memory chunk x Pn + Pn x r_max doubles within 96 KB
         const int rmax = *std::max_element(h->nb_rank.begin(), h->nb_rank.end());
         int chunk = 256;
-        while (chunk > 16 && ((size_t)chunk * P + (size_t)P * rmax) * sizeof(double) > 160 * 1024) chunk /= 2;
-        size_t smem2 = ((size_t)chunk * P + (size_t)P * rmax) * sizeof(double);
+        while (chunk > 16 && ((size_t)chunk * Pn + (size_t)Pn * rmax) * sizeof(double) > 160 * 1024) chunk /= 2;
+        size_t smem2 = ((size_t)chunk * Pn + (size_t)Pn * rmax) * sizeof(double);
         if (o.prec == PH_FP32) {
             PH_CUDA(cudaFuncSetAttribute(near_project_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem2));

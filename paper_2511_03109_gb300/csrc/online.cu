@@ -105,20 +105,23 @@ __global__ void instantiate_kernel(DevView<T> v, double th0, double th1, double 
     const double th[3] = {th0, th1, th2};
     parametric_vectors(v.theta_nodes, v.theta_bw, v.p_theta, v.dtheta, th, deriv, sv);
     __syncthreads();
+    __shared__ double svn[kMaxDim][kMaxPTheta];  // the near field's own grid
+    if ((int)blockIdx.x < near_ctas) parametric_vectors(v.theta_nodes_near, v.theta_bw_near, v.p_theta_near, v.dtheta, th, deriv, svn);
+    __syncthreads();
     const int dt = v.dtheta;
     if (blockIdx.x == 0)
         for (int e = threadIdx.x; e < dt * kMaxPTheta; e += blockDim.x)
             v.v64[e] = ((e % kMaxPTheta) < v.p_theta[e / kMaxPTheta]) ? sv[e / kMaxPTheta][e % kMaxPTheta] : 0.0;
     int P = 1;
-    for (int i = 0; i < dt; ++i) P *= v.p_theta[i];
+    for (int i = 0; i < dt; ++i) P *= v.p_theta_near[i];
     if ((int)blockIdx.x < near_ctas) {
-        // tensor-product weights, theta-grid index t = k_1 + p_1 (k_2 + p_2 k_3)
+        // tensor-product weights of the near grid, theta-grid index t = k_1 + p_1 (k_2 + p_2 k_3)
         for (int t = threadIdx.x; t < P; t += blockDim.x) {
             double w = 1.0;
             int rest = t;
             for (int i = 0; i < dt; ++i) {
-                w *= sv[i][rest % v.p_theta[i]];
-                rest /= v.p_theta[i];
+                w *= svn[i][rest % v.p_theta_near[i]];
+                rest /= v.p_theta_near[i];
             }
             vprod[t] = w;
         }
@@ -2879,7 +2882,9 @@ ph_status online_matvec_batched(ph_handle* h, const double* thetas, int n_theta,
     // FP32 derivatives always take the direct route: the derivative weights alternate in sign and
     // grow like p^2 / (theta_hi - theta_lo), so combining FP32 node products would amplify their
     // rounding; the direct route cancels in FP64 inside the instantiation
-    if (h->opts.dtheta != 1 || n_theta < p || (deriv >= 0 && h->opts.prec == PH_FP32)) {
+    // (the node combination needs one theta grid for both fields)
+    const bool one_grid = h->opts.near_degree[0] == 0 || h->opts.near_degree[0] == h->opts.degree[0];
+    if (h->opts.dtheta != 1 || !one_grid || n_theta < p || (deriv >= 0 && h->opts.prec == PH_FP32)) {
         // one instantiation and product per theta
         for (int t = 0; t < n_theta; ++t) {
             online_instantiate(h, thetas + t, stream, deriv);

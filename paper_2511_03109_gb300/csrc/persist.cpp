@@ -14,7 +14,7 @@
 
 namespace {
 
-const char kMagic[8] = {'P', 'H', 'L', 'I', 'B', '0', '0', '4'};  // 004: near mirror-sharing option
+const char kMagic[8] = {'P', 'H', 'L', 'I', 'B', '0', '0', '4'};  // 004: near mirror sharing, near-field grid
 constexpr int kArenas = 9;  // near, near theta, far, far theta, S/T, U, E, L/R, tensor-core R (this order)
 
 struct Writer {
@@ -85,6 +85,7 @@ void scalars_io(IO& io, H& h) {
     io.val(h.PD);
     io.val(h.Delta);
     io.val(h.p_theta_total);
+    io.val(h.p_theta_near_total);
     io.val(h.scalar);
     io.val(h.offline_seconds);
     io.vec(h.nb_rank);

@@ -49,15 +49,18 @@ void validate_handle(const ph_handle& h, const std::vector<size_t>& arena_bytes)
     need(o.coupling == 0 || o.coupling == 1, "coupling mode");
     need((int)h.kernel >= 0 && (int)h.kernel <= PH_KERNEL_POLY2, "kernel");
     need(h.scalar == (o.prec == PH_FP32 ? 4u : 8u), "scalar size");
-    int PD = 1, P = 1;
+    int PD = 1, Pf = 1, P = 1;  // P: the near-field grid
     for (int k = 0; k < o.d; ++k) PD *= o.p_s;
     for (int k = 0; k < o.dtheta; ++k) {
         need(o.degree[k] >= 0 && o.degree[k] + 1 <= kMaxPTheta, "theta degree");
-        P *= o.degree[k] + 1;
+        need(o.near_degree[k] >= 0 && o.near_degree[k] + 1 <= kMaxPTheta, "near-field theta degree");
+        Pf *= o.degree[k] + 1;
+        P *= (o.near_degree[k] > 0 ? o.near_degree[k] : o.degree[k]) + 1;
     }
-    need(h.PD == PD && h.Delta == 2 * o.d + o.dtheta && h.p_theta_total == P, "derived sizes");
-    need_size(h.theta_nodes, (size_t)kMaxDim * kMaxPTheta, "theta nodes");
-    need_size(h.theta_bw, (size_t)kMaxDim * kMaxPTheta, "barycentric weights");
+    need(h.PD == PD && h.Delta == 2 * o.d + o.dtheta && h.p_theta_total == Pf && h.p_theta_near_total == P,
+         "derived sizes");
+    need_size(h.theta_nodes, (size_t)2 * kMaxDim * kMaxPTheta, "theta nodes");
+    need_size(h.theta_bw, (size_t)2 * kMaxDim * kMaxPTheta, "barycentric weights");
     need_size(h.E64, (size_t)2 * o.p_s * o.p_s, "transfer factors");
 
     // cluster tree

@@ -40,7 +40,8 @@ class BuildOpts(C.Structure):
                 ("l_max", C.c_int), ("eta", C.c_double), ("tol", C.c_double),
                 ("near_tol", C.c_double), ("rank_cap", C.c_int), ("fmt", C.c_int),
                 ("prec", C.c_int), ("dedup", C.c_int), ("check_finite", C.c_int),
-                ("device", C.c_int), ("coupling", C.c_int), ("near_unshared", C.c_int)]
+                ("device", C.c_int), ("coupling", C.c_int), ("near_unshared", C.c_int),
+                ("near_degree", C.c_int * 3)]
 
 
 class Info(C.Structure):
@@ -123,7 +124,7 @@ def check(status, handle=None):
 
 def make_opts(d, theta_lo, theta_hi, degree, p_s, l_max, eta, tol, rank_cap=0, fmt="h2",
               prec="fp32", dedup=True, check_finite=False, near_tol=-1.0, device=0,
-              coupling="explicit", near_shared=True) -> BuildOpts:
+              coupling="explicit", near_shared=True, near_degree=None) -> BuildOpts:
     o = BuildOpts()
     o.d = d
     o.dtheta = len(theta_lo)
@@ -141,6 +142,8 @@ def make_opts(d, theta_lo, theta_hi, degree, p_s, l_max, eta, tol, rank_cap=0, f
     o.device = int(device)
     o.coupling = {"explicit": 0, "chain": 1}[coupling]
     o.near_unshared = 0 if near_shared else 1
+    for k in range(len(theta_lo)):
+        o.near_degree[k] = 0 if near_degree is None else int(near_degree[k])
     return o
 
 

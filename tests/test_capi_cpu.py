@@ -136,7 +136,7 @@ def _handle_file(mutate=None):
     vec = lambda fmt, xs: struct.pack("<Q", len(xs)) + struct.pack("<%d%s" % (len(xs), fmt), *xs)
     out += struct.pack("<i", 0)  # kernel: Gaussian
     out += bytes(f["opts"])
-    out += struct.pack("<iii", f["PD"], f["Delta"], f["P"])
+    out += struct.pack("<iiii", f["PD"], f["Delta"], f["P"], f["P"])  # far and near theta-grid sizes
     out += struct.pack("<Qd", f["scalar"], 0.0)
     out += vec("i", f["nb_rank"]) + vec("q", f["nb_off"]) + vec("q", f["nb_toff"]) + vec("i", f["nb_woff"])
     out += vec("i", []) + vec("q", []) + vec("q", [])          # key ranks, core offsets, H offsets
@@ -144,7 +144,7 @@ def _handle_file(mutate=None):
     out += vec("q", []) + struct.pack("<q", 0)                   # L/R offsets, L/R elements
     out += vec("q", []) + struct.pack("<q", 0)                   # tensor-core offsets, elements
     out += struct.pack("<7q", f["near_elems"], f["near_theta_elems"], 0, 0, 0, 0, f["w_elems"])
-    out += vec("d", [0.0] * 96) + vec("d", [0.0] * 96) + vec("d", [0.0] * 8)
+    out += vec("d", [0.0] * 192) + vec("d", [0.0] * 192) + vec("d", [0.0] * 8)  # nodes, weights (2 grids), E
     out += struct.pack("<iqi", 1, 4, 0)                          # plan: d, n, depth
     for key in ("perm", "leaves", "near_s", "near_t"):
         out += vec("i", f[key])
