@@ -130,6 +130,9 @@ typedef struct {
     int kernel_variants;     /* kernels the last ph_matvec on this handle launched: bit 0 the
                                 bulk-copy near field, bit 1 the bulk-copy phase 2 of the
                                 coupling, bit 2 the tensor-core phase 1 (0 before any call) */
+    long far_core_elems;     /* sum over translation classes of r_d r_{d+d_theta}: the instantiated
+                                far-field cores H_k(theta) (and the surrogate's outputs) */
+    int p_theta_near[3];     /* nodes per parameter dimension of the near-field grid */
 } ph_info;
 
 /* Build the parametric matrix (offline stage).
@@ -259,6 +262,91 @@ ph_status ph_selftest_timeout(ph_handle* h, void* stream);
  * allocation failed in ph_matvec stays valid (destroy it, or switch the injection off and
  * call again).  Affects every handle of the process; always returns PH_OK. */
 ph_status ph_inject_alloc_failure(long after);
+
+/* ------------------------------------------------------------------------------------------
+ * Learned surrogate of the far-field cores.  The paper names learning the theta-dependence as
+ * future work (§7); this part is an extension, not the paper's method.  In the H^2 format with
+ * the explicit coupling (coupling = 0) the only theta-dependent far-field quantity is the core
+ * H_k(theta) of each translation class (App. A.4); the spatial factors L_k, R_k stay fixed.  A
+ * perceptron theta -> (H_k(theta))_k replaces the polynomial contraction of the stored theta
+ * cores when its validation error passes the acceptance test; otherwise the polynomial path stays.
+ * None of these calls changes the polynomial data.  The network is not written by ph_save.
+ * ------------------------------------------------------------------------------------------ */
+
+/* The exact far-field cores in the gauge of the stored spatial factors, for n_theta parameters:
+ *   H*_k(theta) = (L_k^T L_k)^{-1} L_k^T W_k(theta) R_k (R_k^T R_k)^{-1},
+ * the least-squares solution of L_k H R_k^T = W_k(theta), W_k(theta) the coupling matrix of §3.6.2
+ * (the kernel on the Chebyshev grids of the class's representative boxes) at theta.  These are the
+ * surrogate's training targets.
+ *   thetas : host, n_theta x d_theta (row-major), each inside the box (PH_ERR_THETA_OUT_OF_BOX).
+ *   out    : device, n_theta x ph_info.far_core_elems scalars of the handle's precision; core k of
+ *            theta t at out[t * far_core_elems + (offset of class k)], column-major r_d x r_{d+d_theta}
+ *            (the layout ph_instantiate_cores reads).
+ * H^2 with coupling = 0 only (else PH_ERR_UNSUPPORTED).  Asynchronous on `stream` after a
+ * synchronous first-call set-up (the factors' Gram matrices, on the host in FP64). */
+ph_status ph_far_project(ph_handle* h, const double* thetas, int n_theta, void* out, void* stream);
+
+/* Instantiate at theta (as ph_instantiate for the near field) with the far-field cores copied from
+ * `cores` (device, far_core_elems scalars in the layout of ph_far_project) instead of the
+ * polynomial contraction.  Asynchronous. */
+ph_status ph_instantiate_cores(ph_handle* h, const double* theta, const void* cores, void* stream);
+
+/* Training options of the surrogate (zero fields take the default in brackets). */
+typedef struct {
+    int hidden;              /* width of both hidden layers [256] */
+    int steps;               /* Adam steps [2000] */
+    int batch;               /* samples per step [256] */
+    double lr;               /* Adam learning rate, decayed by a cosine to lr / 100 [1e-3] */
+    double accept_tol;       /* acceptance on the RMS validation error (ph_surrogate_report): > 0 accept
+                                when the network's is at most this; 0 [default] accept when it is at
+                                most the polynomial path's */
+    unsigned long long seed; /* initial weights ~ N(0, 1 / fan_in) from this seed, and the batch order */
+} ph_surrogate_opts;
+
+/* What ph_surrogate_train measured on the validation thetas t, with E_t = ||H_t - H*_t|| the
+ * Frobenius norm of the error of all classes' cores at t and S = sqrt(mean_t ||H*_t||^2) their RMS size:
+ *   rms = sqrt(sum_t E_t^2 / sum_t ||H*_t||^2),   max = max_t E_t / S.
+ * (Per-theta relative errors would be dominated by the thetas where the far field is negligible,
+ * e.g. the shortest length scales.) */
+typedef struct {
+    long params;             /* weights and biases of the network */
+    long out_dim;            /* network outputs (= far_core_elems) */
+    double loss_first, loss_last;  /* training loss of the first and the last step (scaled targets) */
+    double val_err_net_rms, val_err_net_max;     /* the network's cores */
+    double val_err_poly_rms, val_err_poly_max;   /* the polynomial path's cores */
+    double targets_seconds, train_seconds;       /* wall time: targets (ph_far_project), training */
+    int accepted;            /* 1: ph_surrogate_use may switch the network on */
+} ph_surrogate_report;
+
+/* Train the surrogate on the GPU (forward, backward and Adam kernels of this library; BF16 weight
+ * copies in the matrix products with FP32 accumulation, FP32 master weights):
+ *   u = 2 (theta - lo) / (hi - lo) - 1,  h1 = gelu(W1 u + b1),  h2 = gelu(W2 h1 + b2),
+ *   y = W3 h2 + b3,  H_k(theta) = s_k y_k,
+ * gelu(x) = x Phi(x) (exact), s_k the RMS of class k's training targets.  Loss: mean squared error
+ * of y against the targets H*_k / s_k.  thetas_train / thetas_val: host, n x d_theta, inside the box
+ * (the caller draws them).  The acceptance test compares the network's validation error with
+ * opts->accept_tol or with the polynomial cores' (see ph_surrogate_opts).  rep may be NULL.
+ * A later call replaces the network.  Synchronous. */
+ph_status ph_surrogate_train(ph_handle* h, const double* thetas_train, int n_train, const double* thetas_val,
+                             int n_val, const ph_surrogate_opts* opts, ph_surrogate_report* rep, void* stream);
+
+/* enable = 1: ph_instantiate takes the far-field cores from the trained network (one forward pass
+ * per theta); PH_ERR_UNSUPPORTED if no network was accepted (the polynomial path stays).  enable = 0
+ * goes back to the polynomial path.  ph_instantiate_derivative and ph_matvec_batched's node
+ * combination always use the polynomial path. */
+ph_status ph_surrogate_use(ph_handle* h, int enable);
+
+/* Test hook for the network kernels alone: one forward pass, loss and backward pass of a
+ * perceptron n_in -> hidden -> hidden -> n_out on `batch` inputs, on the current device.
+ *   params  : host FP32 [W1 (hidden x n_in) b1 W2 (hidden x hidden) b2 W3 (n_out x hidden) b3],
+ *             row-major; the weights are used as BF16 (rounded to nearest even), biases as FP32
+ *   U, T    : host, batch x n_in inputs (already in [-1, 1]) and batch x n_out targets
+ *   Y       : host, receives batch x n_out outputs
+ *   grads   : host, receives the gradient of the loss sum (Y - T)^2 / (2 batch n_out) in the layout
+ *             of params (with respect to the weights as used)
+ *   loss    : receives the loss. */
+ph_status ph_mlp_check(int n_in, int hidden, int n_out, const float* params, int batch, const float* U,
+                       const float* T, float* Y, float* grads, double* loss);
 
 /* Fill *info with sizes and counts of a built handle. */
 ph_status ph_get_info(const ph_handle* h, ph_info* info);

@@ -743,6 +743,11 @@ ph_status ph_get_info(const ph_handle* h, ph_info* info) {
     r.alg_bytes_per_call = alg;
     r.tensor_core_phase1 = (h->tc_elems > 0 && h->use_tc && h->rank_max_lr <= 64) ? 1 : 0;  // for 8 < m <= 16
     r.kernel_variants = h->last_variants;
+    r.far_core_elems = (long)h->H_elems;
+    for (int k = 0; k < 3; ++k)
+        r.p_theta_near[k] = (k < h->opts.dtheta)
+                                ? (h->opts.near_degree[k] > 0 ? h->opts.near_degree[k] : h->opts.degree[k]) + 1
+                                : 0;
     // flops per right-hand side
     double fl = 2.0 * (double)r.near_entries;  // D_b x
     for (size_t b = 0; b < plan.near_s.size(); ++b) {

@@ -121,6 +121,10 @@ struct DeviceBuffer {
     size_t bytes = 0;
 };
 
+namespace ph {
+struct Surrogate;  // surrogate.cu
+}
+
 struct ph_handle {
     // configuration
     ph_kernel kernel = PH_KERNEL_GAUSS;
@@ -218,6 +222,9 @@ struct ph_handle {
     DevView<float> vfT{};
     DevView<double> vdT{};
     bool instantiated = false;
+    // learned surrogate of the far-field cores (surrogate.cu); null until ph_surrogate_train or
+    // ph_far_project
+    ph::Surrogate* sur = nullptr;
     bool overlap = true;                        // far path on the side stream (ph_set_overlap)
     bool use_bulk = true;                       // bulk-copy pipelined near field and phase 2 when they apply
     int last_variants = 0;                      // kernels the last ph_matvec chose (ph_info.kernel_variants)
@@ -239,6 +246,11 @@ namespace ph {
 ph_status offline_build(ph_handle* h, const double* points, long n);
 // online.cu
 ph_status online_instantiate(ph_handle* h, const double* theta, cudaStream_t stream, int deriv = -1);
+// the near-field part of the online stage only (w_b for every near block)
+void online_instantiate_near(ph_handle* h, const double* theta, cudaStream_t stream);
+// far-field cores from the surrogate network at theta into H (surrogate.cu); false if not in use
+bool surrogate_instantiate_far(ph_handle* h, const double* theta, cudaStream_t stream);
+void surrogate_free(ph_handle* h);
 ph_status online_matvec_batched(ph_handle* h, const double* thetas, int n_theta, const void* X, long ldx, int m,
                                 void* Y, long ldy, long stride_y, int deriv, cudaStream_t stream);
 ph_status wait_bound_selftest(int device, double* waited);  // bounded mbarrier wait on a barrier nothing completes

@@ -470,6 +470,7 @@ void* dev_alloc(ph_handle* h, size_t bytes) {
 }
 
 void free_device(ph_handle* h) {
+    surrogate_free(h);  // host state of the surrogate (its device buffers are in h->buffers)
     for (auto& b : h->buffers)
         if (b.ptr) cudaFree(b.ptr);
     h->buffers.clear();

@@ -2788,9 +2788,10 @@ ph_status matvec_typed(ph_handle* h, DevView<T>& v, const T* X, long long ldx, i
 }
 
 template <typename T>
-void instantiate_typed(ph_handle* h, DevView<T>& v, const double* theta, int deriv, cudaStream_t stream) {
+void instantiate_typed(ph_handle* h, DevView<T>& v, const double* theta, int deriv, cudaStream_t stream,
+                       bool far = true) {
     const int near_ctas = (int)ceil_div(std::max(v.n_near, 1), kThreads);
-    const int grid = near_ctas + v.n_keys;
+    const int grid = near_ctas + (far ? v.n_keys : 0);
     double th[3] = {0, 0, 0};
     for (int k = 0; k < h->opts.dtheta; ++k) th[k] = theta[k];
     ProfScope ps(h, 0, stream);
@@ -2863,9 +2864,19 @@ ph_status handle_timeout_selftest(ph_handle* h, cudaStream_t stream) {
 }
 
 ph_status online_instantiate(ph_handle* h, const double* theta, cudaStream_t stream, int deriv) {
+    if (deriv < 0 && h->sur) {
+        // the surrogate's cores when it is switched on (the derivative stays polynomial)
+        online_instantiate_near(h, theta, stream);
+        if (surrogate_instantiate_far(h, theta, stream)) return PH_OK;
+    }
     if (h->opts.prec == PH_FP32) instantiate_typed<float>(h, h->vf, theta, deriv, stream);
     else instantiate_typed<double>(h, h->vd, theta, deriv, stream);
     return PH_OK;
+}
+
+void online_instantiate_near(ph_handle* h, const double* theta, cudaStream_t stream) {
+    if (h->opts.prec == PH_FP32) instantiate_typed<float>(h, h->vf, theta, -1, stream, false);
+    else instantiate_typed<double>(h, h->vd, theta, -1, stream, false);
 }
 
 ph_status online_matvec_view(ph_handle* h, DevView<float>& vf, DevView<double>& vd, const void* X, long ldx, int m,

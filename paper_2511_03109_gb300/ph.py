@@ -9,6 +9,8 @@ from __future__ import annotations
 import ctypes as C
 import os
 
+import numpy as np
+
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "libph.so")
 
@@ -56,7 +58,8 @@ class Info(C.Structure):
                 ("basis_bytes", C.c_long), ("alg_bytes_per_call", C.c_double),
                 ("flops_per_rhs", C.c_double), ("offline_seconds", C.c_double),
                 ("coupling_a_flops_per_rhs", C.c_double), ("coupling_b_flops_per_rhs", C.c_double),
-                ("tensor_core_phase1", C.c_int), ("kernel_variants", C.c_int)]
+                ("tensor_core_phase1", C.c_int), ("kernel_variants", C.c_int),
+                ("far_core_elems", C.c_long), ("p_theta_near", C.c_int * 3)]
 
     def as_dict(self):
         out = {}
@@ -66,8 +69,24 @@ class Info(C.Structure):
         return out
 
 
+class SurrogateOpts(C.Structure):
+    _fields_ = [("hidden", C.c_int), ("steps", C.c_int), ("batch", C.c_int), ("lr", C.c_double),
+                ("accept_tol", C.c_double), ("seed", C.c_ulonglong)]
+
+
+class SurrogateReport(C.Structure):
+    _fields_ = [("params", C.c_long), ("out_dim", C.c_long), ("loss_first", C.c_double),
+                ("loss_last", C.c_double), ("val_err_net_rms", C.c_double), ("val_err_net_max", C.c_double),
+                ("val_err_poly_rms", C.c_double), ("val_err_poly_max", C.c_double),
+                ("targets_seconds", C.c_double), ("train_seconds", C.c_double), ("accepted", C.c_int)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 _H = C.c_void_p
 _P = C.c_void_p
+_F = C.POINTER(C.c_float)
 
 _SIGS = {
     "ph_offline_build": (C.c_int, [C.POINTER(C.c_double), C.c_long, C.c_int, C.POINTER(BuildOpts),
@@ -96,6 +115,12 @@ _SIGS = {
     "ph_check": (C.c_int, [_H, _P]),
     "ph_inject_alloc_failure": (C.c_int, [C.c_long]),
     "ph_selftest_timeout": (C.c_int, [_H, _P]),
+    "ph_far_project": (C.c_int, [_H, C.POINTER(C.c_double), C.c_int, _P, _P]),
+    "ph_instantiate_cores": (C.c_int, [_H, C.POINTER(C.c_double), _P, _P]),
+    "ph_surrogate_train": (C.c_int, [_H, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_double), C.c_int,
+                                     C.POINTER(SurrogateOpts), C.POINTER(SurrogateReport), _P]),
+    "ph_surrogate_use": (C.c_int, [_H, C.c_int]),
+    "ph_mlp_check": (C.c_int, [C.c_int, C.c_int, C.c_int, _F, C.c_int, _F, _F, _F, _F, C.POINTER(C.c_double)]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -265,6 +290,32 @@ class ParametricMatrix:
         check(ph_profile_read(self.h, ms, la), self.h)
         return {k: (ms[i], la[i]) for i, k in enumerate(PROF_KINDS)}
 
+    def far_project_ptr(self, thetas, out_ptr, stream=0):
+        """Projected far cores H*_k(theta) of every class for each theta into the device buffer
+        out_ptr (n_theta x info()["far_core_elems"] scalars of the handle's precision)."""
+        th = np.ascontiguousarray(np.atleast_2d(np.asarray(thetas, float)))
+        check(ph_far_project(self.h, th.ctypes.data_as(C.POINTER(C.c_double)), th.shape[0], out_ptr, stream),
+              self.h)
+
+    def instantiate_cores_ptr(self, theta, cores_ptr, stream=0):
+        th = np.ascontiguousarray(np.atleast_1d(np.asarray(theta, float)))
+        check(ph_instantiate_cores(self.h, th.ctypes.data_as(C.POINTER(C.c_double)), cores_ptr, stream), self.h)
+
+    def surrogate_train(self, thetas_train, thetas_val, hidden=0, steps=0, batch=0, lr=0.0, accept_tol=0.0,
+                        seed=1, stream=0) -> dict:
+        """Train the far-field surrogate on the GPU (ph_surrogate_train); returns its report."""
+        tt = np.ascontiguousarray(np.atleast_2d(np.asarray(thetas_train, float)))
+        tv = np.ascontiguousarray(np.atleast_2d(np.asarray(thetas_val, float)))
+        o = SurrogateOpts(int(hidden), int(steps), int(batch), float(lr), float(accept_tol), int(seed))
+        r = SurrogateReport()
+        check(ph_surrogate_train(self.h, tt.ctypes.data_as(C.POINTER(C.c_double)), tt.shape[0],
+                                 tv.ctypes.data_as(C.POINTER(C.c_double)), tv.shape[0], C.byref(o), C.byref(r),
+                                 stream), self.h)
+        return r.as_dict()
+
+    def surrogate_use(self, enable=True):
+        check(ph_surrogate_use(self.h, 1 if enable else 0), self.h)
+
     def save(self, path):
         return check(ph_save(self.h, path.encode()), self.h)
 
@@ -278,6 +329,21 @@ class ParametricMatrix:
             self.close()
         except Exception:
             pass
+
+
+def mlp_check(n_in, hidden, n_out, params, U, T):
+    """One forward pass, loss and backward pass of the library's perceptron kernels on the current
+    device (ph_mlp_check): returns (Y, grads, loss)."""
+    p = np.ascontiguousarray(params, np.float32)
+    U = np.ascontiguousarray(U, np.float32)
+    T = np.ascontiguousarray(T, np.float32)
+    B = U.shape[0]
+    Y = np.empty((B, n_out), np.float32)
+    g = np.empty_like(p)
+    loss = C.c_double()
+    fp = lambda a: a.ctypes.data_as(_F)
+    check(ph_mlp_check(n_in, hidden, n_out, fp(p), B, fp(U), fp(T), fp(Y), fp(g), C.byref(loss)))
+    return Y, g, loss.value
 
 
 def _colmajor(X) -> bool:
