@@ -680,6 +680,224 @@ def run_reference(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+# ----------------------------------------------------------- the differentiated and learned forms
+
+
+def _make(wl, ph):
+    opts = ph.make_opts(wl.d, wl.theta_lo, wl.theta_hi, wl.degree, wl.p_s, wl.l_max, wl.eta, wl.tol,
+                        rank_cap=wl.rank_cap, fmt=wl.fmt, prec=wl.precision,
+                        near_degree=list(wl.near_degree) if wl.near_degree else None)
+    return ph.ParametricMatrix(wl.points(), wl.kernel, opts)
+
+
+def _timed(fn, count, stream):
+    import torch
+
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for k in range(count):
+        fn(k)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / count
+
+
+def run_differentiation(args):
+    """y = K_hat(theta) x, its adjoint K_hat^T ybar (d/dx) and the d_theta derivative products
+    dK_hat/dtheta_i x (d/dtheta through the derivatives of the Lagrange weights), each timed against
+    the forward product; checked by central differences (step 1e-4), the adjoint identity and the
+    oracle's exact dK/dtheta x on sampled rows."""
+    import torch
+
+    from paper_2511_03109_gb300 import ph
+
+    wl = inputs.DIFF_2D_ANISO
+    log(f"offline build {wl.name}")
+    A = _make(wl, ph)
+    info = A.info()
+    n, m, dt = wl.n, wl.m, wl.d
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    X = torch.tensor(wl.rhs().T, dtype=torch.float32, device="cuda").contiguous()
+    Y = torch.empty_like(X)
+    Z = torch.empty_like(X)
+    K, W = args.steps, args.warmup
+    th = wl.thetas(K + W)
+
+    def fwd(k):
+        A.instantiate(th[k % len(th)], sp)
+        A.matvec_ptr(X.data_ptr(), n, m, Y.data_ptr(), n, sp)
+
+    def adj(k):
+        A.instantiate(th[k % len(th)], sp)
+        A.matvec_transpose_ptr(X.data_ptr(), n, m, Z.data_ptr(), n, sp)
+
+    def der(k):
+        for i in range(dt):
+            A.instantiate_derivative(th[k % len(th)], i, sp)
+            A.matvec_ptr(X.data_ptr(), n, m, Z.data_ptr(), n, sp)
+
+    def grad(k):  # one loss gradient: forward, adjoint, every theta derivative
+        fwd(k)
+        adj(k)
+        der(k)
+
+    res = {}
+    for name, fn in (("forward", fwd), ("adjoint", adj), ("dtheta_products", der), ("gradient_step", grad)):
+        for k in range(W):
+            fn(k)
+        ms = _timed(fn, K, stream)
+        res[name] = {"ms_per_step": ms, "value": m / (ms / 1e3), "unit": UNIT}
+    for name in ("adjoint", "dtheta_products", "gradient_step"):
+        res[name]["vs_forward"] = res[name]["ms_per_step"] / res["forward"]["ms_per_step"]
+    # checks at one theta
+    t0 = np.asarray(th[0], float)
+    h = 1e-4
+    A.instantiate(t0, sp)
+    A.matvec_ptr(X.data_ptr(), n, m, Y.data_ptr(), n, sp)
+    A.matvec_transpose_ptr(X.data_ptr(), n, m, Z.data_ptr(), n, sp)
+    torch.cuda.synchronize()
+    Xh = X.double().cpu().numpy()
+    ident = abs(float(np.sum(Xh * Y.double().cpu().numpy()) - np.sum(Z.double().cpu().numpy() * Xh)))
+    ident /= float(np.linalg.norm(Xh) * np.linalg.norm(Y.double().cpu().numpy()))
+    fd = []
+    Yp, Ym = torch.empty_like(X), torch.empty_like(X)
+    for i in range(dt):
+        A.instantiate_derivative(t0, i, sp)
+        A.matvec_ptr(X.data_ptr(), n, m, Z.data_ptr(), n, sp)
+        tp, tm = t0.copy(), t0.copy()
+        tp[i] += h
+        tm[i] -= h
+        A.instantiate(tp, sp)
+        A.matvec_ptr(X.data_ptr(), n, m, Yp.data_ptr(), n, sp)
+        A.instantiate(tm, sp)
+        A.matvec_ptr(X.data_ptr(), n, m, Ym.data_ptr(), n, sp)
+        torch.cuda.synchronize()
+        num = (Yp.double() - Ym.double()) / (2 * h)
+        fd.append(float(((num - Z.double()).norm() / Z.double().norm()).item()))
+    out = {"metric": "differentiated online stage (theta*RHS)/s", "workload": wl.name, "n": n, "d": wl.d,
+           "dtheta": dt, "degree": list(wl.degree), "m": m, "dtype": "f32", "data": "synthetic", "steps": K,
+           "warmup": W, "results": res, "adjoint_identity_rel": ident,
+           "fd_check_rel_err": {"step": h, "per_dim": fd,
+                                "note": "central differences in FP32: rounding of the two products over 2h"},
+           "structure": {k: info[k] for k in ("n_near", "n_far", "n_far_keys", "near_bytes", "far_rank_max")},
+           "offline_seconds": info["offline_seconds"]}
+    if not args.no_cpu_baseline:
+        from oracle import pmatrix
+        M = pmatrix.ParametricMatrix(wl.points(), wl.kernel, wl.theta_lo, wl.theta_hi, wl.degree, wl.p_s, wl.l_max,
+                                     wl.eta, wl.tol, rank_cap=wl.rank_cap, fmt=wl.fmt)
+        targets = M.leaves[:: max(1, len(M.leaves) // 2)][:2]
+        log("oracle: sampled rows of the forward and derivative products")
+        M.offline(targets)
+        rows = np.sort(np.concatenate([c.idx for c in targets]))
+        Xo = wl.rhs()
+        errs = {}
+        for name, deriv in (("forward", None),) + tuple((f"dtheta_{i}", i) for i in range(dt)):
+            ref = M.matvec(M.instantiate(t0, targets, deriv=deriv), Xo, targets)[rows]
+            if deriv is None:
+                A.instantiate(t0, sp)
+            else:
+                A.instantiate_derivative(t0, deriv, sp)
+            A.matvec_ptr(X.data_ptr(), n, m, Z.data_ptr(), n, sp)
+            torch.cuda.synchronize()
+            got = Z.double().cpu().numpy().T[rows]
+            errs[name] = float((np.linalg.norm(got - ref, axis=0) / np.linalg.norm(ref, axis=0)).max())
+        out["rel_err_vs_oracle"] = errs
+        out["oracle_rows"] = int(len(rows))
+    print(json.dumps(out), flush=True)
+    A.close()
+
+
+def run_surrogate(args):
+    """The learned far-field cores against the degree-8 tensor-grid polynomial on the same
+    handle: training on the GPU, then 64 theta x 16 RHS through each path; accuracy of each path's
+    cores (against the exact projected cores) and of each product (against the product with the
+    projected cores, and against the exact K(theta) X on sampled rows)."""
+    import torch
+
+    from oracle import kernels
+    from paper_2511_03109_gb300 import ph
+
+    wl = inputs.SURROGATE_3D_ANISO
+    log(f"offline build {wl.name}")
+    A = _make(wl, ph)
+    info = A.info()
+    n, m = wl.n, wl.m
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    n_train = args.sur_train
+    tt = inputs.uniform_thetas(wl.theta_lo, wl.theta_hi, n_train, wl.theta_seed)
+    tv = inputs.uniform_thetas(wl.theta_lo, wl.theta_hi, 64, wl.theta_seed + 1)
+    log(f"training on {n_train} thetas")
+    rep = A.surrogate_train(tt, tv, hidden=256, steps=args.sur_steps, batch=256, lr=1e-3, seed=7, stream=sp)
+    X = torch.tensor(wl.rhs().T, dtype=torch.float32, device="cuda").contiguous()
+    Y = torch.empty_like(X)
+    th64 = inputs.uniform_thetas(wl.theta_lo, wl.theta_hi, 64, wl.theta_seed + 2)
+
+    def step(k):
+        A.instantiate(th64[k % 64], sp)
+        A.matvec_ptr(X.data_ptr(), n, m, Y.data_ptr(), n, sp)
+
+    def inst(k):
+        A.instantiate(th64[k % 64], sp)
+
+    paths = {}
+    for use in (False, True):
+        if use and not rep["accepted"]:
+            continue
+        A.surrogate_use(use)
+        for k in range(3):
+            step(k)
+        ms = _timed(step, 64, stream)
+        ms_i = _timed(inst, 64, stream)
+        paths["network" if use else "polynomial"] = {"ms_per_theta": ms, "instantiate_ms": ms_i,
+                                                     "value": m / (ms / 1e3), "unit": UNIT}
+    # accuracy on four thetas: products with each path's cores against the product with the exact
+    # projected cores (the far-field error) and against the exact K(theta) X on 200 sampled rows
+    P = wl.points()
+    Xh = wl.rhs()
+    rows = inputs.sample_rows(n, 200, wl.theta_seed + 3)
+    cores = torch.empty((1, info["far_core_elems"]), dtype=torch.float32, device="cuda")
+    acc = {"far_field_err": {}, "total_err_vs_exact": {}}
+    for th in tv[:4]:
+        A.far_project_ptr([th], cores.data_ptr(), sp)
+        A.instantiate_cores_ptr(th, cores.data_ptr(), sp)
+        A.matvec_ptr(X.data_ptr(), n, m, Y.data_ptr(), n, sp)
+        torch.cuda.synchronize()
+        ystar = Y.double().cpu().numpy().T
+        exact = kernels.dense_apply(wl.kernel, P, th, Xh, rows=rows)
+        e = float((np.linalg.norm(ystar[rows] - exact, axis=0) / np.linalg.norm(exact, axis=0)).max())
+        acc["total_err_vs_exact"].setdefault("projected_cores", []).append(e)
+        for name, use in (("polynomial", False), ("network", True)):
+            if use and not rep["accepted"]:
+                continue
+            A.surrogate_use(use)
+            A.instantiate(th, sp)
+            A.matvec_ptr(X.data_ptr(), n, m, Y.data_ptr(), n, sp)
+            torch.cuda.synchronize()
+            y = Y.double().cpu().numpy().T
+            acc["far_field_err"].setdefault(name, []).append(
+                float((np.linalg.norm(y - ystar, axis=0) / np.linalg.norm(ystar, axis=0)).max()))
+            acc["total_err_vs_exact"].setdefault(name, []).append(
+                float((np.linalg.norm(y[rows] - exact, axis=0) / np.linalg.norm(exact, axis=0)).max()))
+    A.surrogate_use(False)
+    out = {"metric": "learned far-field cores vs tensor-grid polynomial (theta*RHS)/s", "workload": wl.name,
+           "n": n, "d": wl.d, "dtheta": len(wl.theta_lo), "far_degree": list(wl.degree),
+           "near_degree": list(wl.near_degree), "m": m, "thetas_timed": 64, "dtype": "f32", "data": "synthetic",
+           "network": {"shape": f"{len(wl.theta_lo)} -> 256 -> 256 -> {rep['out_dim']}", "params": rep["params"],
+                       "weights": "BF16 copies in the products, FP32 accumulation and master weights",
+                       "train_thetas": n_train, "steps": args.sur_steps},
+           "training": rep, "paths": paths, "accuracy_on_4_thetas": acc,
+           "network_weight_bytes_bf16": 2 * rep["params"],
+           "structure": {k: info[k] for k in ("n_near", "n_far", "n_far_keys", "near_bytes", "far_rank_max",
+                                              "far_core_elems", "far_bytes")},
+           "offline_seconds": info["offline_seconds"]}
+    print(json.dumps(out), flush=True)
+    A.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -693,7 +911,16 @@ def main():
                     help="phase 1 of the coupling on the tensor cores (1) or CUDA cores (0); default: the library's")
     ap.add_argument("--n", type=int, default=0,
                     help="profiling only: a smaller point count of the same workload (not a bench line)")
+    ap.add_argument("--workload", default="plain", choices=["plain", "differentiation", "surrogate"],
+                    help="plain: the headline line; differentiation / surrogate: the differentiated and the "
+                         "learned forms on their own workloads (one JSON line each, one GPU)")
+    ap.add_argument("--sur-train", type=int, default=4096, help="surrogate: training thetas")
+    ap.add_argument("--sur-steps", type=int, default=1500, help="surrogate: Adam steps")
     args = ap.parse_args()
+    if args.workload == "differentiation":
+        return run_differentiation(args)
+    if args.workload == "surrogate":
+        return run_surrogate(args)
     if args.n:
         global WL
         import dataclasses

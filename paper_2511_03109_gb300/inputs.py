@@ -83,6 +83,7 @@ class Workload:
     rhs_seed: int
     theta_seed: int
     theta: tuple = field(default=())
+    near_degree: tuple = field(default=())  # the near field's own grid (empty: degree)
 
     def points(self) -> np.ndarray:
         return uniform_points(self.n, self.d, self.point_seed)
@@ -120,4 +121,26 @@ LARGE_3D_MATERN_H2 = Workload(
     eta=float(np.sqrt(3.0)), tol=1e-5, rank_cap=64, fmt="h2", precision="fp32",
     m=16, point_seed=1002, rhs_seed=2002, theta_seed=3002)
 
-WORKLOADS = {w.name: w for w in (SMALL_2D_GAUSS_H2, SMALL_2D_GAUSS_H, LARGE_3D_MATERN_H2)}
+# Differentiation: n = 262144 uniform points in [0,1]^2, anisotropic Gaussian with
+# (l_1, l_2) in [0.05, 0.5]^2, tensor Chebyshev degree 12 x 12, p_s = 8, l_max = 6 (mean
+# leaf 64), eta = sqrt(2), rank <= 64, FP32, 8 N(0,1) right-hand sides.
+DIFF_2D_ANISO = Workload(
+    name="n262144_d2_aniso_gauss_h2_fp32_m8", n=262144, d=2, kernel="aniso_gauss",
+    theta_lo=(0.05, 0.05), theta_hi=(0.5, 0.5), degree=(12, 12), p_s=8, l_max=6,
+    eta=float(np.sqrt(2.0)), tol=1e-5, rank_cap=64, fmt="h2", precision="fp32",
+    m=8, point_seed=1004, rhs_seed=2004, theta_seed=3004)
+
+# Learned surrogate: n = 65536 uniform points in [0,1]^3, anisotropic Gaussian with
+# (l_1, l_2, l_3) in [0.05, 0.5]^3, near-field degree 4 (125 grid points), far-field
+# degree 8 (729 grid points, the polynomial path the network is compared with), p_s = 4
+# (with p_s = 8 the offline TT-SVD of the 632 far tensors of 512 x 729 x 512 entries takes
+# about ten minutes; network and polynomial share the spatial factors either way), l_max = 3,
+# eta = sqrt(3), rank <= 64, FP32, 16 N(0,1) right-hand sides.
+SURROGATE_3D_ANISO = Workload(
+    name="n65536_d3_aniso_gauss_ps4_h2_fp32_m16", n=65536, d=3, kernel="aniso_gauss",
+    theta_lo=(0.05, 0.05, 0.05), theta_hi=(0.5, 0.5, 0.5), degree=(8, 8, 8), p_s=4, l_max=3,
+    eta=float(np.sqrt(3.0)), tol=1e-5, rank_cap=64, fmt="h2", precision="fp32",
+    m=16, point_seed=1005, rhs_seed=2005, theta_seed=3005, near_degree=(4, 4, 4))
+
+WORKLOADS = {w.name: w for w in (SMALL_2D_GAUSS_H2, SMALL_2D_GAUSS_H, LARGE_3D_MATERN_H2, DIFF_2D_ANISO,
+                                 SURROGATE_3D_ANISO)}
