@@ -311,28 +311,32 @@ __device__ __forceinline__ float to_f(__nv_bfloat16 x) { return __bfloat162float
 // C[m][n] = beta C[m][n] + sum_k A(m, k) B(k, n) (+ bias[n]) with A(m, k) = A[m as0 + k as1],
 // B(k, n) = B[k bs0 + n bs1], C row-major (ldc); FP32 accumulation.  64 x 64 tiles, 16-deep
 // slices of A and B in shared memory (loaded along whichever index is contiguous), 4 x 4 outputs
-// per thread.  The network's products: the weights enter as BF16, activations as FP32.
+// per thread.  The network's products: the weights enter as BF16, activations as FP32.  With
+// gridDim.z > 1 the K range is split (kchunk per CTA) and the partial sums are added atomically
+// into C, which the caller has zeroed (beta = 0): the products whose K is the network's output
+// dimension would otherwise run on a few CTAs only.
 template <typename TA, typename TB>
 __global__ void __launch_bounds__(kT) gemm_kernel(int M, int N, int K, const TA* __restrict__ A, long long as0,
                                                   long long as1, const TB* __restrict__ B, long long bs0,
                                                   long long bs1, float* __restrict__ C, long long ldc, float beta,
-                                                  const float* __restrict__ bias) {
+                                                  const float* __restrict__ bias, int kchunk) {
     __shared__ float As[16][64 + 4];
     __shared__ float Bs[16][64 + 4];
     const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int kb0 = blockIdx.z * kchunk, ke = min(K, kb0 + kchunk);
     float acc[4][4] = {};
     const bool a_k_fast = (as1 == 1), b_k_fast = (bs0 == 1);
-    for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int k0 = kb0; k0 < ke; k0 += 16) {
         for (int e = threadIdx.x; e < 64 * 16; e += kT) {
             int mm, kk;
             if (a_k_fast) { kk = e % 16; mm = e / 16; } else { mm = e % 64; kk = e / 64; }
             const int m = m0 + mm, k = k0 + kk;
-            As[kk][mm] = (m < M && k < K) ? to_f(A[(long long)m * as0 + (long long)k * as1]) : 0.f;
+            As[kk][mm] = (m < M && k < ke) ? to_f(A[(long long)m * as0 + (long long)k * as1]) : 0.f;
             int nn, kb;
             if (b_k_fast) { kb = e % 16; nn = e / 16; } else { nn = e % 64; kb = e / 64; }
             const int n = n0 + nn, kq = k0 + kb;
-            Bs[kb][nn] = (n < N && kq < K) ? to_f(B[(long long)kq * bs0 + (long long)n * bs1]) : 0.f;
+            Bs[kb][nn] = (n < N && kq < ke) ? to_f(B[(long long)kq * bs0 + (long long)n * bs1]) : 0.f;
         }
         __syncthreads();
 #pragma unroll
@@ -358,9 +362,13 @@ __global__ void __launch_bounds__(kT) gemm_kernel(int M, int N, int K, const TA*
         for (int w = 0; w < 4; ++w) {
             const int n = n0 + tx * 4 + w;
             if (n >= N) continue;
-            float val = acc[u][w] + (bias ? bias[n] : 0.f);
             float* c = C + (long long)m * ldc + n;
-            *c = (beta != 0.f) ? beta * *c + val : val;
+            if (gridDim.z > 1) {
+                atomicAdd(c, acc[u][w] + ((bias && blockIdx.z == 0) ? bias[n] : 0.f));
+            } else {
+                const float val = acc[u][w] + (bias ? bias[n] : 0.f);
+                *c = (beta != 0.f) ? beta * *c + val : val;
+            }
         }
     }
 }
@@ -369,8 +377,15 @@ template <typename TA, typename TB>
 void gemm(cudaStream_t s, int M, int N, int K, const TA* A, long long as0, long long as1, const TB* B, long long bs0,
           long long bs1, float* C, long long ldc, float beta, const float* bias) {
     if (M <= 0 || N <= 0) return;
-    dim3 grid((unsigned)ceil_div(N, 64), (unsigned)ceil_div(M, 64));
-    gemm_kernel<TA, TB><<<grid, kT, 0, s>>>(M, N, K, A, as0, as1, B, bs0, bs1, C, ldc, beta, bias);
+    const long long tiles = ceil_div(N, 64) * ceil_div(M, 64);
+    int splits = 1;
+    if (beta == 0.f && ldc == N && tiles < 296 && K >= 8192)
+        splits = (int)std::max<long long>(1, std::min<long long>(ceil_div(K, 2048), 1184 / tiles));
+    const int kchunk = (int)(ceil_div(ceil_div(K, splits), 16) * 16);
+    splits = (int)ceil_div(K, kchunk);
+    if (splits > 1) PH_CUDA(cudaMemsetAsync(C, 0, (size_t)M * N * sizeof(float), s));
+    dim3 grid((unsigned)ceil_div(N, 64), (unsigned)ceil_div(M, 64), (unsigned)splits);
+    gemm_kernel<TA, TB><<<grid, kT, 0, s>>>(M, N, K, A, as0, as1, B, bs0, bs1, C, ldc, beta, bias, kchunk);
     PH_LAUNCH("gemm_kernel");
 }
 

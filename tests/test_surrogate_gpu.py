@@ -35,7 +35,8 @@ def _bf16(x):
     return u.astype(np.uint32).view(np.float32)
 
 
-@pytest.mark.parametrize("n_in,hidden,n_out,B", [(3, 32, 37, 5), (2, 64, 300, 17), (3, 256, 1000, 64)])
+@pytest.mark.parametrize("n_in,hidden,n_out,B", [(3, 32, 37, 5), (2, 64, 300, 17), (3, 256, 1000, 64),
+                                                 (3, 64, 20000, 32)])  # the last splits K = n_out over CTAs
 def test_network_kernels_match_the_oracle(n_in, hidden, n_out, B):
     from paper_2511_03109_gb300 import ph
 
