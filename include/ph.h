@@ -303,11 +303,14 @@ typedef struct {
     unsigned long long seed; /* initial weights ~ N(0, 1 / fan_in) from this seed, and the batch order */
 } ph_surrogate_opts;
 
-/* What ph_surrogate_train measured on the validation thetas t, with E_t = ||H_t - H*_t|| the
- * Frobenius norm of the error of all classes' cores at t and S = sqrt(mean_t ||H*_t||^2) their RMS size:
- *   rms = sqrt(sum_t E_t^2 / sum_t ||H*_t||^2),   max = max_t E_t / S.
+/* What ph_surrogate_train measured on the validation thetas t.  Errors are taken on the coupling
+ * matrices, E_t^2 = sum_k ||L_k (H_k - H*_k) R_k^T||_F^2 at t (computed in orthonormal bases of the
+ * stored factors, where it is the Frobenius norm of the transformed core), with
+ * S = sqrt(mean_t sum_k ||L_k H*_k R_k^T||_F^2) their RMS size:
+ *   rms = sqrt(sum_t E_t^2 / sum_t sum_k ||L_k H*_k R_k^T||^2),   max = max_t E_t / S.
  * (Per-theta relative errors would be dominated by the thetas where the far field is negligible,
- * e.g. the shortest length scales.) */
+ * e.g. the shortest length scales; errors of H itself would weigh directions that the factors
+ * scale down.) */
 typedef struct {
     long params;             /* weights and biases of the network */
     long out_dim;            /* network outputs (= far_core_elems) */
@@ -321,9 +324,10 @@ typedef struct {
 /* Train the surrogate on the GPU (forward, backward and Adam kernels of this library; BF16 weight
  * copies in the matrix products with FP32 accumulation, FP32 master weights):
  *   u = 2 (theta - lo) / (hi - lo) - 1,  h1 = gelu(W1 u + b1),  h2 = gelu(W2 h1 + b2),
- *   y = W3 h2 + b3,  H_k(theta) = s_k y_k,
- * gelu(x) = x Phi(x) (exact), s_k the RMS of class k's training targets.  Loss: mean squared error
- * of y against the targets H*_k / s_k.  thetas_train / thetas_val: host, n x d_theta, inside the box
+ *   y = W3 h2 + b3,  K_k(theta) = s_k y_k,  H_k = A_{L,k}^{-1} K_k A_{R,k}^{-T},
+ * gelu(x) = x Phi(x) (exact), A the upper Cholesky factors of L_k^T L_k and R_k^T R_k (so that K_k is
+ * the core in orthonormal bases of the factors' column spaces), s_k the RMS of class k's training
+ * targets.  Loss: mean squared error of y against the targets K*_k / s_k, K* = A_L H* A_R^T.  thetas_train / thetas_val: host, n x d_theta, inside the box
  * (the caller draws them).  The acceptance test compares the network's validation error with
  * opts->accept_tol or with the polynomial cores' (see ph_surrogate_opts).  rep may be NULL.
  * A later call replaces the network.  Synchronous. */

@@ -26,6 +26,11 @@ struct Surrogate {
     // arena, Lp = L (L^T L)^{-1}, Rp = R (R^T R)^{-1}; Chebyshev nodes of each class's boxes
     void* proj = nullptr;
     double* geo = nullptr;  // [key][2][d][p_s]: target box nodes, then source box nodes
+    // per class, FP64 row-major: [A_L | A_R | A_L^{-1} | A_R^{-1}], A the upper Cholesky factors of
+    // L^T L and R^T R; K = A_L H A_R^T is the core in orthonormal bases (|L H R^T| = |K|)
+    double* bal = nullptr;
+    long long* bal_off = nullptr;
+    float* kbuf = nullptr;  // inference: the network's balanced cores before the change of basis
     bool proj_ready = false;
     // network
     int n_in = 0, hidden = 0;
@@ -163,45 +168,84 @@ __global__ void __launch_bounds__(kT) project_left_kernel(DevView<T> v, const T*
     }
 }
 
-// Gauss-Jordan inverse of an SPD r x r matrix (FP64, r <= 64, well conditioned: Gram matrices of
-// the TT factors).
-void spd_inverse(int r, std::vector<double>& A) {
-    std::vector<double> I((size_t)r * r, 0.0);
-    for (int i = 0; i < r; ++i) I[(size_t)i * r + i] = 1.0;
-    for (int c = 0; c < r; ++c) {
-        int piv = c;
-        for (int i = c + 1; i < r; ++i)
-            if (std::fabs(A[(size_t)i * r + c]) > std::fabs(A[(size_t)piv * r + c])) piv = i;
-        if (A[(size_t)piv * r + c] == 0.0) throw Error(PH_ERR_UNSUPPORTED, "singular Gram matrix of a far-field factor");
-        if (piv != c)
-            for (int k = 0; k < r; ++k) {
-                std::swap(A[(size_t)piv * r + k], A[(size_t)c * r + k]);
-                std::swap(I[(size_t)piv * r + k], I[(size_t)c * r + k]);
-            }
-        const double inv = 1.0 / A[(size_t)c * r + c];
-        for (int k = 0; k < r; ++k) {
-            A[(size_t)c * r + k] *= inv;
-            I[(size_t)c * r + k] *= inv;
-        }
-        for (int i = 0; i < r; ++i) {
-            if (i == c) continue;
-            const double f = A[(size_t)i * r + c];
-            if (f == 0.0) continue;
-            for (int k = 0; k < r; ++k) {
-                A[(size_t)i * r + k] -= f * A[(size_t)c * r + k];
-                I[(size_t)i * r + k] -= f * I[(size_t)c * r + k];
-            }
+// Upper Cholesky factor A of an SPD r x r matrix G (row-major, G = A^T A), FP64.
+std::vector<double> chol_upper(int r, const std::vector<double>& G) {
+    std::vector<double> A((size_t)r * r, 0.0);
+    for (int i = 0; i < r; ++i) {
+        double dsum = G[(size_t)i * r + i];
+        for (int k = 0; k < i; ++k) dsum -= A[(size_t)k * r + i] * A[(size_t)k * r + i];
+        if (!(dsum > 0.0)) throw Error(PH_ERR_UNSUPPORTED, "singular Gram matrix of a far-field factor");
+        const double aii = std::sqrt(dsum);
+        A[(size_t)i * r + i] = aii;
+        for (int j = i + 1; j < r; ++j) {
+            double v = G[(size_t)i * r + j];
+            for (int k = 0; k < i; ++k) v -= A[(size_t)k * r + i] * A[(size_t)k * r + j];
+            A[(size_t)i * r + j] = v / aii;
         }
     }
-    A.swap(I);
+    return A;
 }
+
+// Inverse of an upper-triangular r x r matrix (row-major), by back substitution per column.
+std::vector<double> upper_inverse(int r, const std::vector<double>& A) {
+    std::vector<double> X((size_t)r * r, 0.0);
+    for (int c = 0; c < r; ++c)
+        for (int i = c; i >= 0; --i) {
+            double v = (i == c) ? 1.0 : 0.0;
+            for (int k = i + 1; k <= c; ++k) v -= A[(size_t)i * r + k] * X[(size_t)k * r + c];
+            X[(size_t)i * r + c] = v / A[(size_t)i * r + i];
+        }
+    return X;
+}
+
+// Per (class, theta): out = M1 in M2^T on the class's r_d x r' block (column-major at its H
+// offset), with (M1, M2) = (A_L, A_R) (inverse = 0: a core into orthonormal bases) or
+// (A_L^{-1}, A_R^{-1}) (inverse = 1: back); `in` optionally scaled per entry first.  FP64 in
+// shared memory; in == out is allowed (each CTA reads its block before it writes it).
+template <typename TI, typename TO>
+__global__ void __launch_bounds__(kT) class_transform_kernel(DevView<TO> v, const TI* in, const float* in_scale,
+                                                             TO* out, long long stride, const double* bal,
+                                                             const long long* bal_off, int inverse) {
+    extern __shared__ double tsm[];
+    double* X = tsm;              // rd x rp, column-major (ld 64)
+    double* T1 = tsm + 64 * 64;
+    const int key = blockIdx.x, t = blockIdx.y;
+    const int* rk = v.key_ranks + (size_t)key * (v.Delta + 1);
+    const int rd = rk[v.d], rp = rk[v.d + v.dtheta];
+    const long long base = (long long)t * stride + v.key_hoff[key];
+    const double* AL = bal + bal_off[key];
+    const double* AR = AL + (size_t)rd * rd;
+    const double* M1 = inverse ? AR + (size_t)rp * rp : AL;
+    const double* M2 = inverse ? M1 + (size_t)rd * rd : AR;
+    for (int e = threadIdx.x; e < rd * rp; e += blockDim.x)
+        X[(e % rd) + 64 * (e / rd)] = (double)in[base + e] * (in_scale ? (double)in_scale[v.key_hoff[key] + e] : 1.0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < rd * rp; e += blockDim.x) {
+        const int q = e % rd, a = e / rd;
+        double acc = 0.0;
+        for (int b = 0; b < rd; ++b) acc += M1[(size_t)q * rd + b] * X[b + 64 * a];
+        T1[q + 64 * a] = acc;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < rd * rp; e += blockDim.x) {
+        const int q = e % rd, a = e / rd;
+        double acc = 0.0;
+        for (int c = 0; c < rp; ++c) acc += T1[q + 64 * c] * M2[(size_t)a * rp + c];
+        out[base + e] = (TO)acc;
+    }
+}
+
+template <typename TI, typename TO>
+void class_transform(ph_handle* h, DevView<TO>& v, const TI* in, const float* in_scale, TO* out, long long stride,
+                     int n_theta, int inverse, cudaStream_t s);
 
 Surrogate& sur_of(ph_handle* h) {
     if (!h->sur) h->sur = new Surrogate();
     return *h->sur;
 }
 
-// The projected factors and the class geometry (once per handle; synchronous).
+// The projection factors (orthonormal bases of the stored factors' column spaces), the changes of
+// basis between H and the balanced core K, and the class geometry (once per handle; synchronous).
 void build_projection(ph_handle* h) {
     Surrogate& S = sur_of(h);
     if (S.proj_ready) return;
@@ -216,7 +260,8 @@ void build_projection(ph_handle* h) {
     auto at = [&](size_t i) -> double {
         return sc == 4 ? (double)reinterpret_cast<const float*>(raw.data())[i] : reinterpret_cast<const double*>(raw.data())[i];
     };
-    std::vector<double> out((size_t)h->lr_elems, 0.0);
+    std::vector<double> out((size_t)h->lr_elems, 0.0), bal;
+    std::vector<long long> bal_off;
     for (int k = 0; k < nk; ++k) {
         const int rd = h->key_ranks[(size_t)k * (D + 1) + d], rp = h->key_ranks[(size_t)k * (D + 1) + d + dt];
         const int rp4 = (rp + 3) & ~3;
@@ -236,22 +281,32 @@ void build_projection(ph_handle* h) {
                 for (int J = 0; J < PD; ++J) s += at(rb + (size_t)J * rp4 + a) * at(rb + (size_t)J * rp4 + b);
                 GR[(size_t)a * rp + b] = s;
             }
-        spd_inverse(rd, GL);
-        spd_inverse(rp, GR);
-        // Lp^T = (L^T L)^{-1} L^T ; Rp = R (R^T R)^{-1}
+        // L = Q_L A_L, R = Q_R A_R (A upper Cholesky factors of the Gram matrices): the targets are
+        // computed in the orthonormal bases, K* = Q_L^T W(theta) Q_R = A_L H* A_R^T, which is well
+        // conditioned however unevenly the stored factors scale their columns
+        const std::vector<double> AL = chol_upper(rd, GL), AR = chol_upper(rp, GR);
+        const std::vector<double> ALi = upper_inverse(rd, AL), ARi = upper_inverse(rp, AR);
+        bal_off.push_back((long long)bal.size());
+        for (const auto* m : {&AL, &AR, &ALi, &ARi}) bal.insert(bal.end(), m->begin(), m->end());
+        // Q_L^T = A_L^{-T} L^T ; Q_R = R A_R^{-1}
         for (int a = 0; a < rd; ++a)
             for (int J = 0; J < PD; ++J) {
                 double s = 0;
-                for (int b = 0; b < rd; ++b) s += GL[(size_t)a * rd + b] * at(base + (size_t)b * PD + J);
+                for (int b = 0; b <= a; ++b) s += ALi[(size_t)b * rd + a] * at(base + (size_t)b * PD + J);
                 out[base + (size_t)a * PD + J] = s;
             }
         for (int J = 0; J < PD; ++J)
             for (int a = 0; a < rp; ++a) {
                 double s = 0;
-                for (int b = 0; b < rp; ++b) s += at(rb + (size_t)J * rp4 + b) * GR[(size_t)b * rp + a];
+                for (int b = 0; b <= a; ++b) s += at(rb + (size_t)J * rp4 + b) * ARi[(size_t)b * rp + a];
                 out[rb + (size_t)J * rp4 + a] = s;
             }
     }
+    S.bal = (double*)dev_alloc(h, std::max<size_t>(1, bal.size()) * sizeof(double));
+    if (!bal.empty()) PH_CUDA(cudaMemcpy(S.bal, bal.data(), bal.size() * sizeof(double), cudaMemcpyHostToDevice));
+    S.bal_off = (long long*)dev_alloc(h, std::max<size_t>(1, bal_off.size()) * sizeof(long long));
+    if (!bal_off.empty())
+        PH_CUDA(cudaMemcpy(S.bal_off, bal_off.data(), bal_off.size() * sizeof(long long), cudaMemcpyHostToDevice));
     S.proj = dev_alloc(h, std::max<size_t>(1, out.size()) * sc);
     if (sc == 4) {
         std::vector<float> f(out.begin(), out.end());
@@ -274,9 +329,11 @@ void build_projection(ph_handle* h) {
     S.proj_ready = true;
 }
 
+// The exact cores at n_theta parameters into out (n_theta x H_elems): H*_k, or with `balanced` the
+// cores K*_k = Q_L^T W Q_R in the orthonormal bases.
 template <typename T>
 void far_project_typed(ph_handle* h, DevView<T>& v, const double* thetas_host, int n_theta, T* out,
-                       cudaStream_t stream) {
+                       cudaStream_t stream, bool balanced = false) {
     Surrogate& S = sur_of(h);
     const int nk = v.n_keys, dt = h->opts.dtheta;
     if (nk == 0 || n_theta == 0) return;
@@ -298,9 +355,27 @@ void far_project_typed(ph_handle* h, DevView<T>& v, const double* thetas_host, i
                                                                  (long long)h->H_elems);
         PH_LAUNCH("project_left_kernel");
     }
+    if (!balanced) class_transform<T, T>(h, v, out, nullptr, out, (long long)h->H_elems, n_theta, 1, stream);
     PH_CUDA(cudaStreamSynchronize(stream));
     dev_free(h, Tm);
     dev_free(h, d_th);
+}
+
+template <typename TI, typename TO>
+void class_transform(ph_handle* h, DevView<TO>& v, const TI* in, const float* in_scale, TO* out, long long stride,
+                     int n_theta, int inverse, cudaStream_t s) {
+    Surrogate& S = *h->sur;
+    const int nk = v.n_keys;
+    if (nk == 0 || n_theta == 0) return;
+    const size_t smem = (size_t)2 * 64 * 64 * sizeof(double);
+    PH_CUDA(cudaFuncSetAttribute(class_transform_kernel<TI, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    for (int t0 = 0; t0 < n_theta; t0 += 65535) {
+        const int cnt = std::min(65535, n_theta - t0);
+        class_transform_kernel<TI, TO><<<dim3(nk, cnt), kT, smem, s>>>(v, in + (long long)t0 * stride, in_scale,
+                                                                      out + (long long)t0 * stride, stride, S.bal,
+                                                                      S.bal_off, inverse);
+        PH_LAUNCH("class_transform_kernel");
+    }
 }
 
 // ------------------------------------------------------------------------------- the network
@@ -675,8 +750,10 @@ void train_typed(ph_handle* h, DevView<T>& v, const double* th_train, int n_trai
     // targets: the projected cores of the training and validation thetas
     T* Ht = (T*)dev_alloc(h, (size_t)n_train * n_out * sizeof(T));
     T* Hv = (T*)dev_alloc(h, (size_t)n_val * n_out * sizeof(T));
-    far_project_typed<T>(h, v, th_train, n_train, Ht, s);
-    far_project_typed<T>(h, v, th_val, n_val, Hv, s);
+    // the network learns the cores in orthonormal bases (K = A_L H A_R^T): there the squared error
+    // of a core is the squared error of its coupling matrix L H R^T
+    far_project_typed<T>(h, v, th_train, n_train, Ht, s, true);
+    far_project_typed<T>(h, v, th_val, n_val, Hv, s, true);
     auto t1 = std::chrono::steady_clock::now();
     rep.targets_seconds = std::chrono::duration<double>(t1 - t0).count();
     // class scales s_k (RMS of the class's training targets) and the initial output bias (mean)
@@ -718,6 +795,8 @@ void train_typed(ph_handle* h, DevView<T>& v, const double* th_train, int n_trai
     S.params = (float*)dev_alloc(h, (size_t)L.total * sizeof(float));
     S.wbf = (__nv_bfloat16*)dev_alloc(h, (size_t)L.qtotal * sizeof(__nv_bfloat16));
     S.work = (float*)dev_alloc(h, (size_t)std::max(H, 32) * sizeof(float));
+    if (S.kbuf) dev_free(h, S.kbuf);
+    S.kbuf = (float*)dev_alloc(h, (size_t)std::max<long long>(1, n_out) * sizeof(float));
     PH_CUDA(cudaMemcpy(S.params, p0.data(), p0.size() * sizeof(float), cudaMemcpyHostToDevice));
     weights_to_bf16(s, L, dt, H, n_out, S.params, S.wbf);
     float* G = (float*)dev_alloc(h, (size_t)L.total * sizeof(float));
@@ -805,6 +884,7 @@ void train_typed(ph_handle* h, DevView<T>& v, const double* th_train, int n_trai
         PH_CUDA(cudaMemcpyAsync(Hp + (size_t)t * n_out, h->d_H, (size_t)n_out * sizeof(T), cudaMemcpyDeviceToDevice, s));
     }
     h->instantiated = false;  // the handle's cores were overwritten by the validation
+    class_transform<T, T>(h, v, Hp, nullptr, Hp, n_out, n_val, 0, s);  // polynomial cores into the same bases
     double* d_err = (double*)dev_alloc(h, (size_t)4 * std::max(1, n_val) * sizeof(double));
     PH_CUDA(cudaMemsetAsync(d_err, 0, (size_t)4 * std::max(1, n_val) * sizeof(double), s));
     const dim3 eg((unsigned)std::min<long long>(ceil_div(n_out, kT), 64), (unsigned)std::max(1, n_val));
@@ -842,6 +922,13 @@ void train_typed(ph_handle* h, DevView<T>& v, const double* th_train, int n_trai
 }
 
 template <typename T>
+DevView<T>& view_of(ph_handle* h);
+template <>
+DevView<float>& view_of<float>(ph_handle* h) { return h->vf; }
+template <>
+DevView<double>& view_of<double>(ph_handle* h) { return h->vd; }
+
+template <typename T>
 void infer_typed(ph_handle* h, const double* theta, cudaStream_t s) {
     Surrogate& S = *h->sur;
     const Layout L(S.n_in, S.hidden, S.n_out);
@@ -853,9 +940,11 @@ void infer_typed(ph_handle* h, const double* theta, cudaStream_t s) {
                                                                         S.hidden, th[0], th[1], th[2], lo[0], lo[1],
                                                                         lo[2], hi[0], hi[1], hi[2], S.work);
     const int grid = (int)std::max<long long>(1, std::min<long long>(ceil_div(S.n_out, kT / 32), (long long)h->num_sms * 8));
-    infer_out_kernel<T><<<grid, kT, (size_t)S.hidden * sizeof(float), s>>>(S.params, S.wbf, L.b3, L.q3, S.hidden, S.n_out,
-                                                                          S.work, S.scale, (T*)h->d_H);
+    infer_out_kernel<float><<<grid, kT, (size_t)S.hidden * sizeof(float), s>>>(S.params, S.wbf, L.b3, L.q3, S.hidden,
+                                                                              S.n_out, S.work, S.scale, S.kbuf);
     PH_LAUNCH("surrogate inference");
+    DevView<T>& v = view_of<T>(h);
+    class_transform<float, T>(h, v, S.kbuf, nullptr, (T*)h->d_H, S.n_out, 1, 1, s);  // K -> H
     if (h->adj_ready) transpose_H(h, s);
 }
 
