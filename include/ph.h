@@ -352,6 +352,14 @@ ph_status ph_surrogate_use(ph_handle* h, int enable);
 ph_status ph_mlp_check(int n_in, int hidden, int n_out, const float* params, int batch, const float* U,
                        const float* T, float* Y, float* grads, double* loss);
 
+/* Test hook of the TT-cross compressor (no GPU involved): greedy TT-cross and TT-rounding (§2.1)
+ * of a dense host tensor of q dimensions (Fortran order, dims[0] fastest) with tolerance eps and
+ * rank cap (0: none).  Writes the ranks r_0..r_q (q + 1 ints), the reconstructed tensor (same
+ * size and order as tensor) and the number of distinct entries the cross evaluated.  The offline
+ * build uses the same routine on the far-field tensors when compressor = 1. */
+ph_status ph_tt_cross_check(int q, const int* dims, const double* tensor, double eps, int cap, int* ranks,
+                            double* approx, long* evals);
+
 /* Fill *info with sizes and counts of a built handle. */
 ph_status ph_get_info(const ph_handle* h, ph_info* info);
 

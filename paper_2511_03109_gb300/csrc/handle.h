@@ -7,6 +7,7 @@
 #include <new>
 #include <stdexcept>
 #include <string>
+#include <functional>
 #include <vector>
 
 #include "common.cuh"
@@ -284,6 +285,10 @@ ph_status take_timeout(ph_handle* h);
 // TT-SVD truncation rank at one cut (offline.cu): smallest r >= 1 whose discarded tail is at
 // most delta2, then the cap (0: none), then numerically tied singular values kept together.
 int choose_rank_sv(const double* s, int n, double delta2, int cap);
+// ttcross_host.cpp: greedy TT-cross of a tensor given entry-wise, then TT-rounding (cores Fortran
+// (r_k, n_k, r_{k+1}), ranks r_0..r_q); returns the number of distinct entries evaluated
+long long tt_cross_round(const std::vector<int>& dims, const std::function<double(const int*)>& f, double eps, int cap,
+                         unsigned long long seed, std::vector<std::vector<double>>& cores, std::vector<int>& ranks);
 // Host FP64 thin SVD of a small m x n column-major matrix, s descending (ttsvd_host.cpp).
 void svd_small(int m, int n, const std::vector<double>& A, std::vector<double>& U, std::vector<double>& s,
                std::vector<double>& Vt);

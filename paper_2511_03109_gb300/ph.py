@@ -121,6 +121,8 @@ _SIGS = {
                                      C.POINTER(SurrogateOpts), C.POINTER(SurrogateReport), _P]),
     "ph_surrogate_use": (C.c_int, [_H, C.c_int]),
     "ph_mlp_check": (C.c_int, [C.c_int, C.c_int, C.c_int, _F, C.c_int, _F, _F, _F, _F, C.POINTER(C.c_double)]),
+    "ph_tt_cross_check": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_double, C.c_int,
+                                    C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_long)]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -344,6 +346,21 @@ def mlp_check(n_in, hidden, n_out, params, U, T):
     fp = lambda a: a.ctypes.data_as(_F)
     check(ph_mlp_check(n_in, hidden, n_out, fp(p), B, fp(U), fp(T), fp(Y), fp(g), C.byref(loss)))
     return Y, g, loss.value
+
+
+def tt_cross_check(tensor, eps, cap=0):
+    """The library's TT-cross + TT-rounding of a dense tensor (ph_tt_cross_check, host only):
+    returns (ranks, reconstructed tensor, entries evaluated)."""
+    A = np.asfortranarray(tensor, dtype=np.float64)
+    dims = np.array(A.shape, dtype=np.int32)
+    ranks = np.zeros(A.ndim + 1, dtype=np.int32)
+    out = np.zeros(A.size, dtype=np.float64)
+    ev = C.c_long()
+    flat = np.ascontiguousarray(A.ravel(order="F"))
+    check(ph_tt_cross_check(A.ndim, dims.ctypes.data_as(C.POINTER(C.c_int)), flat.ctypes.data_as(C.POINTER(C.c_double)),
+                            float(eps), int(cap), ranks.ctypes.data_as(C.POINTER(C.c_int)),
+                            out.ctypes.data_as(C.POINTER(C.c_double)), C.byref(ev)))
+    return ranks.tolist(), out.reshape(A.shape, order="F"), ev.value
 
 
 def _colmajor(X) -> bool:
