@@ -102,6 +102,10 @@ typedef struct {
                               The near and far grids are independent: each field interpolates on its own
                               nodes (the near field often needs fewer, e.g. 5 per dimension for
                               d_theta = 3).  ph_matvec_batched then applies one theta at a time. */
+    int compressor;        /* far-field tensors: 0 (default) TT-SVD of the formed tensor on the GPU (QR +
+                              SVD per cut, FP64); 1 greedy TT-cross + TT-rounding on the host (§2.1, the
+                              paper's compressor), which evaluates only the entries it needs.  The
+                              near field always uses TT-SVD. */
 } ph_build_opts;
 
 /* Sizes and counts of a built handle; all byte counts are of stored data. */

@@ -135,8 +135,9 @@ def tt_cross(f, dims, eps, rank_cap=None, max_sweeps=200, rook_steps=3, samples=
     index; each sweep adds at most one pivot per bond (bond ranks capped at rank_cap and at the
     unfolding sizes).  A sweep whose pivot residuals are all <= eps * max |entry seen| is checked
     on `samples` random entries; if the interpolant misses one of them by more, its prefixes and
-    suffixes join the index sets of every bond (the restricted super cores can look exact while
-    the tensor is not, e.g. for separable kernels) and the sweeps go on."""
+    suffixes join the index sets of the bonds wherever the sets stay nested (the restricted super
+    cores can look exact while the tensor is not, e.g. for separable kernels) and the sweeps go
+    on."""
     T = Entries(f, dims)
     q = len(T.dims)
     rng = np.random.default_rng(seed)
@@ -188,18 +189,32 @@ def tt_cross(f, dims, eps, rank_cap=None, max_sweeps=200, rook_steps=3, samples=
             if err[w] <= eps * vmax:
                 break
             x = tuple(int(v) for v in probe[w])
-            grown = False
+            # bonds that take the pair (prefix, suffix) of the missed entry: both new, room left, and
+            # the sets stay nested (the cross interpolation needs I_{k+1} in I_k x n_k and
+            # J_{k+1} in n_{k+1} x J_{k+2}): the pair's shorter prefix / suffix present or added too
+            take = []
             for k in range(q - 1):
                 rows_max = len(I[k]) * T.dims[k]
                 cols_max = T.dims[k + 1] * len(J[k + 2])
-                if len(I[k + 1]) >= min(rows_max + 1, cols_max + 1, (rank_cap or rows_max + 1)):
-                    continue
-                if x[:k + 1] not in I[k + 1] and x[k + 1:] not in J[k + 1]:
+                take.append(len(I[k + 1]) < min(rows_max, cols_max, rank_cap or rows_max)
+                            and x[:k + 1] not in I[k + 1] and x[k + 1:] not in J[k + 1])
+            changed = True
+            while changed:
+                changed = False
+                for k in range(q - 1):
+                    if not take[k]:
+                        continue
+                    left_ok = k == 0 or take[k - 1] or x[:k] in I[k]
+                    right_ok = k + 2 >= q or take[k + 1] or x[k + 2:] in J[k + 2]
+                    if not (left_ok and right_ok):
+                        take[k] = False
+                        changed = True
+            if not any(take):
+                break
+            for k in range(q - 1):
+                if take[k]:
                     I[k + 1].append(x[:k + 1])
                     J[k + 1].append(x[k + 1:])
-                    grown = True
-            if not grown:
-                break
     cores = _cross_cores(T, I, J)
     ranks = [1] + [len(I[k]) for k in range(1, q)] + [1]
     T.I, T.J = I, J  # the index sets, for inspection

@@ -534,6 +534,8 @@ ph_status ph_offline_build(const double* points, long n, ph_kernel kernel, const
             return fail(nullptr, PH_ERR_INVALID_ARG, "ph_offline_build: bad parameter box or degree");
     if (o->near_unshared != 0 && o->near_unshared != 1)
         return fail(nullptr, PH_ERR_INVALID_ARG, "ph_offline_build: near_unshared must be 0 or 1");
+    if (o->compressor != 0 && o->compressor != 1)
+        return fail(nullptr, PH_ERR_INVALID_ARG, "ph_offline_build: compressor must be 0 (TT-SVD) or 1 (TT-cross)");
     ph_handle* h = nullptr;
     try {
         h = new ph_handle();

@@ -799,7 +799,64 @@ ph_status offline_build(ph_handle* h, const double* points, long n) {
     std::vector<std::vector<std::vector<double>>> key_cores(nkeys);
     std::vector<double> far_sp, far_th;
     long long hoff = 0;
-    if (nkeys > 0) {
+    if (nkeys > 0 && o.compressor == 1) {
+        // TT-cross + TT-rounding on the host (§2.1): the tensor M_k is never formed; its entries
+        // are kernel values on the Chebyshev grids of the class's boxes and the theta grid
+        std::vector<int> dims;
+        for (int k = 0; k < d; ++k) dims.push_back(ps);
+        for (int k = 0; k < dt; ++k) dims.push_back(pt[k]);
+        for (int k = 0; k < d; ++k) dims.push_back(ps);
+        const int kern = (int)h->kernel;
+        std::atomic<int> next{0};
+        std::vector<std::string> errors(nkeys);
+        auto work = [&]() {
+            for (int key = next++; key < nkeys; key = next++) {
+                try {
+                    const int fb = plan.key_rep[key];
+                    const Node& s = plan.nodes[plan.far_s[fb]];
+                    const Node& t = plan.nodes[plan.far_t[fb]];
+                    std::vector<double> xs(kMaxDim * kMaxPs), yt(kMaxDim * kMaxPs);
+                    for (int k = 0; k < d; ++k) {
+                        cheb_nodes(s.lo[k], s.hi[k], ps, &xs[k * kMaxPs]);
+                        cheb_nodes(t.lo[k], t.hi[k], ps, &yt[k * kMaxPs]);
+                    }
+                    const std::vector<double>& tn = h->theta_nodes;
+                    std::function<double(const int*)> f = [&](const int* x) {
+                        double a[kMaxDim], b[kMaxDim], th[kMaxDim];
+                        for (int k = 0; k < d; ++k) {
+                            a[k] = xs[k * kMaxPs + x[k]];
+                            b[k] = yt[k * kMaxPs + x[d + dt + k]];
+                        }
+                        for (int k = 0; k < dt; ++k) th[k] = tn[k * kMaxPTheta + x[d + k]];
+                        return kappa_host(kern, a, b, th, d);
+                    };
+                    std::vector<int> ranks;
+                    tt_cross_round(dims, f, o.tol, o.rank_cap, 0x5eedull + (unsigned long long)key, key_cores[key], ranks);
+                    for (int k = 0; k <= Delta; ++k) h->key_ranks[(size_t)key * (Delta + 1) + k] = ranks[k];
+                } catch (const std::exception& e) {
+                    errors[key] = e.what();
+                }
+            }
+        };
+        const int nthr = std::max(1, std::min(64, (int)std::thread::hardware_concurrency()));
+        std::vector<std::thread> pool;
+        for (int w = 0; w < nthr; ++w) pool.emplace_back(work);
+        for (auto& th : pool) th.join();
+        for (int key = 0; key < nkeys; ++key)
+            if (!errors[key].empty()) throw Error(PH_ERR_CUDA, "TT-cross of a far-field tensor failed: " + errors[key]);
+        for (int key = 0; key < nkeys; ++key) {
+            const int* rk = &h->key_ranks[(size_t)key * (Delta + 1)];
+            for (int k = 0; k < Delta; ++k) {
+                auto& core = key_cores[key][k];
+                bool theta_core = (k >= d && k < d + dt);
+                auto& arena = theta_core ? far_th : far_sp;
+                h->key_off[(size_t)key * Delta + k] = (long long)arena.size();
+                arena.insert(arena.end(), core.begin(), core.end());
+            }
+            h->key_hoff[key] = hoff;
+            hoff += (long long)rk[d] * rk[d + dt];
+        }
+    } else if (nkeys > 0) {
         TTEngine eng;
         eng.h = h;
         PH_BLAS(cublasCreate(&eng.blas));

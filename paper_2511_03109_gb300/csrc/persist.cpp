@@ -14,7 +14,7 @@
 
 namespace {
 
-const char kMagic[8] = {'P', 'H', 'L', 'I', 'B', '0', '0', '4'};  // 004: near mirror sharing, near-field grid
+const char kMagic[8] = {'P', 'H', 'L', 'I', 'B', '0', '0', '5'};  // 005: near sharing, near grid, compressor
 constexpr int kArenas = 9;  // near, near theta, far, far theta, S/T, U, E, L/R, tensor-core R (this order)
 
 struct Writer {

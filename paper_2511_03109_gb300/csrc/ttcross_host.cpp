@@ -9,9 +9,11 @@
 // one index; each sweep visits the bonds and adds to each one pivot found by partially pivoted
 // (rook) search on the residual of the bond's two-mode unfolding; a sweep whose pivot residuals
 // are all below eps times the largest entry seen is checked on random entries, and a missed entry
-// joins every bond's sets through its prefixes and suffixes.  The interpolant
-//   T~ = C_1 P_1^+ C_2 P_2^+ ... C_q,  C_k(i)[a, b] = T(I_k[a], i, J_{k+1}[b]),  P_k = T(I_{k+1}, J_{k+1})
-// is recompressed by TT-rounding (Oseledets 2011, Alg. 2) with the truncation rule of TT-SVD.
+// joins the bonds' sets through its prefixes and suffixes wherever the sets stay nested.  The interpolant
+//   T~ = C_1 P_1^{-1} C_2 P_2^{-1} ... C_q,  C_k(i)[a, b] = T(I_k[a], i, J_{k+1}[b]),  P_k = T(I_{k+1}, J_{k+1})
+// (C_k P_k^{-1} formed as Q Q[piv]^{-1} from an orthonormal basis Q of C_k's columns, which stays
+// accurate when the pivots span many orders of magnitude) is recompressed by TT-rounding
+// (Oseledets 2011, Alg. 2) with the truncation rule of TT-SVD.
 #include <algorithm>
 #include <cmath>
 #include <functional>
@@ -62,6 +64,65 @@ std::vector<double> pinv(int m, int n, const std::vector<double>& A) {
     return X;
 }
 
+// Inverse of a square r x r column-major matrix by Gauss-Jordan elimination with partial
+// pivoting, without truncation: the greedy pivots make the elimination well ordered even when P
+// spans many orders of magnitude, where a truncated pseudo-inverse would discard the small pivots
+// the cross needs.  A pivot matrix made singular by an enrichment falls back to the pseudo-inverse.
+std::vector<double> pivot_inverse(int r, const std::vector<double>& P) {
+    std::vector<double> A(P), X((size_t)r * r, 0.0);
+    double amax = 0.0;
+    for (double v : P) amax = std::max(amax, std::fabs(v));
+    for (int i = 0; i < r; ++i) X[i + (size_t)r * i] = 1.0;
+    for (int c = 0; c < r; ++c) {
+        int piv = c;
+        for (int i = c + 1; i < r; ++i)
+            if (std::fabs(A[i + (size_t)r * c]) > std::fabs(A[piv + (size_t)r * c])) piv = i;
+        if (!(std::fabs(A[piv + (size_t)r * c]) > 1e-300 + 1e-15 * amax)) return pinv(r, r, P);
+        if (piv != c)
+            for (int k = 0; k < r; ++k) {
+                std::swap(A[piv + (size_t)r * k], A[c + (size_t)r * k]);
+                std::swap(X[piv + (size_t)r * k], X[c + (size_t)r * k]);
+            }
+        const double inv = 1.0 / A[c + (size_t)r * c];
+        for (int k = 0; k < r; ++k) {
+            A[c + (size_t)r * k] *= inv;
+            X[c + (size_t)r * k] *= inv;
+        }
+        for (int i = 0; i < r; ++i) {
+            if (i == c) continue;
+            const double fct = A[i + (size_t)r * c];
+            if (fct == 0.0) continue;
+            for (int k = 0; k < r; ++k) {
+                A[i + (size_t)r * k] -= fct * A[c + (size_t)r * k];
+                X[i + (size_t)r * k] -= fct * X[c + (size_t)r * k];
+            }
+        }
+    }
+    return X;
+}
+
+// Orthonormal basis Q (m x n, column-major) of the columns of C by Gram-Schmidt with one
+// reorthogonalisation pass (the columns of a cross fiber block are linearly independent).
+std::vector<double> orth_columns(int m, int n, const std::vector<double>& C) {
+    std::vector<double> Q(C);
+    for (int j = 0; j < n; ++j) {
+        double* qj = &Q[(size_t)m * j];
+        for (int pass = 0; pass < 2; ++pass)
+            for (int i = 0; i < j; ++i) {
+                const double* qi = &Q[(size_t)m * i];
+                double d = 0.0;
+                for (int t = 0; t < m; ++t) d += qi[t] * qj[t];
+                for (int t = 0; t < m; ++t) qj[t] -= d * qi[t];
+            }
+        double nrm = 0.0;
+        for (int t = 0; t < m; ++t) nrm += qj[t] * qj[t];
+        nrm = std::sqrt(nrm);
+        const double inv = nrm > 0 ? 1.0 / nrm : 0.0;
+        for (int t = 0; t < m; ++t) qj[t] *= inv;
+    }
+    return Q;
+}
+
 struct Cross {
     const std::vector<int>& dims;
     Entries& T;
@@ -75,68 +136,71 @@ struct Cross {
         x.insert(x.end(), b.begin(), b.end());
         return T(x.data());
     }
-    // P_k = T(I[k+1], J[k+1]) (column-major) and its pseudo-inverse
-    std::vector<double> pivots_pinv(int k) {
-        const int r = (int)I[k + 1].size();
-        std::vector<double> P((size_t)r * r);
-        for (int b = 0; b < r; ++b)
-            for (int a = 0; a < r; ++a) P[a + (size_t)r * b] = at(I[k + 1][a], {}, J[k + 1][b]);
-        return pinv(r, r, P);
+    // C_k = T(I[k][a], i, J[k+1][b]), rows (a, i) with a fastest, column-major
+    std::vector<double> fiber(int k) {
+        const int r0 = (int)I[k].size(), n = dims[k], r1 = (int)J[k + 1].size();
+        std::vector<double> C((size_t)r0 * n * r1);
+        for (int b = 0; b < r1; ++b)
+            for (int i = 0; i < n; ++i)
+                for (int a = 0; a < r0; ++a) C[a + (size_t)r0 * (i + (size_t)n * b)] = at(I[k][a], {i}, J[k + 1][b]);
+        return C;
     }
-    // residual of bond k's super core on column (j, b): rows (a, i) with a fastest
-    std::vector<double> residual_col(int k, int j, int b, const std::vector<double>& Pi) {
+    // G_k = C_k P_k^{-1} for a bond k < q - 1, formed stably as Q Q[piv]^{-1}, Q an orthonormal basis
+    // of C_k's columns and piv the rows of C_k that are the pivots I[k+1] (the sets are nested).
+    std::vector<double> interp(int k) {
+        const int r0 = (int)I[k].size(), n = dims[k], r1 = (int)I[k + 1].size();
+        const int m = r0 * n;
+        const std::vector<double> Q = orth_columns(m, r1, fiber(k));
+        std::vector<double> Qp((size_t)r1 * r1);
+        for (int e = 0; e < r1; ++e) {
+            const Tuple& pre = I[k + 1][e];
+            const Tuple head(pre.begin(), pre.end() - 1);
+            const int a = (int)(std::find(I[k].begin(), I[k].end(), head) - I[k].begin());
+            const int row = a + r0 * pre.back();
+            for (int c = 0; c < r1; ++c) Qp[e + (size_t)r1 * c] = Q[row + (size_t)m * c];
+        }
+        const std::vector<double> Qi = pivot_inverse(r1, Qp);  // r1 x r1
+        std::vector<double> G((size_t)m * r1, 0.0);
+        for (int e = 0; e < r1; ++e)
+            for (int c = 0; c < r1; ++c) {
+                const double v = Qi[c + (size_t)r1 * e];
+                if (v == 0.0) continue;
+                for (int row = 0; row < m; ++row) G[row + (size_t)m * e] += Q[row + (size_t)m * c] * v;
+            }
+        return G;
+    }
+    // residual of bond k's super core on column (j, b): rows (a, i) with a fastest; Gk = interp(k)
+    std::vector<double> residual_col(int k, int j, int b, const std::vector<double>& Gk) {
         const int ra = (int)I[k].size(), n = dims[k], r = (int)I[k + 1].size();
-        std::vector<double> right(r), w(r, 0.0), out((size_t)ra * n);
-        for (int c = 0; c < r; ++c) right[c] = at(I[k + 1][c], {j}, J[k + 2][b]);
-        for (int c = 0; c < r; ++c)
-            for (int e = 0; e < r; ++e) w[c] += Pi[c + (size_t)r * e] * right[e];
+        const int m = ra * n;
+        std::vector<double> right(r), out((size_t)m);
+        for (int e = 0; e < r; ++e) right[e] = at(I[k + 1][e], {j}, J[k + 2][b]);
         for (int i = 0; i < n; ++i)
             for (int a = 0; a < ra; ++a) {
+                const int row = a + ra * i;
                 double apx = 0.0;
-                for (int c = 0; c < r; ++c) apx += at(I[k][a], {i}, J[k + 1][c]) * w[c];
-                out[a + (size_t)ra * i] = at(I[k][a], {i, j}, J[k + 2][b]) - apx;
+                for (int e = 0; e < r; ++e) apx += Gk[row + (size_t)m * e] * right[e];
+                out[row] = at(I[k][a], {i, j}, J[k + 2][b]) - apx;
             }
         return out;
     }
     // residual on row (a, i): columns (j, b) with j fastest
-    std::vector<double> residual_row(int k, int a, int i, const std::vector<double>& Pi) {
-        const int n1 = dims[k + 1], rb = (int)J[k + 2].size(), r = (int)I[k + 1].size();
-        std::vector<double> left(r), w(r, 0.0), out((size_t)n1 * rb);
-        for (int c = 0; c < r; ++c) left[c] = at(I[k][a], {i}, J[k + 1][c]);
-        for (int e = 0; e < r; ++e)
-            for (int c = 0; c < r; ++c) w[e] += left[c] * Pi[c + (size_t)r * e];  // (P^+)[c][e]
+    std::vector<double> residual_row(int k, int a, int i, const std::vector<double>& Gk) {
+        const int ra = (int)I[k].size(), n1 = dims[k + 1], rb = (int)J[k + 2].size(), r = (int)I[k + 1].size();
+        const int m = ra * dims[k], row = a + ra * i;
+        std::vector<double> out((size_t)n1 * rb);
         for (int b = 0; b < rb; ++b)
             for (int j = 0; j < n1; ++j) {
                 double apx = 0.0;
-                for (int e = 0; e < r; ++e) apx += w[e] * at(I[k + 1][e], {j}, J[k + 2][b]);
+                for (int e = 0; e < r; ++e) apx += Gk[row + (size_t)m * e] * at(I[k + 1][e], {j}, J[k + 2][b]);
                 out[j + (size_t)n1 * b] = at(I[k][a], {i, j}, J[k + 2][b]) - apx;
             }
         return out;
     }
-    // cores C_k P_k^+ (Fortran (r_k, n_k, r_{k+1}))
+    // the TT cores: G_k (k < q - 1) and C_q (Fortran (r_k, n_k, r_{k+1}))
     std::vector<std::vector<double>> cores() {
         std::vector<std::vector<double>> G(q);
-        for (int k = 0; k < q; ++k) {
-            const int r0 = (int)I[k].size(), n = dims[k], r1 = (int)J[k + 1].size();
-            std::vector<double> C((size_t)r0 * n * r1);
-            for (int b = 0; b < r1; ++b)
-                for (int i = 0; i < n; ++i)
-                    for (int a = 0; a < r0; ++a) C[a + (size_t)r0 * (i + (size_t)n * b)] = at(I[k][a], {i}, J[k + 1][b]);
-            if (k < q - 1) {
-                const std::vector<double> Pi = pivots_pinv(k);  // r1 x r1
-                std::vector<double> Gk(C.size(), 0.0);
-                const size_t rows = (size_t)r0 * n;
-                for (int b = 0; b < r1; ++b)
-                    for (int c = 0; c < r1; ++c) {
-                        const double p = Pi[c + (size_t)r1 * b];
-                        if (p == 0.0) continue;
-                        for (size_t row = 0; row < rows; ++row) Gk[row + rows * b] += C[row + rows * c] * p;
-                    }
-                G[k].swap(Gk);
-            } else {
-                G[k].swap(C);
-            }
-        }
+        for (int k = 0; k < q; ++k) G[k] = (k < q - 1) ? interp(k) : fiber(k);
         return G;
     }
 };
@@ -155,6 +219,41 @@ double tt_entry(const std::vector<std::vector<double>>& G, const std::vector<int
 }
 
 }  // namespace
+
+// kappa(x, y; theta) of the ph_kernel enumeration on the host (the formulas of the kernel table in
+// ph.h), for the entries the cross asks for.
+double kappa_host(int kernel, const double* x, const double* y, const double* th, int d) {
+    double r2 = 0.0;
+    for (int k = 0; k < d; ++k) r2 += (x[k] - y[k]) * (x[k] - y[k]);
+    const double l = th[0];
+    switch (kernel) {
+        case PH_KERNEL_GAUSS: return std::exp(-r2 / (2.0 * l * l));
+        case PH_KERNEL_MATERN32: {
+            const double s = std::sqrt(3.0 * r2) / l;
+            return (1.0 + s) * std::exp(-s);
+        }
+        case PH_KERNEL_MATERN52: {
+            const double s = std::sqrt(5.0 * r2) / l;
+            return (1.0 + s + s * s / 3.0) * std::exp(-s);
+        }
+        case PH_KERNEL_ANISO_GAUSS: {
+            double q = 0.0;
+            for (int k = 0; k < d; ++k) q += (x[k] - y[k]) * (x[k] - y[k]) / (2.0 * th[k] * th[k]);
+            return std::exp(-q);
+        }
+        case PH_KERNEL_SE: return std::exp(-r2 / (l * l));
+        case PH_KERNEL_EXPONENTIAL: return std::exp(-std::sqrt(r2) / l);
+        case PH_KERNEL_MULTIQUADRIC: return std::sqrt(1.0 + r2 / (l * l));
+        case PH_KERNEL_POLY: return 1.0 + l * r2 + l * l * r2 * r2;
+        case PH_KERNEL_POLY2: return 1.0 + th[0] * r2 + th[1] * th[1] * r2 * r2;
+        case PH_KERNEL_POLYXY: {
+            double dot = 0.0;
+            for (int k = 0; k < d; ++k) dot += x[k] * y[k];
+            return (1.0 + dot) * (1.0 + dot) * (1.0 + l);
+        }
+    }
+    return 0.0;
+}
 
 // TT-rounding of cores (Fortran (r_k, n_k, r_{k+1})): right-to-left orthogonalisation, then
 // left-to-right truncated SVDs with delta^2 = eps^2 ||T||^2 / (q - 1) and the rank rule of TT-SVD.
@@ -249,17 +348,17 @@ long long tt_cross_round(const std::vector<int>& dims, const std::function<doubl
         for (int k = 0; k + 1 < q; ++k) {
             const int rows_max = (int)X.I[k].size() * dims[k], cols_max = dims[k + 1] * (int)X.J[k + 2].size();
             if ((int)X.I[k + 1].size() >= std::min(std::min(rows_max, cols_max), cap_r)) continue;
-            const std::vector<double> Pi = X.pivots_pinv(k);
+            const std::vector<double> Gk = X.interp(k);
             int j = rnd(dims[k + 1]), b = rnd((int)X.J[k + 2].size());
             double best = 0.0;
             int ba = -1, bi = -1, bj = -1, bb = -1;
             for (int step = 0; step < 3; ++step) {
-                const std::vector<double> e = X.residual_col(k, j, b, Pi);
+                const std::vector<double> e = X.residual_col(k, j, b, Gk);
                 int ir = 0;
                 for (size_t t = 1; t < e.size(); ++t)
                     if (std::fabs(e[t]) > std::fabs(e[ir])) ir = (int)t;
                 const int a = ir % (int)X.I[k].size(), i = ir / (int)X.I[k].size();
-                const std::vector<double> er = X.residual_row(k, a, i, Pi);
+                const std::vector<double> er = X.residual_row(k, a, i, Gk);
                 int jc = 0;
                 for (size_t t = 1; t < er.size(); ++t)
                     if (std::fabs(er[t]) > std::fabs(er[jc])) jc = (int)t;
@@ -272,7 +371,7 @@ long long tt_cross_round(const std::vector<int>& dims, const std::function<doubl
                 }
             }
             worst = std::max(worst, best);
-            if (ba < 0 || best <= 1e-14 * vmax) continue;
+            if (ba < 0 || best <= 0.1 * eps * vmax) continue;  // no pivots below the target accuracy
             Tuple ni(X.I[k][ba]);
             ni.push_back(bi);
             Tuple nj(1, bj);
@@ -300,18 +399,37 @@ long long tt_cross_round(const std::vector<int>& dims, const std::function<doubl
             }
         }
         if (emax <= eps * vmax) break;
-        bool grown = false;
+        // bonds that take the pair (prefix, suffix) of the missed entry: both new, room left, and
+        // the sets stay nested (the pair's shorter prefix / suffix present or added with it)
+        auto has = [](const std::vector<Tuple>& set, const Tuple& t) {
+            return std::find(set.begin(), set.end(), t) != set.end();
+        };
+        std::vector<char> take(q, 0);
         for (int k = 0; k + 1 < q; ++k) {
             const int rows_max = (int)X.I[k].size() * dims[k], cols_max = dims[k + 1] * (int)X.J[k + 2].size();
-            if ((int)X.I[k + 1].size() >= std::min(std::min(rows_max + 1, cols_max + 1), cap_r)) continue;
-            Tuple ni(wx.begin(), wx.begin() + k + 1), nj(wx.begin() + k + 1, wx.end());
-            if (std::find(X.I[k + 1].begin(), X.I[k + 1].end(), ni) != X.I[k + 1].end() ||
-                std::find(X.J[k + 1].begin(), X.J[k + 1].end(), nj) != X.J[k + 1].end())
-                continue;
-            X.I[k + 1].push_back(ni);
-            X.J[k + 1].push_back(nj);
-            grown = true;
+            take[k] = (int)X.I[k + 1].size() < std::min(std::min(rows_max, cols_max), cap_r) &&
+                      !has(X.I[k + 1], Tuple(wx.begin(), wx.begin() + k + 1)) &&
+                      !has(X.J[k + 1], Tuple(wx.begin() + k + 1, wx.end()));
         }
+        for (bool changed = true; changed;) {
+            changed = false;
+            for (int k = 0; k + 1 < q; ++k) {
+                if (!take[k]) continue;
+                const bool left_ok = (k == 0) || take[k - 1] || has(X.I[k], Tuple(wx.begin(), wx.begin() + k));
+                const bool right_ok = (k + 2 >= q) || take[k + 1] || has(X.J[k + 2], Tuple(wx.begin() + k + 2, wx.end()));
+                if (!left_ok || !right_ok) {
+                    take[k] = 0;
+                    changed = true;
+                }
+            }
+        }
+        bool grown = false;
+        for (int k = 0; k + 1 < q; ++k)
+            if (take[k]) {
+                X.I[k + 1].push_back(Tuple(wx.begin(), wx.begin() + k + 1));
+                X.J[k + 1].push_back(Tuple(wx.begin() + k + 1, wx.end()));
+                grown = true;
+            }
         if (!grown) break;
     }
     cores = X.cores();

@@ -47,6 +47,7 @@ void validate_handle(const ph_handle& h, const std::vector<size_t>& arena_bytes)
     need(o.fmt == PH_FMT_H || o.fmt == PH_FMT_H2, "format");
     need(o.prec == PH_FP32 || o.prec == PH_FP64, "precision");
     need(o.coupling == 0 || o.coupling == 1, "coupling mode");
+    need(o.compressor == 0 || o.compressor == 1, "compressor");
     need((int)h.kernel >= 0 && (int)h.kernel <= PH_KERNEL_POLY2, "kernel");
     need(h.scalar == (o.prec == PH_FP32 ? 4u : 8u), "scalar size");
     int PD = 1, Pf = 1, P = 1;  // P: the near-field grid

@@ -43,7 +43,7 @@ class BuildOpts(C.Structure):
                 ("near_tol", C.c_double), ("rank_cap", C.c_int), ("fmt", C.c_int),
                 ("prec", C.c_int), ("dedup", C.c_int), ("check_finite", C.c_int),
                 ("device", C.c_int), ("coupling", C.c_int), ("near_unshared", C.c_int),
-                ("near_degree", C.c_int * 3)]
+                ("near_degree", C.c_int * 3), ("compressor", C.c_int)]
 
 
 class Info(C.Structure):
@@ -151,7 +151,7 @@ def check(status, handle=None):
 
 def make_opts(d, theta_lo, theta_hi, degree, p_s, l_max, eta, tol, rank_cap=0, fmt="h2",
               prec="fp32", dedup=True, check_finite=False, near_tol=-1.0, device=0,
-              coupling="explicit", near_shared=True, near_degree=None) -> BuildOpts:
+              coupling="explicit", near_shared=True, near_degree=None, compressor="svd") -> BuildOpts:
     o = BuildOpts()
     o.d = d
     o.dtheta = len(theta_lo)
@@ -171,6 +171,7 @@ def make_opts(d, theta_lo, theta_hi, degree, p_s, l_max, eta, tol, rank_cap=0, f
     o.near_unshared = 0 if near_shared else 1
     for k in range(len(theta_lo)):
         o.near_degree[k] = 0 if near_degree is None else int(near_degree[k])
+    o.compressor = {"svd": 0, "cross": 1}[compressor]
     return o
 
 

@@ -70,6 +70,12 @@ def test_build_argument_checks_without_gpu():
     swapped = ph.make_opts(2, [1.0], [0.1], [8], 4, 2, 1.0, 1e-6)  # empty parameter box
     with pytest.raises(ph.PHError):
         ph.ParametricMatrix(P, "gauss", swapped)
+    for field, value in (("compressor", 2), ("near_unshared", 3)):  # options outside their sets
+        o = ph.make_opts(2, [0.1], [1.0], [8], 4, 2, 1.0, 1e-6)
+        setattr(o, field, value)
+        with pytest.raises(ph.PHError) as e:
+            ph.ParametricMatrix(P, "gauss", o)
+        assert e.value.status == ph.PH_ERR_INVALID_ARG, field
 
 
 def test_null_handle_calls_fail_cleanly():
@@ -104,13 +110,13 @@ def test_load_rejects_missing_foreign_old_and_corrupt_files(tmp_path):
     assert load(tmp_path / "missing.ph") == ph.PH_ERR_IO
     (tmp_path / "foreign.ph").write_bytes(b"not a handle at all" * 10)
     assert load(tmp_path / "foreign.ph") == ph.PH_ERR_IO
-    (tmp_path / "old.ph").write_bytes(b"PHLIB003" + bytes(4096))
+    (tmp_path / "old.ph").write_bytes(b"PHLIB004" + bytes(4096))
     assert load(tmp_path / "old.ph") == ph.PH_ERR_IO
-    (tmp_path / "short.ph").write_bytes(b"PHLIB004" + bytes(3))
+    (tmp_path / "short.ph").write_bytes(b"PHLIB005" + bytes(3))
     assert load(tmp_path / "short.ph") == ph.PH_ERR_IO
     # the right magic followed by 8-byte words of 2^40: whichever field reads a length first
     # gets an impossible one
-    (tmp_path / "huge.ph").write_bytes(b"PHLIB004" + struct.pack("<Q", 1 << 40) * 4096)
+    (tmp_path / "huge.ph").write_bytes(b"PHLIB005" + struct.pack("<Q", 1 << 40) * 4096)
     assert load(tmp_path / "huge.ph") == ph.PH_ERR_IO
 
 
@@ -132,7 +138,7 @@ def _handle_file(mutate=None):
     }
     if mutate:
         mutate(f)
-    out = bytearray(b"PHLIB004")
+    out = bytearray(b"PHLIB005")
     vec = lambda fmt, xs: struct.pack("<Q", len(xs)) + struct.pack("<%d%s" % (len(xs), fmt), *xs)
     out += struct.pack("<i", 0)  # kernel: Gaussian
     out += bytes(f["opts"])
@@ -183,6 +189,10 @@ def _bad_sharing_option(f):
     f["opts"].near_unshared = 2
 
 
+def _bad_compressor(f):
+    f["opts"].compressor = 7
+
+
 @pytest.mark.parametrize("mutate", [
     _set("nb_off", [1]),            # the block's cores would end one entry past the arena
     _set("perm", 4, 0),             # a permutation entry outside 0..n-1
@@ -194,7 +204,9 @@ def _bad_sharing_option(f):
     _short_near_arena,              # an arena shorter than its element count (length still consistent)
     _other_p_s,                     # options from another build (p_s^d no longer the stored PD)
     _bad_sharing_option,            # a near-sharing option that is neither 0 nor 1
-], ids=["nb_off", "perm", "near_t", "nb_woff", "rank", "leaves", "node_end", "arena", "p_s", "sharing"])
+    _bad_compressor,                # a compressor that is neither TT-SVD nor TT-cross
+], ids=["nb_off", "perm", "near_t", "nb_woff", "rank", "leaves", "node_end", "arena", "p_s", "sharing",
+        "compressor"])
 def test_load_refuses_corrupt_contents(tmp_path, mutate):
     """ph_load checks every stored offset, index and size on the host before it touches a
     device: one flipped value in an otherwise consistent file is refused with PH_ERR_IO."""
