@@ -393,6 +393,14 @@ const char* ph_last_error(const ph_handle* h);
 ph_status ph_plan(const double* points, long n, int d, int l_max, double eta,
                   long* counts, int* perm);
 
+/* The same for the adaptive cluster tree (§3.2 with a leaf-size stopping rule instead of a fixed
+ * depth): a node is split while it holds more than leaf_size points and its level is below 20;
+ * empty children are dropped.  The block tree then also has near blocks between a leaf and an
+ * inner cluster (counted in counts[2] and counts[5]; counts[6] counts leaf x leaf blocks only) and
+ * far blocks between clusters of different levels, whose translation classes are keyed by both
+ * levels.  Planning only: ph_offline_build builds uniform trees. */
+ph_status ph_plan_adaptive(const double* points, long n, int d, int leaf_size, double eta, long* counts, int* perm);
+
 /* Every launch of the library also sits in an NVTX range named for its kind (and each
  * ph_instantiate / ph_matvec / ph_matvec_batched in one named for the call); without an
  * attached tool these are no-ops.

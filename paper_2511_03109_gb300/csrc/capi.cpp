@@ -486,21 +486,22 @@ const char* ph_last_error(const ph_handle* h) {
     return g_last_error.c_str();
 }
 
-ph_status ph_plan(const double* points, long n, int d, int l_max, double eta, long* counts, int* perm) {
+static ph_status plan_counts(const double* points, long n, int d, int l_max, double eta, int leaf_size, long* counts,
+                             int* perm) {
     return guarded(nullptr, [&]() -> ph_status {
-        if (!points || !counts || n < 1 || d < 1 || d > 3 || l_max < 0 || l_max > 10 || !(eta > 0))
-            return fail(nullptr, PH_ERR_INVALID_ARG, "ph_plan: invalid argument");
         ph::Plan plan;
-        ph::build_plan(points, n, d, l_max, eta, true, plan);
+        ph::build_plan(points, n, d, l_max, eta, true, plan, leaf_size);
         long sum_near = 0;
         for (size_t b = 0; b < plan.near_s.size(); ++b)
             sum_near += (long)plan.nodes[plan.near_s[b]].size() * plan.nodes[plan.near_t[b]].size();
+        for (size_t b = 0; b < plan.inner_near_s.size(); ++b)
+            sum_near += (long)plan.nodes[plan.inner_near_s[b]].size() * plan.nodes[plan.inner_near_t[b]].size();
         int maxper = 0;
         for (size_t l = 0; l + 1 < plan.near_by_leaf.size(); ++l)
             maxper = std::max(maxper, plan.near_by_leaf[l + 1] - plan.near_by_leaf[l]);
         counts[0] = (long)plan.nodes.size();
         counts[1] = (long)plan.leaves.size();
-        counts[2] = (long)plan.near_s.size();
+        counts[2] = (long)(plan.near_s.size() + plan.inner_near_s.size());
         counts[3] = (long)plan.far_s.size();
         counts[4] = (long)plan.key_rep.size();
         counts[5] = sum_near;
@@ -510,6 +511,18 @@ ph_status ph_plan(const double* points, long n, int d, int l_max, double eta, lo
             for (long i = 0; i < n; ++i) perm[i] = plan.perm[i];
         return PH_OK;
     });
+}
+
+ph_status ph_plan(const double* points, long n, int d, int l_max, double eta, long* counts, int* perm) {
+    if (!points || !counts || n < 1 || d < 1 || d > 3 || l_max < 0 || l_max > 10 || !(eta > 0))
+        return fail(nullptr, PH_ERR_INVALID_ARG, "ph_plan: invalid argument");
+    return plan_counts(points, n, d, l_max, eta, 0, counts, perm);
+}
+
+ph_status ph_plan_adaptive(const double* points, long n, int d, int leaf_size, double eta, long* counts, int* perm) {
+    if (!points || !counts || n < 1 || d < 1 || d > 3 || leaf_size < 1 || !(eta > 0))
+        return fail(nullptr, PH_ERR_INVALID_ARG, "ph_plan_adaptive: invalid argument");
+    return plan_counts(points, n, d, 0, eta, leaf_size, counts, perm);
 }
 
 ph_status ph_offline_build(const double* points, long n, ph_kernel kernel, const ph_build_opts* o,

@@ -39,6 +39,7 @@ struct Plan {
     std::vector<int> perm;             // cluster position -> original point index
     std::vector<int> leaves;           // node ids of the leaves, in cluster order
     std::vector<int> near_s, near_t;   // near blocks (node ids), grouped by target leaf
+    std::vector<int> inner_near_s, inner_near_t;  // adaptive trees: near blocks with an inner cluster
     std::vector<int> far_s, far_t;     // far blocks (node ids), grouped by target node
     std::vector<int> far_key;          // far block -> compressed-tensor class
     std::vector<int> key_rep;          // class -> representative far block
@@ -50,7 +51,11 @@ struct Plan {
 // Builds the uniform cluster tree of depth l_max over [0,1]^d and the block
 // cluster tree with admissibility eta.  Throws std::invalid_argument for
 // points outside the root box.
-void build_plan(const double* points, long n, int d, int l_max, double eta, bool dedup, Plan& plan);
+// leaf_size > 0 builds the adaptive tree instead: a node is split while it holds more than
+// leaf_size points and its level is below 20 (l_max is then ignored); near blocks between a leaf
+// and an inner cluster go to inner_near_s / inner_near_t.
+void build_plan(const double* points, long n, int d, int l_max, double eta, bool dedup, Plan& plan,
+                int leaf_size = 0);
 
 bool kernel_translation_invariant(ph_kernel k);
 

@@ -16,6 +16,7 @@ namespace {
 // Equality counts as admissible; the slack keeps exact ties (eta = sqrt(d) at
 // a one-box gap) independent of rounding.
 constexpr double kAdmSlack = 1e-12;
+constexpr int kAdaptiveMaxDepth = 20;
 
 double diam(const Node& a, int d) {
     double s = 0;
@@ -43,12 +44,15 @@ struct Builder {
     int l_max;
     Plan& plan;
     std::vector<int> order;  // cluster order being assembled
+    int leaf_size = 0;       // > 0: adaptive tree (split while more points than this, level < 20)
 
     // Splits node `id` holding the original indices `idx` (ascending).
     void split(int id, std::vector<int>& idx) {
         Node& nd = plan.nodes[id];
         nd.begin = (int)order.size();
-        if (nd.level >= l_max) {
+        const bool leaf = leaf_size > 0 ? ((int)idx.size() <= leaf_size || nd.level >= kAdaptiveMaxDepth)
+                                        : nd.level >= l_max;
+        if (leaf) {
             order.insert(order.end(), idx.begin(), idx.end());
             nd.end = (int)order.size();
             nd.leaf = (int)plan.leaves.size();
@@ -107,7 +111,7 @@ void block_recurse(Plan& plan, int s, int t, double eta, std::vector<std::pair<i
 
 bool kernel_translation_invariant(ph_kernel k) { return k != PH_KERNEL_POLYXY; }
 
-void build_plan(const double* points, long n, int d, int l_max, double eta, bool dedup, Plan& plan) {
+void build_plan(const double* points, long n, int d, int l_max, double eta, bool dedup, Plan& plan, int leaf_size) {
     if (d < 1 || d > kMaxDim) throw std::invalid_argument("d must be 1..3");
     if (n < 1) throw std::invalid_argument("n must be positive");
     for (long i = 0; i < n * d; ++i) {
@@ -122,7 +126,7 @@ void build_plan(const double* points, long n, int d, int l_max, double eta, bool
     plan.nodes.push_back(root);
     std::vector<int> idx(n);
     for (long i = 0; i < n; ++i) idx[i] = (int)i;
-    Builder b{points, d, l_max, plan, {}};
+    Builder b{points, d, l_max, plan, {}, leaf_size};
     b.order.reserve(n);
     b.split(0, idx);
     plan.perm = std::move(b.order);
@@ -137,8 +141,15 @@ void build_plan(const double* points, long n, int d, int l_max, double eta, bool
     });
     plan.near_by_leaf.assign(plan.leaves.size() + 1, 0);
     for (auto& p : near) {
-        if (plan.nodes[p.first].leaf < 0 || plan.nodes[p.second].leaf < 0)
-            throw std::logic_error("near block between non-leaf clusters");
+        // an adaptive tree also has near blocks between a leaf and an inner cluster: they are
+        // planned (counted) but not grouped by leaf; the offline build refuses such plans
+        const bool leaves = plan.nodes[p.first].leaf >= 0 && plan.nodes[p.second].leaf >= 0;
+        if (!leaves) {
+            if (leaf_size <= 0) throw std::logic_error("near block between non-leaf clusters");
+            plan.inner_near_s.push_back(p.first);
+            plan.inner_near_t.push_back(p.second);
+            continue;
+        }
         plan.near_s.push_back(p.first);
         plan.near_t.push_back(p.second);
         plan.near_by_leaf[plan.nodes[p.first].leaf + 1]++;
@@ -160,13 +171,14 @@ void build_plan(const double* points, long n, int d, int l_max, double eta, bool
         plan.far_t.push_back(t);
         int key;
         if (dedup) {
-            // class = (level, offset of B_t from B_s in units of the box side): with a
-            // translation-invariant kernel M_b depends only on it (§5.2)
+            // class = (both levels, offset of B_t from B_s in units of the finer box side): with
+            // a translation-invariant kernel M_b depends only on it (§5.2); in a uniform tree both
+            // levels are equal and this is (level, offset in box sides)
             const Node& a = plan.nodes[s];
             const Node& c = plan.nodes[t];
-            std::vector<long> k{a.level};
-            for (int q = 0; q < d; ++q)
-                k.push_back(std::lround((c.lo[q] - a.lo[q]) / (a.hi[q] - a.lo[q])));
+            const double unit = std::min(a.hi[0] - a.lo[0], c.hi[0] - c.lo[0]);
+            std::vector<long> k{a.level, c.level};
+            for (int q = 0; q < d; ++q) k.push_back(std::lround((c.lo[q] - a.lo[q]) / unit));
             auto it = classes.find(k);
             if (it == classes.end()) {
                 key = (int)plan.key_rep.size();

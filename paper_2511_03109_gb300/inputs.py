@@ -42,6 +42,27 @@ def uniform_thetas(lo, hi, count: int, seed: int) -> np.ndarray:
     return lo + (hi - lo) * rng.random((count, lo.size))
 
 
+def gaussian_mixture_points(n: int, d: int, components: int, seed: int) -> np.ndarray:
+    """n points in [0,1]^d from an equal-weight mixture of anisotropic Gaussians: means uniform in
+    [0.1, 0.9]^d, per-component axis standard deviations log-uniform in [0.005, 0.05], a random
+    rotation per component (the Q factor of a Gaussian matrix, signs fixed by R's diagonal),
+    points clipped to the unit cube."""
+    rng = np.random.default_rng(seed)
+    means = rng.uniform(0.1, 0.9, (components, d))
+    sds = np.exp(rng.uniform(np.log(0.005), np.log(0.05), (components, d)))
+    rots = []
+    for _ in range(components):
+        Q, R = np.linalg.qr(rng.standard_normal((d, d)))
+        rots.append(Q * np.sign(np.diag(R)))
+    which = rng.integers(0, components, n)
+    Z = rng.standard_normal((n, d))
+    P = np.empty((n, d))
+    for c in range(components):
+        sel = which == c
+        P[sel] = means[c] + (Z[sel] * sds[c]) @ rots[c].T
+    return np.clip(P, 0.0, 1.0)
+
+
 def sample_rows(n: int, count: int, seed: int) -> np.ndarray:
     """count distinct row indices drawn uniformly from 0..n-1, sorted."""
     rng = np.random.default_rng(seed)

@@ -104,6 +104,8 @@ _SIGS = {
     "ph_load": (C.c_int, [C.c_char_p, C.c_int, C.POINTER(_H)]),
     "ph_destroy": (None, [_H]),
     "ph_last_error": (C.c_char_p, [_H]),
+    "ph_plan_adaptive": (C.c_int, [C.POINTER(C.c_double), C.c_long, C.c_int, C.c_int, C.c_double,
+                                   C.POINTER(C.c_long), C.POINTER(C.c_int)]),
     "ph_plan": (C.c_int, [C.POINTER(C.c_double), C.c_long, C.c_int, C.c_int, C.c_double,
                           C.POINTER(C.c_long), C.POINTER(C.c_int)]),
     "ph_version": (C.c_char_p, []),
@@ -182,15 +184,19 @@ def selftest_wait_bound(device=0):
     return st, waited.value
 
 
-def plan(points, l_max, eta):
-    """Host-only tree / block tree sizes (ph_plan); returns (counts dict, perm)."""
-    import numpy as np
+def plan(points, l_max, eta, leaf_size=None):
+    """Host-only tree / block tree sizes (ph_plan, or ph_plan_adaptive with leaf_size); returns
+    (counts dict, perm)."""
     P = np.ascontiguousarray(points, dtype=np.float64)
     n, d = P.shape
     counts = (C.c_long * 8)()
     perm = np.empty(n, dtype=np.int32)
-    check(ph_plan(P.ctypes.data_as(C.POINTER(C.c_double)), n, d, int(l_max), float(eta), counts,
-                  perm.ctypes.data_as(C.POINTER(C.c_int))))
+    if leaf_size is None:
+        check(ph_plan(P.ctypes.data_as(C.POINTER(C.c_double)), n, d, int(l_max), float(eta), counts,
+                      perm.ctypes.data_as(C.POINTER(C.c_int))))
+    else:
+        check(ph_plan_adaptive(P.ctypes.data_as(C.POINTER(C.c_double)), n, d, int(leaf_size), float(eta), counts,
+                               perm.ctypes.data_as(C.POINTER(C.c_int))))
     keys = ["nodes", "leaves", "near", "far", "far_keys", "near_entries", "max_near_per_leaf", "depth"]
     return dict(zip(keys, list(counts))), perm
 
