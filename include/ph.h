@@ -364,6 +364,15 @@ ph_status ph_mlp_check(int n_in, int hidden, int n_out, const float* params, int
 ph_status ph_tt_cross_check(int q, const int* dims, const double* tensor, double eps, int cap, int* ranks,
                             double* approx, long* evals);
 
+/* Test hook (no GPU): the offline build's TT-cross of one far-field tensor M_b (App. A.4): modes
+ * (i_1..i_d, theta_1..theta_dtheta, j_1..j_d), entries kappa(x_i, y_j; theta) on the Chebyshev grids
+ * of the target box [s_lo, s_hi], the source box [t_lo, t_hi] (p_s nodes per dimension) and the
+ * parameter box (degree[k] + 1 nodes); writes the ranks (2d + dtheta + 1 ints) and the reconstructed
+ * tensor (Fortran order, p_s^(2d) prod(degree + 1) doubles). */
+ph_status ph_far_cross_check(int kernel, int d, int dtheta, int p_s, const int* degree, const double* s_lo,
+                             const double* s_hi, const double* t_lo, const double* t_hi, const double* theta_lo,
+                             const double* theta_hi, double eps, int cap, int* ranks, double* approx);
+
 /* Fill *info with sizes and counts of a built handle. */
 ph_status ph_get_info(const ph_handle* h, ph_info* info);
 

@@ -290,6 +290,9 @@ int choose_rank_sv(const double* s, int n, double delta2, int cap);
 long long tt_cross_round(const std::vector<int>& dims, const std::function<double(const int*)>& f, double eps, int cap,
                          unsigned long long seed, std::vector<std::vector<double>>& cores, std::vector<int>& ranks);
 double kappa_host(int kernel, const double* x, const double* y, const double* th, int d);
+long long far_cross(int kernel, int d, int dt, int ps, const int* pt, const double* s_lo, const double* s_hi,
+                    const double* t_lo, const double* t_hi, const double* theta_nodes, double eps, int cap,
+                    unsigned long long seed, std::vector<std::vector<double>>& cores, std::vector<int>& ranks);
 // Host FP64 thin SVD of a small m x n column-major matrix, s descending (ttsvd_host.cpp).
 void svd_small(int m, int n, const std::vector<double>& A, std::vector<double>& U, std::vector<double>& s,
                std::vector<double>& Vt);

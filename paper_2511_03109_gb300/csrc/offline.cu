@@ -802,10 +802,6 @@ ph_status offline_build(ph_handle* h, const double* points, long n) {
     if (nkeys > 0 && o.compressor == 1) {
         // TT-cross + TT-rounding on the host (§2.1): the tensor M_k is never formed; its entries
         // are kernel values on the Chebyshev grids of the class's boxes and the theta grid
-        std::vector<int> dims;
-        for (int k = 0; k < d; ++k) dims.push_back(ps);
-        for (int k = 0; k < dt; ++k) dims.push_back(pt[k]);
-        for (int k = 0; k < d; ++k) dims.push_back(ps);
         const int kern = (int)h->kernel;
         std::atomic<int> next{0};
         std::vector<std::string> errors(nkeys);
@@ -815,23 +811,9 @@ ph_status offline_build(ph_handle* h, const double* points, long n) {
                     const int fb = plan.key_rep[key];
                     const Node& s = plan.nodes[plan.far_s[fb]];
                     const Node& t = plan.nodes[plan.far_t[fb]];
-                    std::vector<double> xs(kMaxDim * kMaxPs), yt(kMaxDim * kMaxPs);
-                    for (int k = 0; k < d; ++k) {
-                        cheb_nodes(s.lo[k], s.hi[k], ps, &xs[k * kMaxPs]);
-                        cheb_nodes(t.lo[k], t.hi[k], ps, &yt[k * kMaxPs]);
-                    }
-                    const std::vector<double>& tn = h->theta_nodes;
-                    std::function<double(const int*)> f = [&](const int* x) {
-                        double a[kMaxDim], b[kMaxDim], th[kMaxDim];
-                        for (int k = 0; k < d; ++k) {
-                            a[k] = xs[k * kMaxPs + x[k]];
-                            b[k] = yt[k * kMaxPs + x[d + dt + k]];
-                        }
-                        for (int k = 0; k < dt; ++k) th[k] = tn[k * kMaxPTheta + x[d + k]];
-                        return kappa_host(kern, a, b, th, d);
-                    };
                     std::vector<int> ranks;
-                    tt_cross_round(dims, f, o.tol, o.rank_cap, 0x5eedull + (unsigned long long)key, key_cores[key], ranks);
+                    far_cross(kern, d, dt, ps, pt, s.lo, s.hi, t.lo, t.hi, h->theta_nodes.data(), o.tol, o.rank_cap,
+                              0x5eedull + (unsigned long long)key, key_cores[key], ranks);
                     for (int k = 0; k <= Delta; ++k) h->key_ranks[(size_t)key * (Delta + 1) + k] = ranks[k];
                 } catch (const std::exception& e) {
                     errors[key] = e.what();

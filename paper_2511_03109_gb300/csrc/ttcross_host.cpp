@@ -439,6 +439,38 @@ long long tt_cross_round(const std::vector<int>& dims, const std::function<doubl
 
 }  // namespace ph
 
+namespace ph {
+
+// The far-field tensor M_k of one translation class by TT-cross (the offline build's route for
+// compressor = 1): modes (i_1..i_d, k_1..k_dtheta, j_1..j_d), entries kappa(x_i, y_j; theta_k)
+// with x on the Chebyshev grid of the target box [s_lo, s_hi], y on the source box's, theta on the
+// far-field theta nodes (theta_nodes: dtheta rows of kMaxPTheta).
+long long far_cross(int kernel, int d, int dt, int ps, const int* pt, const double* s_lo, const double* s_hi,
+                    const double* t_lo, const double* t_hi, const double* theta_nodes, double eps, int cap,
+                    unsigned long long seed, std::vector<std::vector<double>>& cores, std::vector<int>& ranks) {
+    std::vector<int> dims;
+    for (int k = 0; k < d; ++k) dims.push_back(ps);
+    for (int k = 0; k < dt; ++k) dims.push_back(pt[k]);
+    for (int k = 0; k < d; ++k) dims.push_back(ps);
+    std::vector<double> xs((size_t)kMaxDim * kMaxPs), yt((size_t)kMaxDim * kMaxPs);
+    for (int k = 0; k < d; ++k) {
+        cheb_nodes(s_lo[k], s_hi[k], ps, &xs[(size_t)k * kMaxPs]);
+        cheb_nodes(t_lo[k], t_hi[k], ps, &yt[(size_t)k * kMaxPs]);
+    }
+    std::function<double(const int*)> f = [&](const int* x) {
+        double a[kMaxDim], b[kMaxDim], th[kMaxDim];
+        for (int k = 0; k < d; ++k) {
+            a[k] = xs[(size_t)k * kMaxPs + x[k]];
+            b[k] = yt[(size_t)k * kMaxPs + x[d + dt + k]];
+        }
+        for (int k = 0; k < dt; ++k) th[k] = theta_nodes[(size_t)k * kMaxPTheta + x[d + k]];
+        return kappa_host(kernel, a, b, th, d);
+    };
+    return tt_cross_round(dims, f, eps, cap, seed, cores, ranks);
+}
+
+}  // namespace ph
+
 // Test hook (no GPU): TT-cross + TT-rounding of a dense host tensor (Fortran order, dims[0]
 // fastest); writes the ranks (q + 1 values) and the reconstructed tensor, and the number of
 // distinct entries the cross evaluated.  Declared in include/ph.h.
@@ -472,6 +504,52 @@ extern "C" ph_status ph_tt_cross_check(int q, const int* dims, const double* ten
                 rest /= d[k];
             }
             approx[t] = ph::tt_entry(G, d, x.data());
+        }
+        return PH_OK;
+    });
+}
+
+// Test hook (no GPU): the offline build's TT-cross of one far-field tensor (far_cross) for the
+// boxes [s_lo, s_hi] (target) and [t_lo, t_hi] (source) of [0,1]^d and the parameter box
+// [theta_lo, theta_hi] with degree[k] + 1 Chebyshev nodes per dimension; writes the ranks
+// (2d + dtheta + 1 values) and the reconstructed tensor (Fortran order, modes i, theta, j).
+// Declared in include/ph.h.
+extern "C" ph_status ph_far_cross_check(int kernel, int d, int dtheta, int p_s, const int* degree,
+                                        const double* s_lo, const double* s_hi, const double* t_lo,
+                                        const double* t_hi, const double* theta_lo, const double* theta_hi,
+                                        double eps, int cap, int* ranks, double* approx) {
+    if (kernel < 0 || kernel > PH_KERNEL_POLY2 || d < 1 || d > 3 || dtheta < 1 || dtheta > 3 || p_s < 1 ||
+        p_s > ph::kMaxPs || !degree || !s_lo || !s_hi || !t_lo || !t_hi || !theta_lo || !theta_hi || !ranks ||
+        !approx || !(eps > 0))
+        return ph::fail(nullptr, PH_ERR_INVALID_ARG, "ph_far_cross_check: invalid argument");
+    return ph::guarded(nullptr, [&]() -> ph_status {
+        int pt[ph::kMaxDim] = {1, 1, 1};
+        std::vector<double> nodes((size_t)ph::kMaxDim * ph::kMaxPTheta, 0.0);
+        for (int k = 0; k < dtheta; ++k) {
+            if (degree[k] < 0 || degree[k] + 1 > ph::kMaxPTheta)
+                throw ph::Error(PH_ERR_INVALID_ARG, "ph_far_cross_check: bad degree");
+            pt[k] = degree[k] + 1;
+            ph::cheb_nodes(theta_lo[k], theta_hi[k], pt[k], &nodes[(size_t)k * ph::kMaxPTheta]);
+        }
+        std::vector<std::vector<double>> G;
+        std::vector<int> r;
+        ph::far_cross(kernel, d, dtheta, p_s, pt, s_lo, s_hi, t_lo, t_hi, nodes.data(), eps, cap, 7ull, G, r);
+        const int q = 2 * d + dtheta;
+        for (int k = 0; k <= q; ++k) ranks[k] = r[k];
+        std::vector<int> dims;
+        for (int k = 0; k < d; ++k) dims.push_back(p_s);
+        for (int k = 0; k < dtheta; ++k) dims.push_back(pt[k]);
+        for (int k = 0; k < d; ++k) dims.push_back(p_s);
+        long long total = 1;
+        for (int v : dims) total *= v;
+        std::vector<int> x(q, 0);
+        for (long long t = 0; t < total; ++t) {
+            long long rest = t;
+            for (int k = 0; k < q; ++k) {
+                x[k] = (int)(rest % dims[k]);
+                rest /= dims[k];
+            }
+            approx[t] = ph::tt_entry(G, dims, x.data());
         }
         return PH_OK;
     });

@@ -104,6 +104,9 @@ _SIGS = {
     "ph_load": (C.c_int, [C.c_char_p, C.c_int, C.POINTER(_H)]),
     "ph_destroy": (None, [_H]),
     "ph_last_error": (C.c_char_p, [_H]),
+    "ph_far_cross_check": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)]
+                           + [C.POINTER(C.c_double)] * 6 + [C.c_double, C.c_int, C.POINTER(C.c_int),
+                                                            C.POINTER(C.c_double)]),
     "ph_plan_adaptive": (C.c_int, [C.POINTER(C.c_double), C.c_long, C.c_int, C.c_int, C.c_double,
                                    C.POINTER(C.c_long), C.POINTER(C.c_int)]),
     "ph_plan": (C.c_int, [C.POINTER(C.c_double), C.c_long, C.c_int, C.c_int, C.c_double,
@@ -368,6 +371,25 @@ def tt_cross_check(tensor, eps, cap=0):
                             float(eps), int(cap), ranks.ctypes.data_as(C.POINTER(C.c_int)),
                             out.ctypes.data_as(C.POINTER(C.c_double)), C.byref(ev)))
     return ranks.tolist(), out.reshape(A.shape, order="F"), ev.value
+
+
+def far_cross_check(kernel, s_box, t_box, theta_lo, theta_hi, degree, p_s, eps, cap=0):
+    """The offline build's TT-cross of one far-field tensor (ph_far_cross_check, host only):
+    returns (ranks, reconstructed tensor with modes (i_1..i_d, theta.., j_1..j_d))."""
+    d = len(s_box[0])
+    dt = len(theta_lo)
+    arr = lambda v: np.ascontiguousarray(v, dtype=np.float64)
+    s_lo, s_hi, t_lo, t_hi, lo, hi = (arr(s_box[0]), arr(s_box[1]), arr(t_box[0]), arr(t_box[1]), arr(theta_lo),
+                                      arr(theta_hi))
+    deg = np.ascontiguousarray(degree, dtype=np.int32)
+    shape = [p_s] * d + [int(g) + 1 for g in degree] + [p_s] * d
+    out = np.zeros(int(np.prod(shape)), dtype=np.float64)
+    ranks = np.zeros(2 * d + dt + 1, dtype=np.int32)
+    dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+    check(ph_far_cross_check(KERNELS[kernel], d, dt, int(p_s), deg.ctypes.data_as(C.POINTER(C.c_int)), dp(s_lo),
+                             dp(s_hi), dp(t_lo), dp(t_hi), dp(lo), dp(hi), float(eps), int(cap),
+                             ranks.ctypes.data_as(C.POINTER(C.c_int)), dp(out)))
+    return ranks.tolist(), out.reshape(shape, order="F")
 
 
 def _colmajor(X) -> bool:

@@ -57,3 +57,23 @@ def test_rank_cap_is_respected():
     M = _far("matern32", 3, 4, [0.05], [0.5], [8])
     r, B, ev = ph.tt_cross_check(M, 1e-9, cap=8)
     assert max(r) <= 8
+
+
+@pytest.mark.parametrize("kern,d,lo,hi,deg,ps,bound", [
+    ("gauss", 2, [0.1], [1.0], [10], 6, 3),
+    ("matern32", 3, [0.05], [0.5], [8], 4, 3),
+    ("aniso_gauss", 3, [0.05] * 3, [0.5] * 3, [3, 3, 3], 4, 100),  # ranks near the cap: a looser bound
+])
+def test_offline_far_cross_reproduces_the_far_tensor(kern, d, lo, hi, deg, ps, bound):
+    """The offline build's route (ph_far_cross_check: kernel entries on the boxes' Chebyshev grids
+    and the theta grid, then TT-cross) against the oracle's far tensor M_b of the same boxes."""
+    from paper_2511_03109_gb300 import ph
+
+    s = tree.Cluster([], np.zeros(d), np.full(d, 0.25), 0)
+    t = tree.Cluster([], np.full(d, 0.5), np.r_[np.full(d - 1, 0.75), 0.25], 0)
+    M = pmatrix.far_tensor(kern, s, t, pmatrix.theta_grid(lo, hi, deg), ps)
+    r, A = ph.far_cross_check(kern, (s.lo, s.hi), (t.lo, t.hi), lo, hi, deg, ps, 1e-7, 64)
+    assert A.shape == M.shape
+    assert np.linalg.norm(A - M) <= bound * 1e-7 * np.linalg.norm(M)
+    _, rs = tensor.tt_svd(M, 1e-7, 64)
+    assert all(abs(a - b) <= 3 for a, b in zip(r, rs)), (r, rs)
