@@ -226,6 +226,59 @@ def test_load_refuses_corrupt_contents(tmp_path, mutate):
     assert not h.value
 
 
+def _two_leaf_file(mutate=None):
+    """A consistent handle file with two leaves of 2 points in 1-D and mirror sharing: near
+    blocks (1,1), (1,2), (2,1), (2,2) of rank 1, the block (2,1) reading the cores of (1,2)."""
+    import struct
+
+    f = {
+        "opts": ph.make_opts(1, [0.1], [1.0], [1], 2, 1, 1.0, 1e-6, fmt="h2", prec="fp64"),
+        "nb_rank": [1, 1, 1, 1], "nb_off": [0, 4, 4, 8], "nb_toff": [0, 2, 2, 4], "nb_woff": [0, 1, 2, 3, 4],
+        "near_elems": 12, "near_theta_elems": 6, "w_elems": 4,
+    }
+    if mutate:
+        mutate(f)
+    out = bytearray(b"PHLIB005")
+    vec = lambda fmt, xs: struct.pack("<Q", len(xs)) + struct.pack("<%d%s" % (len(xs), fmt), *xs)
+    out += struct.pack("<i", 0) + bytes(f["opts"]) + struct.pack("<iiii", 2, 3, 2, 2) + struct.pack("<Qd", 8, 0.0)
+    out += vec("i", f["nb_rank"]) + vec("q", f["nb_off"]) + vec("q", f["nb_toff"]) + vec("i", f["nb_woff"])
+    out += vec("i", []) + vec("q", []) + vec("q", []) + vec("q", []) + vec("q", [])
+    out += vec("q", []) + struct.pack("<q", 0) + vec("q", []) + struct.pack("<q", 0)
+    out += struct.pack("<7q", f["near_elems"], f["near_theta_elems"], 0, 0, 0, 0, f["w_elems"])
+    out += vec("d", [0.0] * 192) + vec("d", [0.0] * 192) + vec("d", [0.0] * 8)
+    out += struct.pack("<iqi", 1, 4, 1)                          # plan: d, n, depth
+    out += vec("i", [0, 1, 2, 3]) + vec("i", [1, 2])             # perm, leaves
+    out += vec("i", [1, 1, 2, 2]) + vec("i", [1, 2, 1, 2])       # near_s, near_t
+    out += vec("i", []) * 4
+    out += vec("i", [0, 2, 4]) + vec("i", []) + vec("i", [0])
+    nodes = [(0, -1, 0, 0, 4, -1, 0.0, 1.0, [1, 2]), (1, 0, 0, 0, 2, 0, 0.0, 0.5, []), (1, 0, 1, 2, 4, 1, 0.5, 1.0, [])]
+    out += struct.pack("<Q", len(nodes))
+    for level, parent, halves, begin, end, leaf, lo, hi, children in nodes:
+        out += struct.pack("<6i", level, parent, halves, begin, end, leaf)
+        out += struct.pack("<6d", lo, 0, 0, hi, 0, 0) + vec("i", children)
+    for nbytes in (12 * 8, 6 * 8, 0, 0, 0, 4 * 1 * 2 * 8, 2 * 2 * 2 * 8, 0, 0):
+        out += vec("B", [0] * nbytes)
+    return bytes(out)
+
+
+def test_load_checks_the_mirror_blocks(tmp_path):
+    """With mirror sharing the block (t, s) must read exactly the cores of its stored partner
+    (s, t): a file where it points elsewhere is refused before anything reaches a device."""
+    good = tmp_path / "good.ph"
+    good.write_bytes(_two_leaf_file())
+    h = C.c_void_p()
+    st = ph.ph_load(str(good).encode(), 0, C.byref(h))
+    assert st in (ph.PH_OK, ph.PH_ERR_CUDA), ph.ph_last_error(None)
+    if st == ph.PH_OK:
+        ph.ph_destroy(h)
+    for key, value in (("nb_off", [0, 4, 8, 8]), ("nb_toff", [0, 2, 4, 4])):
+        bad = tmp_path / f"bad_{key}.ph"
+        bad.write_bytes(_two_leaf_file(_set(key, value)))
+        h = C.c_void_p()
+        assert ph.ph_load(str(bad).encode(), 0, C.byref(h)) == ph.PH_ERR_IO, key
+        assert b"mirrored near block" in ph.ph_last_error(None), ph.ph_last_error(None)
+
+
 def test_alloc_failure_hook_and_check_without_gpu():
     assert ph.ph_inject_alloc_failure(3) == ph.PH_OK
     assert ph.ph_inject_alloc_failure(-1) == ph.PH_OK
