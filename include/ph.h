@@ -268,8 +268,8 @@ ph_status ph_selftest_timeout(ph_handle* h, void* stream);
 ph_status ph_inject_alloc_failure(long after);
 
 /* ------------------------------------------------------------------------------------------
- * Learned surrogate of the far-field cores.  The paper names learning the theta-dependence as
- * future work (§7); this part is an extension, not the paper's method.  In the H^2 format with
+ * Learned surrogate of the far-field cores.  The paper lists other parametric approximations as
+ * future work (§7); this learned one is an extension, not the paper's method.  In the H^2 format with
  * the explicit coupling (coupling = 0) the only theta-dependent far-field quantity is the core
  * H_k(theta) of each translation class (App. A.4); the spatial factors L_k, R_k stay fixed.  A
  * perceptron theta -> (H_k(theta))_k replaces the polynomial contraction of the stored theta

@@ -2,7 +2,7 @@
 
 Test infrastructure only (see ``oracle/__init__.py``).
 
-The paper names learning the parameter dependence as future work (§7); the network here is the
+The paper lists other parametric approximations as future work (§7); the network here is the
 one the library trains on the GPU, written out plainly so that its forward values and its
 gradients can be checked.  For a parameter theta in the box prod [lo_i, hi_i]:
 

@@ -1,5 +1,5 @@
-// Learned surrogate of the far-field cores H_k(theta) (an extension: the paper names learning the
-// theta-dependence as future work, §7).  In the explicit H^2 coupling C_k = L_k H_k(theta) R_k^T
+// Learned surrogate of the far-field cores H_k(theta) (an extension: the paper lists other
+// parametric approximations as future work, §7).  In the explicit H^2 coupling C_k = L_k H_k(theta) R_k^T
 // (§4.2, App. A.4) the spatial factors are fixed, so a network theta -> (H_k(theta))_k can replace
 // the contraction of the stored theta cores.  This file holds
 //   * the training targets: the exact cores in the gauge of L_k, R_k (least-squares projection of
